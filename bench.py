@@ -1,0 +1,354 @@
+"""Benchmark of the random-sampling multiscale solver on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the 2049^2 log-normal workload
+(eps = 2^-7, 32 x 32 patches of 64 cells, 16-cell buffers, 128 Gaussian
+samples per patch plus the boundary-delta columns of the patches on the
+domain boundary):
+
+  build the medium (face coefficients)              msp_build_medium
+  offline local solves, restriction                 msp_sample_patches
+  basis extraction, edge operators, preconditioner  msp_extract_basis
+  online solve of one batch of Dirichlet data       msp_online_solve
+
+Headline metric: local sample-solves per second of the whole step.  The
+online latency (p50/p99 over repeated single-request solves on the prebuilt
+basis) is reported beside it.  Inputs are synthetic and seeded; every step
+rebuilds everything, and the per-step working set (snapshots, 4.7 GB) is far
+larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica (weak scaling); the
+timed region is bracketed by a barrier and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "elliptic-2049-lognormal-32x32-b16-S128"
+METRIC = "local sample-solves/s"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0])); smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+
+def oracle_sample(budget_s: float = 15.0):
+    """Time the CPU oracle (as it stands) on a bounded sample of the workload:
+    the local solves of whole patches of the 2049^2 medium, interior and
+    boundary ones, until the time budget is used.  Returns solves/s."""
+    from oracle import elliptic as E
+    w = synth.workload_batched()
+    t0 = time.time()
+    aE, aN = E.face_coefficients(w["medium"])
+    t_med = time.time() - t0
+    patches = E.patch_boxes(2048, w["patches"])
+    order = [0, 33, 528, 17, 1023, 300, 700, 31, 992, 64]
+    solves, t_solve, used = 0, 0.0, []
+    for m in order:
+        P = patches[m]
+        t1 = time.time()
+        R = E.snapshots(aE, aN, P, w["seed"], 2048)
+        t_solve += time.time() - t1
+        solves += R.shape[1]
+        used.append(m)
+        if t_solve > budget_s:
+            break
+    # SuperLU factorisation and back-substitution run on one thread
+    return {"value": solves / t_solve, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{solves} local solves (patches {used}) of the 2049^2 workload by sparse LU + "
+                      f"back-substitution; face coefficients {t_med:.1f} s not counted"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(budget_s=3.0)
+    for _ in range(args.steps):
+        vals.append(oracle_sample(budget_s=8.0))
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "bounded per step (whole patches)"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_profile_case(args):
+    """One offline pass (sample + extract) and one online solve on the 513^2
+    log-normal medium (8 x 8 patches of 64 cells, 16-cell buffers, 128 samples):
+    the small case for detailed profiler captures of the same kernels."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    N = 512
+    ms = synth.lognormal(N, 2.0 ** -5, 64, 11)
+    ps = synth.uniform_patches(N, 8, 8, 16, 128)
+    med = msp.Medium(ms, ps)
+    st = med.sample(1, args.precision, tol=1e-10, max_iter=20000)
+    basis = med.extract(1e-6, args.precision)
+    u, it = basis.solve(torch.tensor(synth.phi_sin_cos(N), device="cuda"), tol=1e-8, max_iter=args.online_iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "lognormal-513-8x8", "solves": int(st.n_solves), "cg_iters": int(st.total_iters),
+                      "online_iters": int(it[0])}))
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1807_08848_gb300 as msp
+    from paper_1807_08848_gb300 import _native
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    lib = msp.load_library()
+    stream = torch.cuda.current_stream()
+    w = synth.workload_batched()
+    prec = args.precision
+    tol = 1e-10 if prec == "mixed" else 1e-10
+    phi_host = torch.tensor(w["phi"], dtype=torch.float64).reshape(1, -1).pin_memory()
+    phi_dev = phi_host.cuda()
+    n = 2049
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    state = {}
+
+    def step(host_io: bool):
+        med = msp.Medium(w["medium"], w["patches"])
+        st = med.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
+        basis = med.extract(w["tau"], prec)
+        if host_io:
+            ph = phi_host.cuda(non_blocking=True)
+        else:
+            ph = phi_dev
+        try:
+            u, it = basis.solve(ph, tol=w["online_tol"], max_iter=args.online_iters, want_iters=False)
+        except _native.MspError as e:
+            if e.status != _native.MSP_ERR_NOT_CONVERGED:
+                raise
+            u = None
+        if host_io and u is not None:
+            state["u_host"] = u.to("cpu", non_blocking=False)
+        state["med"], state["basis"] = med, basis
+        return med
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    # solve statistics of one step (outside the timed region)
+    med = msp.Medium(w["medium"], w["patches"])
+    stats = med.sample(w["seed"], prec, tol=tol, max_iter=20000)
+    n_solves = int(stats.n_solves)
+    n_gauss = int(np.sum(w["patches"].samples))
+    # dominant kernel timing (local solves) with events on the launching stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    med.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_kernel = ev0.elapsed_time(ev1) / 1e3
+    del med
+
+    # ---- timed region (device-resident inputs)
+    clocks = ClockSampler(dev)
+    barrier(); torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lib.msp_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(False)
+    e1.record(stream)
+    torch.cuda.synchronize(); barrier()
+    clk = clocks.stop()
+    launches = (lib.msp_kernel_launches() - launches0) / args.steps
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+
+    # ---- end to end through host buffers (medium description and phi from the
+    # host, the reconstructed field back to the host), wall clock with syncs
+    barrier(); torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        step(True)
+    torch.cuda.synchronize(); barrier()
+    t_e2e = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    h2d = int(w["medium"].modes.nbytes + 4 * 4 * (33 + 33 + 1024 + 1024) + phi_host.numel() * 8)
+    d2h = int(n * n * 8)
+
+    # ---- online latency on the prebuilt basis (single requests)
+    basis = state["basis"]
+    lat = []
+    ok = True
+    for i in range(args.online_reqs):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        try:
+            basis.solve(phi_dev, tol=w["online_tol"], max_iter=args.online_iters, want_iters=False)
+        except _native.MspError:
+            ok = False
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - a) * 1e3)
+    lat.sort()
+
+    # ---- roofline of the dominant kernel: FP32 (mixed) / FP64 arithmetic of the CG
+    # iterations.  Algorithmic flops per CG iteration and unknown: 9 for the
+    # 5-point apply (5 mul + 4 add with the diagonal precomputed as a sum), 2 each
+    # for the dots, 2 each for the three axpys, 1 for the Jacobi scaling: 22.
+    flops = 22.0 * float(stats.unknown_iters)
+    achieved = flops / t_kernel / 1e12
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    peak = fp32_peak if prec == "mixed" else fp32_peak / 64.0
+    value = n_solves * world / t
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_nodes": "2049x2049", "patches": "32x32", "buffer": 16,
+                   "gaussian_samples_per_patch": 128, "gaussian_solves": n_gauss, "local_solves": n_solves,
+                   "precision": prec, "local_tol": tol, "tau": w["tau"], "online_tol": w["online_tol"],
+                   "l2": "working set > L2 (4.7 GB snapshots rebuilt every step)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": n_solves * world / t_e2e, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches)),
+        "online": {"p50_ms": lat[len(lat) // 2] if lat else None,
+                   "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)] if lat else None,
+                   "requests": len(lat), "converged": ok, "max_iter": args.online_iters},
+        "local_solve": {"seconds": t_kernel, "solves_per_s": n_solves / t_kernel,
+                        "avg_cg_iters": stats.total_iters / max(1, n_solves),
+                        "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "local_solve_global<float>" if prec == "mixed" else "local_solve_global<double>",
+                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+                                    + ("" if prec == "mixed" else " / 64 (FP64 rate)")},
+        "clocks": clk,
+    }
+    if rank == 0:
+        if args.cpu_baseline and world >= 1:
+            line["cpu_baseline"] = oracle_sample(budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--online-iters", type=int, default=1000)
+    ap.add_argument("--online-reqs", type=int, default=5)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--case", default="full", choices=["full", "profile513"],
+                    help="profile513: one pass of the small 513^2 case for profiler captures")
+    args = ap.parse_args()
+    if args.case == "profile513":
+        run_profile_case(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * msp.h -- C ABI of the GB300 random-sampling multiscale solver.
+ *
+ * Method: K. Chen, Q. Li, J. Lu, S. J. Wright, "Random sampling and efficient
+ * algorithms for multiscale PDEs" (arXiv:1807.08848).  The library runs the
+ * data-parallel hot path of Algorithm alg:summary on one GPU:
+ *
+ *   msp_build_medium    domain decomposition of [0,1]^2 into patches K_m with
+ *                       buffered patches K~_m; fine-grid face coefficients
+ *                       a(x, x/eps) (Sec. 5, Eq. Elliptic).
+ *   msp_sample_patches  offline stage, RanLocalSolu: for every patch and every
+ *                       sample, Gaussian data on the ring of K~_m, local solve of
+ *                       div(a grad u) = 0 on K~_m, restriction to K_m
+ *                       (Sec. 3.3, Sec. 5.2, Eq. elliptic_random).
+ *   msp_extract_basis   orthonormal basis of the snapshot range, truncated at
+ *                       sigma_i > tau sigma_1 (Sec. 3.2, Eq. svd; the QR remark
+ *                       of Sec. 3.3), plus the value/flux edge operators and the
+ *                       patch blocks of the least-squares system.
+ *   msp_online_solve    online stage: c = argmin |P c - d| (Eq.
+ *                       elliptic_cond_reduced) by a patch-block (additive
+ *                       Schwarz) preconditioned CGLS iteration, then
+ *                       u = sum_m chi_m G_m c_m with a partition of unity.
+ *   msp_kinetic_*       the slab radiative-transfer example of Sec. 4 with
+ *                       discrete ordinates (Eq. RTE, Eq. rte_random, Eq.
+ *                       rte_cond_reduced).
+ *
+ * Conventions
+ *  - Every call returns an msp_status: MSP_OK (0) or a negative MSP_ERR_* code;
+ *    msp_last_error() returns the message of the calling thread's last error.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream-ordered; a call returns once its work is enqueued unless
+ *    it says it synchronises.
+ *  - Pointers named *_dev are device pointers, *_host host pointers.  Caller
+ *    buffers are borrowed for the duration of the call only.
+ *  - Handles (msp_medium, msp_basis, msp_kmedium, msp_kbasis, msp_server) are
+ *    opaque and own device memory allocated by the library (stream-ordered);
+ *    free them with the matching *_destroy.
+ *  - Fine grid: N cells per side, n = N+1 nodes, h = 1/N, node (i, j) at
+ *    (ih, jh), grids row-major with i fastest.  Face coefficients:
+ *    aE[j][i] = a((i+1/2)h, jh), (N+1) x N;  aN[j][i] = a(ih, (j+1/2)h),
+ *    N x (N+1).  5-point operator
+ *      (A u)_ij = sum over faces f of (i,j) of a_f (u_ij - u_nbr(f)).
+ *  - Ring of a node box [X0,X1]x[Y0,Y1]: counter-clockwise from (X0,Y0),
+ *    every node once (bottom i=X0..X1-1, right j=Y0..Y1-1, top i=X1..X0+1,
+ *    left j=Y1..Y0+1).  The global boundary ring has 4N nodes.
+ *  - No CPU fallback: without a usable CUDA device every compute call fails
+ *    with MSP_ERR_CUDA.
+ */
+#ifndef MSP_H
+#define MSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int msp_status;
+#define MSP_OK                 0
+#define MSP_ERR_INVALID_ARG   -1   /* bad pointer, size or option; nothing was launched   */
+#define MSP_ERR_OOM           -2   /* device allocation failed                             */
+#define MSP_ERR_NOT_CONVERGED -3   /* an iteration hit max_iter; results are the last iterate */
+#define MSP_ERR_BREAKDOWN     -4   /* Cholesky-QR met a non-positive pivot after all shifts */
+#define MSP_ERR_TIMEOUT       -5   /* a bounded wait gave up                               */
+#define MSP_ERR_CUDA          -6   /* a CUDA runtime call failed (message has the CUDA text) */
+#define MSP_ERR_STATE         -7   /* call out of order (e.g. extract before sample)       */
+
+/* Opaque handles. */
+typedef struct msp_medium_s* msp_medium;   /* medium, patches and snapshot storage  */
+typedef struct msp_basis_s* msp_basis;     /* reduced bases and online operators    */
+
+typedef enum { MSP_FP64 = 0, MSP_MIXED = 1 } msp_precision;
+
+typedef enum {
+    MSP_MEDIUM_PERIODIC_SIN = 0,  /* a = 2 + sin(2 pi x/eps) sin(2 pi y/eps)                      */
+    MSP_MEDIUM_LOGNORMAL    = 1,  /* a = exp(amp * norm * sum_q [A cos(2 pi k.x) + B sin(2 pi k.x)]) */
+    MSP_MEDIUM_CHANNELS     = 2,  /* contrast inside strips of width `width`, 1 elsewhere         */
+    MSP_MEDIUM_HOU_WU       = 3,  /* the two-scale medium of the elliptic test, Sec. 5.3          */
+    MSP_MEDIUM_USER         = 4   /* explicit face coefficients                                   */
+} msp_medium_kind;
+
+/* Coefficient field description.  Host pointers; the library copies them. */
+typedef struct {
+    int kind;                 /* msp_medium_kind                                  */
+    int n_cells;              /* N >= 2                                           */
+    double eps;               /* oscillation scale (PERIODIC_SIN, HOU_WU)         */
+    int n_modes;              /* LOGNORMAL: number of rows of `modes`             */
+    const double* modes_host; /* LOGNORMAL: [n_modes][4] = kx, ky, A, B           */
+    double amp, norm;         /* LOGNORMAL: exponent scale and per-mode factor    */
+    int n_channels;           /* CHANNELS: number of rows of `channels`           */
+    const double* channels_host; /* CHANNELS: [n][3] = px, py, theta (line through (px,py) at angle theta) */
+    double width, contrast;   /* CHANNELS                                         */
+    const double* user_aE_host; /* USER: (N+1) x N                               */
+    const double* user_aN_host; /* USER: N x (N+1)                               */
+} msp_medium_desc;
+
+/* Tensor partition into patches, patch m = p + q * nx_patches (p fastest).
+ * Patch (p,q) covers cells [x_breaks[p], x_breaks[p+1]] x [y_breaks[q], y_breaks[q+1]];
+ * its buffered patch extends it by buffers[m] cells on every side, clipped to
+ * the domain.  Every patch draws samples[m] Gaussian samples; patches whose
+ * buffered ring touches the domain boundary also solve one delta datum per
+ * ring node on the domain boundary (the full basis there, as the boundary
+ * patches of Sec. 4.2 do), so patch m has cols_m = samples[m] + n_b(m)
+ * snapshot columns. */
+typedef struct {
+    int nx_patches, ny_patches;
+    const int* x_breaks_host;   /* nx_patches+1, increasing, 0 .. N */
+    const int* y_breaks_host;   /* ny_patches+1, increasing, 0 .. N */
+    const int* buffers_host;    /* per patch, >= 0                  */
+    const int* samples_host;    /* per patch, >= 1                  */
+} msp_patch_desc;
+
+/* Geometry of one patch (closed node boxes). */
+typedef struct {
+    int x0, x1, y0, y1;   /* K_m                          */
+    int X0, X1, Y0, Y1;   /* K~_m (buffered, clipped)     */
+    int n_k;              /* (x1-x0+1)(y1-y0+1) nodes of K_m */
+    int n_ring;           /* ring nodes of K~_m           */
+    int samples;          /* Gaussian columns             */
+    int n_b;              /* delta columns (ring nodes on the domain boundary) */
+    int cols;             /* samples + n_b                */
+    int64_t snap_offset;  /* first element of this patch's snapshot block */
+} msp_patch_info;
+
+/* Iteration statistics of a batch of local solves. */
+typedef struct {
+    int64_t n_solves;
+    int64_t total_iters;      /* sum over solves of inner (PCG) iterations   */
+    int max_iters;            /* largest inner iteration count of one solve  */
+    int max_refinements;      /* largest number of FP64 refinement steps     */
+    int n_not_converged;      /* solves that stopped at max_iter              */
+    int64_t unknown_iters;    /* sum over solves of (CG iterations x interior unknowns) */
+} msp_solve_stats;
+
+/* Last error message of the calling thread ("" if none). */
+const char* msp_last_error(void);
+
+/* Library version string. */
+const char* msp_version(void);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all threads, all devices); for launch accounting in benchmarks. */
+int64_t msp_kernel_launches(void);
+
+/* --------------------------------------------------------------------- medium */
+
+/* Build the patch tables and evaluate the face coefficients on the device
+ * (Sec. 5: a(x, x/eps) on the fine mesh).  Allocates the snapshot storage
+ * (sum over patches of n_k * cols_m doubles).  INVALID_ARG on malformed
+ * descriptions (breaks not covering [0,N], non-positive sizes, NULL tables). */
+msp_status msp_build_medium(const msp_medium_desc* medium, const msp_patch_desc* patches,
+                            void* stream, msp_medium* out);
+void msp_medium_destroy(msp_medium m);
+
+/* Counts: patches, total snapshot elements, N. */
+msp_status msp_medium_counts(msp_medium m, int* n_patches, int64_t* snapshot_elems, int* n_cells);
+msp_status msp_medium_patch(msp_medium m, int patch, msp_patch_info* out);
+
+/* Copy the FP64 face coefficients to device buffers of (N+1)*N (aE) and
+ * N*(N+1) (aN) doubles. */
+msp_status msp_get_coefficients(msp_medium m, double* aE_dev, double* aN_dev, void* stream);
+
+/* --------------------------------------------------------------------- offline */
+
+/* RanLocalSolu on every patch (Algorithm alg:summary; Eq. elliptic_random):
+ * for each patch m and column s < cols_m, ring data of K~_m -- i.i.d. N(0,1)
+ * from Philox4x32-10 (key = seed, counter = (node pair, s, m, tag)) with
+ * Box-Muller for s < samples[m], a unit delta at the (s - samples[m])-th ring
+ * node on the domain boundary otherwise -- then the local solve on K~_m by
+ * Jacobi-preconditioned CG and the restriction to K_m, stored as the patch's
+ * snapshot block (n_k x cols_m, column-major).
+ *   precision MSP_FP64: CG in FP64 to |r| <= tol |b|.
+ *   precision MSP_MIXED: CG in FP32 inside FP64 iterative refinement (FP64
+ *     residual r = b - A x, FP32 correction), to |r| <= tol |b|.
+ * max_iter bounds the CG iterations of each inner solve.  If stats_host is
+ * not NULL the call synchronises the stream and fills it; it then returns
+ * MSP_ERR_NOT_CONVERGED if any solve stopped at max_iter. */
+msp_status msp_sample_patches(msp_medium m, uint64_t seed, int precision, double tol, int max_iter,
+                              void* stream, msp_solve_stats* stats_host);
+
+/* Copy patch `patch`'s snapshot block (n_k x cols, column-major) to dst_dev. */
+msp_status msp_get_snapshots(msp_medium m, int patch, double* dst_dev, void* stream);
+
+/* Ring data of patch `patch` as the sampler draws it, (n_ring x cols)
+ * column-major, to dst_dev (for checking the generator). */
+msp_status msp_get_samples(msp_medium m, int patch, uint64_t seed, double* dst_dev, void* stream);
+
+/* Orthonormal basis of every patch's snapshot range (Sec. 3.2, Eq. svd):
+ * shifted Cholesky-QR3 of the snapshot block, SVD of its triangular factor by
+ * one-sided Jacobi, truncation k_m = #{sigma_i > tau sigma_1}; basis
+ * Q_m = left singular vectors 1..k_m (n_k x k_m).  Then the edge operators
+ * (value and flux rows on the ring of K_m, Eq. elliptic_cond_tilde), the row
+ * tables of P~ and the Cholesky factors of the patch blocks of P~^T P~.
+ * Synchronises the stream (the k_m decide the online layout).
+ * BREAKDOWN if a Cholesky factorisation fails after its shift retries. */
+msp_status msp_extract_basis(msp_medium m, double tau, int precision, void* stream, msp_basis* out);
+void msp_basis_destroy(msp_basis b);
+
+/* Number of kept vectors k_m and (if sigma_host != NULL, length cols_m) all
+ * singular values of patch `patch`'s snapshot block, descending. */
+msp_status msp_basis_info(msp_basis b, int patch, int* k, double* sigma_host);
+/* Copy Q_m (n_k x k_m, column-major) to dst_dev. */
+msp_status msp_get_basis(msp_basis b, int patch, double* dst_dev, void* stream);
+/* Total unknowns N_p = sum k_m and rows of P~. */
+msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_rows);
+
+/* --------------------------------------------------------------------- online */
+
+/* Online stage for `batch` Dirichlet data sets (Eq. elliptic_cond_reduced):
+ *   phi_dev: [batch][4N] values on the global boundary ring;
+ *   u_dev:   [batch][N+1][N+1] reconstructed fields (output);
+ *   c_dev:   optional [batch][N_p] coefficients (output) or NULL.
+ * CGLS on the normal equations with the patch-block preconditioner
+ * (P~^T P~)_mm^{-1}, stopped per data set at |P~^T r| <= tol |P~^T d| or
+ * max_iter; every data set's iteration is independent of the others in the
+ * batch (fixed-order reductions).  iters_host (optional, [batch]) receives the
+ * iteration counts and makes the call synchronise; NOT_CONVERGED if any data
+ * set hit max_iter. */
+msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
+                            double* u_dev, double* c_dev, int* iters_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSP_H */

@@ -1,0 +1,208 @@
+"""GB300 random-sampling multiscale solver (arXiv:1807.08848) -- Python binding.
+
+Thin wrapper over the C ABI of libmsp.so (include/msp.h).  PyTorch supplies
+device memory and streams; every step of the method runs in the library's
+CUDA kernels.  There is no CPU fallback: without the built library or a CUDA
+device the calls raise.
+
+    med = Medium(medium_spec, patch_spec)          # msp_build_medium
+    stats = med.sample(seed, "mixed", 1e-10)       # msp_sample_patches
+    basis = med.extract(1e-6)                      # msp_extract_basis
+    u, iters = basis.solve(phi)                    # msp_online_solve
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import MspError, MSP_FP64, MSP_MIXED
+
+__all__ = ["Medium", "Basis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library", "precision_code"]
+
+
+def load_library():
+    return N.load()
+
+
+def precision_code(p) -> int:
+    if isinstance(p, int):
+        return p
+    return {"fp64": MSP_FP64, "mixed": MSP_MIXED}[str(p).lower()]
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _f64p(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i32p(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Medium:
+    """Medium, patch decomposition and snapshot storage on the device.
+
+    medium: object with kind, n_cells, eps, modes, amp, norm, channels, width,
+            contrast, user_aE, user_aN (e.g. synth.MediumSpec).
+    patches: object with x_breaks, y_breaks, buffers, samples (e.g. synth.PatchSpec).
+    """
+
+    def __init__(self, medium, patches, stream=None):
+        lib = N.load()
+        self._keep = []
+        d = N.MediumDesc()
+        d.kind = int(medium.kind)
+        d.n_cells = int(medium.n_cells)
+        d.eps = float(medium.eps)
+        modes = np.ascontiguousarray(np.asarray(medium.modes, dtype=np.float64).reshape(-1, 4))
+        chans = np.ascontiguousarray(np.asarray(medium.channels, dtype=np.float64).reshape(-1, 3))
+        self._keep += [modes, chans]
+        d.n_modes = modes.shape[0]
+        d.modes_host = _f64p(modes)
+        d.amp = float(medium.amp)
+        d.norm = float(medium.norm)
+        d.n_channels = chans.shape[0]
+        d.channels_host = _f64p(chans)
+        d.width = float(medium.width)
+        d.contrast = float(medium.contrast)
+        if medium.user_aE is not None:
+            aE = np.ascontiguousarray(medium.user_aE, dtype=np.float64)
+            aN = np.ascontiguousarray(medium.user_aN, dtype=np.float64)
+            self._keep += [aE, aN]
+            d.user_aE_host = _f64p(aE)
+            d.user_aN_host = _f64p(aN)
+        xb = np.ascontiguousarray(patches.x_breaks, dtype=np.int32)
+        yb = np.ascontiguousarray(patches.y_breaks, dtype=np.int32)
+        bu = np.ascontiguousarray(patches.buffers, dtype=np.int32)
+        sa = np.ascontiguousarray(patches.samples, dtype=np.int32)
+        self._keep += [xb, yb, bu, sa]
+        p = N.PatchDesc(len(xb) - 1, len(yb) - 1, _i32p(xb), _i32p(yb), _i32p(bu), _i32p(sa))
+        h = C.c_void_p()
+        N.check(lib.msp_build_medium(C.byref(d), C.byref(p), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        self._keep = []
+        npch, ne, nc = C.c_int(), C.c_int64(), C.c_int()
+        N.check(lib.msp_medium_counts(h, C.byref(npch), C.byref(ne), C.byref(nc)))
+        self.n_patches, self.snapshot_elems, self.n_cells = npch.value, ne.value, nc.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            N.load().msp_medium_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def patch(self, m: int) -> N.PatchInfo:
+        info = N.PatchInfo()
+        N.check(N.load().msp_medium_patch(self._h, m, C.byref(info)))
+        return info
+
+    def coefficients(self, stream=None):
+        n = self.n_cells
+        aE = torch.empty((n + 1, n), dtype=torch.float64, device="cuda")
+        aN = torch.empty((n, n + 1), dtype=torch.float64, device="cuda")
+        N.check(N.load().msp_get_coefficients(self._h, _dptr(aE), _dptr(aN), _stream_ptr(stream)))
+        return aE, aN
+
+    def sample(self, seed: int, precision="fp64", tol: float = 1e-12, max_iter: int = 20000, stream=None,
+               stats: bool = True):
+        st = N.SolveStats()
+        code = N.load().msp_sample_patches(self._h, C.c_uint64(seed), precision_code(precision), tol, max_iter,
+                                           _stream_ptr(stream), C.byref(st) if stats else None)
+        N.check(code)
+        return st if stats else None
+
+    def snapshots(self, m: int, stream=None) -> torch.Tensor:
+        """Snapshot block of patch m as an (n_k, cols) tensor (column-major storage)."""
+        info = self.patch(m)
+        t = torch.empty((info.cols, info.n_k), dtype=torch.float64, device="cuda")
+        N.check(N.load().msp_get_snapshots(self._h, m, _dptr(t), _stream_ptr(stream)))
+        return t.T
+
+    def samples(self, m: int, seed: int, stream=None) -> torch.Tensor:
+        """Ring data of patch m, (n_ring, cols)."""
+        info = self.patch(m)
+        t = torch.empty((info.cols, info.n_ring), dtype=torch.float64, device="cuda")
+        N.check(N.load().msp_get_samples(self._h, m, C.c_uint64(seed), _dptr(t), _stream_ptr(stream)))
+        return t.T
+
+    def extract(self, tau: float = 1e-6, precision="fp64", stream=None) -> "Basis":
+        h = C.c_void_p()
+        N.check(N.load().msp_extract_basis(self._h, tau, precision_code(precision), _stream_ptr(stream), C.byref(h)))
+        return Basis(h, self)
+
+
+class Basis:
+    """Reduced bases Q_m and the online operators of one medium."""
+
+    def __init__(self, handle, medium: Medium):
+        self._h = handle
+        self.n_cells = medium.n_cells
+        self.n_patches = medium.n_patches
+        self._cols = [medium.patch(m).cols for m in range(medium.n_patches)]
+        self._nk = [medium.patch(m).n_k for m in range(medium.n_patches)]
+        nu, nr = C.c_int(), C.c_int()
+        N.check(N.load().msp_online_counts(handle, C.byref(nu), C.byref(nr)))
+        self.n_unknowns, self.n_rows = nu.value, nr.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            N.load().msp_basis_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def k(self, m: int) -> int:
+        k = C.c_int()
+        N.check(N.load().msp_basis_info(self._h, m, C.byref(k), None))
+        return k.value
+
+    def sigma(self, m: int) -> np.ndarray:
+        out = np.zeros(self._cols[m])
+        k = C.c_int()
+        N.check(N.load().msp_basis_info(self._h, m, C.byref(k), _f64p(out)))
+        return out
+
+    def Q(self, m: int, stream=None) -> torch.Tensor:
+        k = self.k(m)
+        t = torch.empty((k, self._nk[m]), dtype=torch.float64, device="cuda")
+        if k:
+            N.check(N.load().msp_get_basis(self._h, m, _dptr(t), _stream_ptr(stream)))
+        return t.T
+
+    def solve(self, phi: torch.Tensor, tol: float = 1e-10, max_iter: int = 5000, stream=None,
+              want_c: bool = False, want_iters: bool = True, u: torch.Tensor | None = None):
+        """Online solve for phi of shape (B, 4N) (or (4N,)) on the device."""
+        squeeze = phi.dim() == 1
+        phi = phi.reshape(-1, 4 * self.n_cells).to(dtype=torch.float64, device="cuda").contiguous()
+        B = phi.shape[0]
+        n = self.n_cells + 1
+        if u is None:
+            u = torch.empty((B, n, n), dtype=torch.float64, device="cuda")
+        c = torch.empty((B, self.n_unknowns), dtype=torch.float64, device="cuda") if want_c else None
+        iters = (C.c_int * B)() if want_iters else None
+        code = N.load().msp_online_solve(self._h, _dptr(phi), B, tol, max_iter, _dptr(u),
+                                         _dptr(c) if c is not None else None, iters, _stream_ptr(stream))
+        N.check(code)
+        it = np.array(list(iters), dtype=np.int64) if want_iters else None
+        if squeeze:
+            u = u[0]
+            c = c[0] if c is not None else None
+        return (u, it, c) if want_c else (u, it)

@@ -1,0 +1,68 @@
+// C ABI: basis extraction and the online solve.
+#include "internal.h"
+
+
+using namespace msp;
+
+extern "C" msp_status msp_extract_basis(msp_medium m, double tau, int precision, void* stream, msp_basis* out) {
+    clear_error();
+    MSP_CHECK_ARG(m && out, "msp_extract_basis: NULL argument");
+    MSP_CHECK_ARG(tau >= 0 && tau < 1, "msp_extract_basis: tau must lie in [0, 1)");
+    MSP_CHECK_ARG(precision == MSP_FP64 || precision == MSP_MIXED, "msp_extract_basis: unknown precision");
+    *out = nullptr;
+    if (!m->M.sampled) {
+        set_error("msp_extract_basis: call msp_sample_patches first");
+        return MSP_ERR_STATE;
+    }
+    auto* b = new msp_basis_s();
+    msp_status st = build_basis(m->M, tau, precision, (cudaStream_t)stream, b->B);
+    if (st != MSP_OK) {
+        delete b;
+        return st;
+    }
+    *out = b;
+    return MSP_OK;
+}
+
+extern "C" void msp_basis_destroy(msp_basis b) { delete b; }
+
+extern "C" msp_status msp_basis_info(msp_basis b, int patch, int* k, double* sigma_host) {
+    clear_error();
+    MSP_CHECK_ARG(b, "msp_basis_info: NULL basis");
+    MSP_CHECK_ARG(patch >= 0 && patch < (int)b->B.patches.size(), "msp_basis_info: patch out of range");
+    if (k) *k = b->B.k[patch];
+    if (sigma_host) {
+        const int c = b->B.patches[patch].cols;
+        for (int i = 0; i < c; ++i) sigma_host[i] = b->B.sigma[b->B.sigma_off[patch] + i];
+    }
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_get_basis(msp_basis b, int patch, double* dst, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(b && dst, "msp_get_basis: NULL argument");
+    MSP_CHECK_ARG(patch >= 0 && patch < (int)b->B.patches.size(), "msp_get_basis: patch out of range");
+    const size_t n = (size_t)b->B.patches[patch].n_k * b->B.k[patch];
+    if (n) MSP_CUDA(cudaMemcpyAsync(dst, b->B.Q.p + b->B.q_off[patch], n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream));
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_rows) {
+    clear_error();
+    MSP_CHECK_ARG(b, "msp_online_counts: NULL basis");
+    if (n_unknowns) *n_unknowns = b->B.Np;
+    if (n_rows) *n_rows = b->B.n_rows;
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_online_solve(msp_basis b, const double* phi, int batch, double tol, int max_iter, double* u,
+                                       double* c_dev, int* iters_host, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(b && phi && u, "msp_online_solve: NULL argument");
+    MSP_CHECK_ARG(batch >= 0, "msp_online_solve: negative batch");
+    MSP_CHECK_ARG(tol > 0 && tol < 1, "msp_online_solve: tol must lie in (0, 1)");
+    MSP_CHECK_ARG(max_iter >= 1, "msp_online_solve: max_iter must be >= 1");
+    if (batch == 0) return MSP_OK;
+    return online_solve(b->B, phi, batch, tol, max_iter, u, c_dev, iters_host, (cudaStream_t)stream);
+}

@@ -1,0 +1,576 @@
+// Basis extraction (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) and the
+// online operators built from it (Eq. elliptic_cond_tilde).
+//
+// Per patch, with R_m the n_k x c snapshot block:
+//   shifted Cholesky-QR3  R = Q3 T   (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+//                                     Yanagisawa, SIAM J. Sci. Comput. 2020)
+//   one-sided Jacobi SVD of T^T     T = U_T S V_T^T   (Hestenes' method)
+//   truncation                       k = #{s_i > tau s_1},  Q_m = Q3 U_T[:, :k]
+// then the value/flux rows of Q_m on the ring of K_m and the inverse of every
+// patch block of P~^T P~ (the additive-Schwarz preconditioner of the online
+// iteration).
+#include "internal.h"
+#include "dense.cuh"
+#include "device_util.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <utility>
+
+namespace msp {
+
+namespace {
+
+struct SmallMat {
+    long long off;   // offset of this patch's c x c block
+    int c;           // order
+    int n;           // rows of the tall matrix
+};
+
+// Cholesky of (G + shift I) = L L^T in global memory (one CTA per matrix),
+// then F = L^T and Fi = L^{-T} (upper triangular), column-major order c.
+// shift0 > 0 requests a shifted factorisation; on a non-positive pivot the
+// shift grows (to 1e-14 trace if it was zero, else x100) up to 6 tries.
+// status[b]: number of tries used, or -1 on failure.
+__global__ void __launch_bounds__(256) chol_factor_kernel(const SmallMat* mats, const double* G, double* L,
+                                                          double* F, double* Fi, const double* shift_scale,
+                                                          int shifted, int* status) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    if (c <= 0) return;
+    const double* g = G + S.off;
+    double* l = L + S.off;
+    double* f = F + S.off;
+    double* fi = Fi + S.off;
+    __shared__ double s_trace;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < c; ++i) t += g[i + (long long)i * c];
+        s_trace = t;
+    }
+    __syncthreads();
+    const double trace = s_trace;
+    double shift = 0.0;
+    if (shifted) shift = shift_scale[blockIdx.x] * trace;
+    int tries = 0;
+    bool ok = false;
+    for (; tries < 6 && !ok; ++tries) {
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            l[e] = (i >= j) ? g[e] + (i == j ? shift : 0.0) : 0.0;
+        }
+        __syncthreads();
+        ok = true;
+        for (int k = 0; k < c; ++k) {
+            if (threadIdx.x == 0) {
+                const double d = l[k + (long long)k * c];
+                s_ok = (d > 0.0 && isfinite(d)) ? 1 : 0;
+                if (s_ok) l[k + (long long)k * c] = sqrt(d);
+            }
+            __syncthreads();
+            if (!s_ok) { ok = false; break; }
+            const double piv = l[k + (long long)k * c];
+            for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) l[i + (long long)k * c] /= piv;
+            __syncthreads();
+            const int R = c - k - 1;
+            for (long long e = threadIdx.x; e < (long long)R * R; e += blockDim.x) {
+                const int i = k + 1 + (int)(e % R), j = k + 1 + (int)(e / R);
+                if (i >= j) l[i + (long long)j * c] -= l[i + (long long)k * c] * l[j + (long long)k * c];
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!ok) shift = (shift == 0.0) ? 1e-14 * trace : shift * 100.0;
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) status[blockIdx.x] = -1;
+        return;
+    }
+    if (threadIdx.x == 0) status[blockIdx.x] = tries;
+    // F = L^T
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        f[e] = (i <= j) ? l[j + (long long)i * c] : 0.0;
+    }
+    // Fi = (L^{-1})^T: thread j forward-substitutes column j of L^{-1},
+    // X(i, j) stored at Fi(j, i) = fi[j + i c]
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        for (int i = 0; i < j; ++i) fi[j + (long long)i * c] = 0.0;
+        for (int i = j; i < c; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int q = j; q < i; ++q) s -= l[i + (long long)q * c] * fi[j + (long long)q * c];
+            fi[j + (long long)i * c] = s / l[i + (long long)i * c];
+        }
+    }
+}
+
+// W = T^T, V = I (per patch, order c).
+__global__ void jacobi_init_kernel(const SmallMat* mats, const double* T, double* W, double* V) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        W[S.off + e] = T[S.off + j + (long long)i * c];
+        V[S.off + e] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+// One-sided (Hestenes) Jacobi on W (c x c): rotate column pairs (p, q) until
+// every pair is orthogonal to relative level tol; V accumulates the rotations.
+// Pairs follow the round-robin tournament order (c/2 disjoint pairs per step,
+// one warp per pair).  Afterwards W = U S and T^T = U S V^T, so V holds the
+// left singular vectors of T.
+__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, double* W, double* V, int max_sweeps,
+                                                         int* sweeps_out) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    if (c <= 1) {
+        if (threadIdx.x == 0) sweeps_out[blockIdx.x] = 0;
+        return;
+    }
+    double* w = W + S.off;
+    double* v = V + S.off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int np = c + (c & 1);   // players, even
+    const double tol = fmax(1e-15, 2.2e-16 * c);
+    __shared__ int s_rot;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) s_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < np - 1; ++r) {
+            for (int pr = warp; pr < np / 2; pr += nw) {
+                int a, b;
+                if (pr == 0) { a = r; b = np - 1; }
+                else { a = (r + pr) % (np - 1); b = (r - pr + (np - 1)) % (np - 1); }
+                if (a >= c || b >= c) continue;
+                const int p = min(a, b), q = max(a, b);
+                double* wp = w + (long long)p * c;
+                double* wq = w + (long long)q * c;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < c; i += 32) {
+                    const double x = wp[i], y = wq[i];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (al == 0.0 || be == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                for (int i = lane; i < c; i += 32) {
+                    const double x = wp[i], y = wq[i];
+                    wp[i] = cs * x - sn * y;
+                    wq[i] = sn * x + cs * y;
+                }
+                double* vp = v + (long long)p * c;
+                double* vq = v + (long long)q * c;
+                for (int i = lane; i < c; i += 32) {
+                    const double x = vp[i], y = vq[i];
+                    vp[i] = cs * x - sn * y;
+                    vq[i] = sn * x + cs * y;
+                }
+                if (lane == 0) atomicAdd(&s_rot, 1);
+            }
+            __syncthreads();
+        }
+        if (s_rot == 0) break;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sweeps_out[blockIdx.x] = sweep;
+}
+
+// Column norms of W = singular values; sort descending (rank by comparison);
+// keep k = #{s_i > tau s_1}.  Writes sigma (sorted), order, k.
+__global__ void sort_truncate_kernel(const SmallMat* mats, const double* W, double tau, double* sig_tmp,
+                                     double* sigma, const long long* sig_off, int* order, int* k_out) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    double* st = sig_tmp + sig_off[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < c; i += nw) {
+        const double* col = W + S.off + (long long)i * c;
+        double a = 0.0;
+        for (int r = lane; r < c; r += 32) a += col[r] * col[r];
+        a = warp_sum(a);
+        if (lane == 0) st[i] = sqrt(a);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < c; i += blockDim.x) {
+        const double si = st[i];
+        int rank = 0;
+        for (int j = 0; j < c; ++j) {
+            const double sj = st[j];
+            rank += (sj > si) || (sj == si && j < i);
+        }
+        sigma[sig_off[blockIdx.x] + rank] = si;
+        order[sig_off[blockIdx.x] + rank] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double s1 = sigma[sig_off[blockIdx.x]];
+        int k = 0;
+        for (int i = 0; i < c; ++i) k += (sigma[sig_off[blockIdx.x] + i] > tau * s1) ? 1 : 0;
+        if (s1 == 0.0) k = 0;
+        k_out[blockIdx.x] = k;
+    }
+}
+
+// Uk = V[:, order[0..k)] (c x k, ld c).
+__global__ void gather_uk_kernel(const SmallMat* mats, const double* V, const int* order, const long long* sig_off,
+                                 const int* k, double* Uk) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c, kk = k[blockIdx.x];
+    for (long long e = threadIdx.x; e < (long long)c * kk; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        Uk[S.off + e] = V[S.off + i + (long long)order[sig_off[blockIdx.x] + j] * c];
+    }
+}
+
+__global__ void copy_kernel(const double* src, double* dst, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        dst[t] = src[t];
+}
+
+// Edge operators of patch m: for every ring node t of K_m, value row
+// E[2t] = Q_m[node] and flux row E[2t+1] = (1/h) sum over faces f at the node
+// inside the closed K_m of (a_f / nu_f)(Q_m[node] - Q_m[nbr_f]), nu_f = 2 on a
+// face lying on a patch break (held by two patches), else 1.
+__global__ void edge_ops_kernel(int N, const double* aE, const double* aN, const PatchDev* patches, const int* kk,
+                                const long long* q_off, const long long* e_off, const double* Q, double* E,
+                                const unsigned char* xbreak, const unsigned char* ybreak) {
+    const int m = blockIdx.x;
+    const PatchDev P = patches[m];
+    const int k = kk[m];
+    const int ne = 2 * (P.x1 - P.x0) + 2 * (P.y1 - P.y0);
+    const int wk = P.x1 - P.x0 + 1;
+    const double* q = Q + q_off[m];
+    double* e = E + e_off[m];
+    const double invh = (double)N;
+    for (long long w = threadIdx.x; w < (long long)ne * k; w += blockDim.x) {
+        const int t = (int)(w / k), col = (int)(w % k);
+        int i, j;
+        ring_node(P.x0, P.x1, P.y0, P.y1, t, i, j);
+        const double* qc = q + (long long)col * P.n_k;
+        const int loc = (i - P.x0) + (j - P.y0) * wk;
+        const double u0 = qc[loc];
+        double fl = 0.0;
+        const double nuh = ybreak[j] ? 0.5 : 1.0;   // x-faces lie on row j
+        const double nuv = xbreak[i] ? 0.5 : 1.0;   // y-faces lie on column i
+        if (i + 1 <= P.x1) fl += aE[(long long)j * N + i] * nuh * (u0 - qc[loc + 1]);
+        if (i - 1 >= P.x0) fl += aE[(long long)j * N + i - 1] * nuh * (u0 - qc[loc - 1]);
+        if (j + 1 <= P.y1) fl += aN[(long long)j * (N + 1) + i] * nuv * (u0 - qc[loc + wk]);
+        if (j - 1 >= P.y0) fl += aN[(long long)(j - 1) * (N + 1) + i] * nuv * (u0 - qc[loc - wk]);
+        e[(long long)(2 * t) * k + col] = u0;
+        e[(long long)(2 * t + 1) * k + col] = invh * fl;
+    }
+}
+
+// Patch block of the normal equations: B_m = sum_s cnt_s E[s]^T E[s] (k x k).
+__global__ void precond_block_kernel(const int* kk, const int* ne, const long long* e_off, const double* E,
+                                     const int* slot_off, const int* tr_ptr, const SmallMat* mats, double* Bm) {
+    const int m = blockIdx.x;
+    const int k = kk[m], ns = 2 * ne[m];
+    const double* e = E + e_off[m];
+    for (long long w = threadIdx.x; w < (long long)k * k; w += blockDim.x) {
+        const int i = (int)(w % k), j = (int)(w / k);
+        double a = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            const int g = slot_off[m] + s;
+            const int cnt = tr_ptr[g + 1] - tr_ptr[g];
+            if (cnt) a += cnt * e[(long long)s * k + i] * e[(long long)s * k + j];
+        }
+        Bm[mats[m].off + w] = a;
+    }
+}
+
+// Binv = Fi Fi^T (Fi = L^{-T}, so Binv = (L L^T)^{-1}); stored at binv_off.
+__global__ void precond_inverse_kernel(const SmallMat* mats, const double* Fi, const long long* binv_off,
+                                       double* Binv) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    const double* f = Fi + S.off;
+    for (long long w = threadIdx.x; w < (long long)c * c; w += blockDim.x) {
+        const int i = (int)(w % c), j = (int)(w / c);
+        double a = 0.0;
+        for (int l = max(i, j); l < c; ++l) a += f[i + (long long)l * c] * f[j + (long long)l * c];
+        Binv[binv_off[blockIdx.x] + w] = a;
+    }
+}
+
+template <class T>
+msp_status upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+    MSP_TRY(d.alloc(std::max<size_t>(1, h.size()), s));
+    if (!h.empty()) MSP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+    return MSP_OK;
+}
+
+int domain_ring_pos(int N, int i, int j) {
+    if (j == 0 && i < N) return i;
+    if (i == N && j < N) return N + j;
+    if (j == N && i > 0) return 2 * N + (N - i);
+    return 3 * N + (N - j);
+}
+
+}  // namespace
+
+msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B) {
+    (void)precision;
+    const int np = (int)M.patches.size();
+    B.N = M.N; B.mx = M.mx; B.my = M.my; B.xb = M.xb; B.yb = M.yb; B.patches = M.patches;
+    B.device = M.device;
+    // ---- small-matrix layout
+    std::vector<SmallMat> mats(np);
+    std::vector<long long> sig_off(np);
+    long long mo = 0, so = 0;
+    int maxc = 0, maxn = 0;
+    for (int m = 0; m < np; ++m) {
+        const PatchDev& P = M.patches[m];
+        mats[m] = SmallMat{mo, P.cols, P.n_k};
+        mo += (long long)P.cols * P.cols;
+        sig_off[m] = so;
+        so += P.cols;
+        maxc = std::max(maxc, P.cols);
+        maxn = std::max(maxn, P.n_k);
+    }
+    DevBuf<SmallMat> d_mats;
+    DevBuf<long long> d_sig_off;
+    MSP_TRY(upload(d_mats, mats, s));
+    MSP_TRY(upload(d_sig_off, sig_off, s));
+    DevBuf<double> G, L, F, Fi, T0, T1, W, V, ping, pong, sig_tmp, sig;
+    DevBuf<int> order, kdev, status, sweeps;
+    DevBuf<double> shift_scale;
+    MSP_TRY(G.alloc(mo, s)); MSP_TRY(L.alloc(mo, s)); MSP_TRY(F.alloc(mo, s)); MSP_TRY(Fi.alloc(mo, s));
+    MSP_TRY(T0.alloc(mo, s)); MSP_TRY(T1.alloc(mo, s));
+    MSP_TRY(ping.alloc(M.snap_elems, s)); MSP_TRY(pong.alloc(M.snap_elems, s));
+    MSP_TRY(sig_tmp.alloc(so, s)); MSP_TRY(sig.alloc(so, s));
+    MSP_TRY(order.alloc(so, s)); MSP_TRY(kdev.alloc(np, s)); MSP_TRY(status.alloc(np, s)); MSP_TRY(sweeps.alloc(np, s));
+    {
+        // shift of the first pass: 11 (n c + c (c+1)) u, times |R|_F^2 (= trace of the Gram)
+        std::vector<double> sc(np);
+        for (int m = 0; m < np; ++m) {
+            const double c = mats[m].c, n = mats[m].n;
+            sc[m] = 11.0 * (n * c + c * (c + 1.0)) * 1.1102230246251565e-16;
+        }
+        MSP_TRY(upload(shift_scale, sc, s));
+    }
+    std::vector<GemmDesc> gd(np);
+    DevBuf<GemmDesc> d_gd;
+    MSP_TRY(d_gd.alloc(np, s));
+    auto run_gemm = [&](bool transA, int max_m, int max_n) -> msp_status {
+        MSP_CUDA(cudaMemcpyAsync(d_gd.p, gd.data(), sizeof(GemmDesc) * np, cudaMemcpyHostToDevice, s));
+        gemm_batched(d_gd.p, np, max_m, max_n, transA, s);
+        MSP_CUDA(cudaGetLastError());
+        MSP_CUDA(cudaStreamSynchronize(s));   // descriptors are reused
+        return MSP_OK;
+    };
+    const double* X = M.snaps.p;
+    double* Tacc = T0.p;
+    double* Tnew = T1.p;
+    double* outs[3] = {ping.p, pong.p, ping.p};
+    std::vector<int> hstat(np);
+    for (int pass = 0; pass < 3; ++pass) {
+        double* Y = outs[pass];
+        // Gram G = X^T X
+        for (int m = 0; m < np; ++m) {
+            const long long so_ = M.patches[m].snap_offset;
+            gd[m] = GemmDesc{X + so_, X + so_, G.p + mats[m].off, mats[m].c, mats[m].c, mats[m].n,
+                             mats[m].n, mats[m].n, mats[m].c};
+        }
+        MSP_TRY(run_gemm(true, maxc, maxc));
+        chol_factor_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p, L.p, F.p, Fi.p, shift_scale.p, pass == 0, status.p);
+        count_launches(1);
+        MSP_CUDA(cudaGetLastError());
+        MSP_CUDA(cudaMemcpyAsync(hstat.data(), status.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        for (int m = 0; m < np; ++m)
+            if (hstat[m] < 0) {
+                set_error("msp_extract_basis: Cholesky-QR breakdown on patch " + std::to_string(m) + " (pass " +
+                          std::to_string(pass) + ")");
+                return MSP_ERR_BREAKDOWN;
+            }
+        // Y = X Fi
+        for (int m = 0; m < np; ++m) {
+            const long long so_ = M.patches[m].snap_offset;
+            gd[m] = GemmDesc{X + so_, Fi.p + mats[m].off, Y + so_, mats[m].n, mats[m].c, mats[m].c,
+                             mats[m].n, mats[m].c, mats[m].n};
+        }
+        MSP_TRY(run_gemm(false, maxn, maxc));
+        // T accumulation: Tacc <- F Tacc
+        if (pass == 0) {
+            copy_kernel<<<1024, 256, 0, s>>>(F.p, Tacc, mo);
+            count_launches(1);
+            MSP_CUDA(cudaGetLastError());
+        } else {
+            for (int m = 0; m < np; ++m)
+                gd[m] = GemmDesc{F.p + mats[m].off, Tacc + mats[m].off, Tnew + mats[m].off, mats[m].c, mats[m].c,
+                                 mats[m].c, mats[m].c, mats[m].c, mats[m].c};
+            MSP_TRY(run_gemm(false, maxc, maxc));
+            std::swap(Tacc, Tnew);
+        }
+        X = Y;
+    }
+    // ---- SVD of the triangular factor
+    MSP_TRY(W.alloc(mo, s));
+    MSP_TRY(V.alloc(mo, s));
+    jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
+    count_launches(1);
+    jacobi_svd_kernel<<<np, 512, 0, s>>>(d_mats.p, W.p, V.p, 60, sweeps.p);
+    count_launches(1);
+    sort_truncate_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, tau, sig_tmp.p, sig.p, d_sig_off.p, order.p, kdev.p);
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    B.k.resize(np);
+    B.sigma.resize(so);
+    B.sigma_off = sig_off;
+    MSP_CUDA(cudaMemcpyAsync(B.k.data(), kdev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaMemcpyAsync(B.sigma.data(), sig.p, sizeof(double) * so, cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    // ---- Q_m = Q3 U_T[:, :k]
+    B.q_off.resize(np);
+    B.c_off.resize(np + 1);
+    long long qo = 0;
+    int co = 0, maxk = 0;
+    for (int m = 0; m < np; ++m) {
+        B.q_off[m] = qo;
+        qo += (long long)M.patches[m].n_k * B.k[m];
+        B.c_off[m] = co;
+        co += B.k[m];
+        maxk = std::max(maxk, B.k[m]);
+    }
+    B.c_off[np] = co;
+    B.Np = co;
+    MSP_TRY(B.Q.alloc(std::max<long long>(qo, 1), s));
+    gather_uk_kernel<<<np, 256, 0, s>>>(d_mats.p, V.p, order.p, d_sig_off.p, kdev.p, G.p);   // Uk into G
+    MSP_CUDA(cudaGetLastError());
+    count_launches(1);
+    for (int m = 0; m < np; ++m) {
+        const long long so_ = M.patches[m].snap_offset;
+        gd[m] = GemmDesc{X + so_, G.p + mats[m].off, B.Q.p + B.q_off[m], mats[m].n, B.k[m], mats[m].c,
+                         mats[m].n, mats[m].c, mats[m].n};
+    }
+    MSP_TRY(run_gemm(false, maxn, std::max(maxk, 1)));
+
+    // ---- online tables (host): skeleton nodes, rows of P~, transpose lists
+    const int N = M.N;
+    B.n_e.resize(np);
+    B.slot_off.resize(np + 1);
+    B.e_off.resize(np);
+    int slots = 0;
+    long long eo = 0;
+    for (int m = 0; m < np; ++m) {
+        const PatchDev& P = M.patches[m];
+        B.n_e[m] = 2 * (P.x1 - P.x0) + 2 * (P.y1 - P.y0);
+        B.slot_off[m] = slots;
+        slots += 2 * B.n_e[m];
+        B.e_off[m] = eo;
+        eo += (long long)2 * B.n_e[m] * B.k[m];
+    }
+    B.slot_off[np] = slots;
+    B.n_slots = slots;
+    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> skel;   // (j, i) -> (m, t)
+    for (int m = 0; m < np; ++m) {
+        const PatchDev& P = M.patches[m];
+        for (int t = 0; t < B.n_e[m]; ++t) {
+            int i, j;
+            ring_node(P.x0, P.x1, P.y0, P.y1, t, i, j);
+            skel[{j, i}].push_back({m, t});
+        }
+    }
+    std::vector<int> row_ptr{0}, row_slot, row_bnd, sk_ptr{0}, sk_slot, sk_node, sk_ring;
+    const unsigned neg = 0x80000000u;
+    for (auto& kv : skel) {
+        const int j = kv.first.first, i = kv.first.second;
+        auto lst = kv.second;
+        std::sort(lst.begin(), lst.end());
+        const bool bnd = (i == 0 || i == N || j == 0 || j == N);
+        for (auto& mt : lst) sk_slot.push_back(B.slot_off[mt.first] + 2 * mt.second);
+        sk_ptr.push_back((int)sk_slot.size());
+        sk_node.push_back(j * (N + 1) + i);
+        sk_ring.push_back(bnd ? domain_ring_pos(N, i, j) : -1);
+        if (bnd) {
+            for (auto& mt : lst) {
+                row_slot.push_back(B.slot_off[mt.first] + 2 * mt.second);
+                row_ptr.push_back((int)row_slot.size());
+                row_bnd.push_back(domain_ring_pos(N, i, j));
+            }
+        } else {
+            for (size_t r = 1; r < lst.size(); ++r) {
+                row_slot.push_back(B.slot_off[lst[0].first] + 2 * lst[0].second);
+                row_slot.push_back((int)((unsigned)(B.slot_off[lst[r].first] + 2 * lst[r].second) | neg));
+                row_ptr.push_back((int)row_slot.size());
+                row_bnd.push_back(-1);
+            }
+            for (auto& mt : lst) row_slot.push_back(B.slot_off[mt.first] + 2 * mt.second + 1);
+            row_ptr.push_back((int)row_slot.size());
+            row_bnd.push_back(-1);
+        }
+    }
+    B.n_rows = (int)row_bnd.size();
+    B.n_skel = (int)sk_node.size();
+    // transpose: per slot, rows touching it
+    std::vector<std::vector<int>> tl(slots);
+    for (int r = 0; r < B.n_rows; ++r)
+        for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            const unsigned v = (unsigned)row_slot[e];
+            tl[v & 0x7fffffffu].push_back((int)((unsigned)r | (v & neg)));
+        }
+    std::vector<int> tr_ptr{0}, tr_ent;
+    for (int g = 0; g < slots; ++g) {
+        for (int v : tl[g]) tr_ent.push_back(v);
+        tr_ptr.push_back((int)tr_ent.size());
+    }
+    MSP_TRY(upload(B.row_ptr, row_ptr, s)); MSP_TRY(upload(B.row_slot, row_slot, s)); MSP_TRY(upload(B.row_bnd, row_bnd, s));
+    MSP_TRY(upload(B.tr_ptr, tr_ptr, s)); MSP_TRY(upload(B.tr_ent, tr_ent, s));
+    MSP_TRY(upload(B.sk_ptr, sk_ptr, s)); MSP_TRY(upload(B.sk_slot, sk_slot, s)); MSP_TRY(upload(B.sk_node, sk_node, s));
+    MSP_TRY(upload(B.sk_ring, sk_ring, s));
+    MSP_TRY(upload(B.d_c_off, B.c_off, s)); MSP_TRY(upload(B.d_k, B.k, s)); MSP_TRY(upload(B.d_slot_off, B.slot_off, s));
+    MSP_TRY(upload(B.d_ne, B.n_e, s)); MSP_TRY(upload(B.d_q_off, B.q_off, s)); MSP_TRY(upload(B.d_e_off, B.e_off, s));
+    MSP_TRY(upload(B.d_patches, B.patches, s));
+    std::vector<unsigned char> xbr(N + 1, 0), ybr(N + 1, 0);
+    for (size_t i = 1; i + 1 < M.xb.size(); ++i) xbr[M.xb[i]] = 1;
+    for (size_t i = 1; i + 1 < M.yb.size(); ++i) ybr[M.yb[i]] = 1;
+    DevBuf<unsigned char> d_xbr, d_ybr;
+    MSP_TRY(upload(d_xbr, xbr, s)); MSP_TRY(upload(d_ybr, ybr, s));
+    MSP_TRY(B.E.alloc(std::max<long long>(eo, 1), s));
+    edge_ops_kernel<<<np, 256, 0, s>>>(N, M.aE.p, M.aN.p, B.d_patches.p, B.d_k.p, B.d_q_off.p, B.d_e_off.p, B.Q.p,
+                                       B.E.p, d_xbr.p, d_ybr.p);
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    // ---- preconditioner blocks (k x k) and their inverses
+    std::vector<SmallMat> kmats(np);
+    B.binv_off.resize(np);
+    long long ko = 0;
+    for (int m = 0; m < np; ++m) {
+        kmats[m] = SmallMat{ko, B.k[m], 0};
+        B.binv_off[m] = ko;
+        ko += (long long)B.k[m] * B.k[m];
+    }
+    DevBuf<SmallMat> d_kmats;
+    MSP_TRY(upload(d_kmats, kmats, s));
+    MSP_TRY(upload(B.d_binv_off, B.binv_off, s));
+    MSP_TRY(B.Binv.alloc(std::max<long long>(ko, 1), s));
+    precond_block_kernel<<<np, 256, 0, s>>>(B.d_k.p, B.d_ne.p, B.d_e_off.p, B.E.p, B.d_slot_off.p, B.tr_ptr.p,
+                                            d_kmats.p, G.p);
+    count_launches(1);
+    chol_factor_kernel<<<np, 256, 0, s>>>(d_kmats.p, G.p, L.p, F.p, Fi.p, shift_scale.p, 0, status.p);
+    count_launches(1);
+    precond_inverse_kernel<<<np, 256, 0, s>>>(d_kmats.p, Fi.p, B.d_binv_off.p, B.Binv.p);
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    MSP_CUDA(cudaMemcpyAsync(hstat.data(), status.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    for (int m = 0; m < np; ++m)
+        if (hstat[m] < 0 && B.k[m] > 0) {
+            set_error("msp_extract_basis: preconditioner block of patch " + std::to_string(m) + " is not positive definite");
+            return MSP_ERR_BREAKDOWN;
+        }
+    return MSP_OK;
+}
+
+}  // namespace msp

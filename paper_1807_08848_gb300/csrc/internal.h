@@ -1,0 +1,163 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/msp.h"
+
+namespace msp {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+void clear_error();
+msp_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define MSP_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) return ::msp::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define MSP_CHECK_ARG(cond, msg)                                                    \
+    do {                                                                            \
+        if (!(cond)) { ::msp::set_error(msg); return MSP_ERR_INVALID_ARG; }          \
+    } while (0)
+
+#define MSP_TRY(call)                                                               \
+    do { msp_status s_ = (call); if (s_ != MSP_OK) return s_; } while (0)
+
+// Stream-ordered device buffer owned by a handle.
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    msp_status alloc(size_t count, cudaStream_t s) {
+        free_now();
+        if (count == 0) return MSP_OK;
+        cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            set_error(std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
+                      " bytes failed: " + cudaGetErrorString(e));
+            return MSP_ERR_OOM;
+        }
+        n = count;
+        return MSP_OK;
+    }
+    void free_now() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { free_now(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// ------------------------------------------------------------------ geometry
+
+// Per-patch geometry as the kernels see it.
+struct PatchDev {
+    int x0, x1, y0, y1;      // K_m closed node box
+    int X0, X1, Y0, Y1;      // buffered box
+    int n_k, n_ring, samples, n_b, cols;
+    int bpos_offset;         // first entry in the boundary-position list
+    long long snap_offset;   // first element of the snapshot block
+};
+
+struct Medium {
+    int N = 0;
+    int mx = 0, my = 0;
+    std::vector<int> xb, yb;
+    std::vector<PatchDev> patches;      // host copy
+    std::vector<int> bpos;              // ring positions on the domain boundary, per patch
+    long long snap_elems = 0;
+    int max_tile_nodes = 0;             // max (X1-X0+1)(Y1-Y0+1)
+    int max_cols = 0;
+    DevBuf<double> aE, aN;              // FP64 face coefficients
+    DevBuf<float> aE32, aN32;           // FP32 copies (mixed path)
+    DevBuf<PatchDev> patches_dev;
+    DevBuf<int> bpos_dev;
+    DevBuf<double> snaps;               // snapshot blocks
+    DevBuf<int2> items;                 // (patch, column) work items, longest first
+    std::vector<int2> items_host;
+    int n_items = 0;
+    DevBuf<int> item_stats;             // per item: iterations, refinements, flag
+    DevBuf<double> scratch;             // local-solve workspace
+    bool sampled = false;
+    int device = 0;
+};
+
+// Ring node t of node box (X0,X1,Y0,Y1): counter-clockwise from (X0,Y0).
+__host__ __device__ inline void ring_node(int X0, int X1, int Y0, int Y1, int t, int& i, int& j) {
+    const int wx = X1 - X0, wy = Y1 - Y0;
+    if (t < wx) { i = X0 + t; j = Y0; }
+    else if (t < wx + wy) { i = X1; j = Y0 + (t - wx); }
+    else if (t < 2 * wx + wy) { i = X1 - (t - wx - wy); j = Y1; }
+    else { i = X0; j = Y1 - (t - 2 * wx - wy); }
+}
+
+// Reduced bases and the online operators of one medium.
+struct Basis {
+    int N = 0, mx = 0, my = 0;
+    std::vector<int> xb, yb;
+    std::vector<PatchDev> patches;
+    std::vector<int> k;                 // kept vectors per patch
+    std::vector<double> sigma;          // singular values, cols_m per patch
+    std::vector<long long> sigma_off;
+    std::vector<long long> q_off;       // Q_m block offsets (n_k x k_m)
+    std::vector<int> c_off;             // first coefficient of patch m
+    std::vector<int> n_e;               // ring nodes of K_m
+    std::vector<int> slot_off;          // first edge slot of patch m (2 slots per ring node)
+    std::vector<long long> e_off;       // E_m block offsets (2 n_e x k_m, row-major)
+    std::vector<long long> binv_off;    // preconditioner block offsets (k_m x k_m)
+    int Np = 0, n_slots = 0, n_rows = 0, n_skel = 0;
+    DevBuf<double> Q, E, Binv;
+    // device tables
+    DevBuf<int> d_c_off, d_k, d_slot_off, d_ne;
+    DevBuf<long long> d_q_off, d_e_off, d_binv_off;
+    DevBuf<PatchDev> d_patches;
+    DevBuf<int> row_ptr, row_slot, row_bnd;      // P~ rows: entries (global slot, sign in bit 31) and rhs ring position
+    DevBuf<int> tr_ptr, tr_ent;                  // transpose: per global slot, rows (sign in bit 31)
+    DevBuf<int> sk_ptr, sk_slot, sk_node, sk_ring;  // skeleton nodes: V slots, node index, ring position (-1 inside)
+    // online work space (grown on demand)
+    int cap_batch = 0;
+    DevBuf<double> w_c, w_p, w_z, w_e, w_q, w_r, w_part, w_scal;
+    DevBuf<int> w_iters;
+    int device = 0;
+};
+
+// ------------------------------------------------------------------ launchers
+struct LocalSolveCfg {
+    int precision;       // MSP_FP64 / MSP_MIXED
+    double tol;          // outer relative residual target
+    double inner_tol;    // FP32 inner solve target (mixed)
+    int max_iter;        // per inner solve
+    int max_ref;         // refinement steps (mixed)
+    uint64_t seed;
+};
+
+msp_status launch_medium_coefficients(Medium& M, const msp_medium_desc& d, cudaStream_t s);
+msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);
+msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst, cudaStream_t s);
+msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B);
+msp_status online_solve(Basis& B, const double* phi, int batch, double tol, int max_iter, double* u, double* c_out,
+                        int* iters_host, cudaStream_t s);
+
+int num_sms();
+
+// Count of kernel launches issued by the library (for launch accounting).
+void count_launches(long long n);
+
+}  // namespace msp
+
+struct msp_medium_s {
+    msp::Medium M;
+};
+struct msp_basis_s {
+    msp::Basis B;
+};

@@ -1,0 +1,413 @@
+// Online stage (Sec. 5.2, Eq. elliptic_cond_reduced): c = argmin |P~ c - d|_2 by
+// CGLS on the normal equations with the patch-block (additive Schwarz)
+// preconditioner M = blockdiag((P~^T P~)_mm), then the reconstruction
+// u = sum_m chi_m Q_m c_m with chi_m = 1/#patches sharing the node.
+//
+// A batch of B right-hand sides runs side by side; vectors are stored
+// element-major with the batch index fastest ([element][B]).  Every quantity of
+// one data set is reduced in an order that does not depend on B, so a data set
+// gets bit-identical results alone or inside any batch.
+#include "internal.h"
+#include "device_util.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace msp {
+
+namespace {
+
+constexpr int kRowChunk = 128;
+constexpr int kMaxBatch = 64;
+
+// scalar block per data set b (w_scal[b * 8 + .]):
+//   0 gamma, 1 alpha, 2 |P^T d|, 3 |s| last, 4 done flag, 5 iterations, 6 q.q
+struct OnArgs {
+    int np, B, n_rows, n_chunks;
+    const int* c_off;
+    const int* k;
+    const int* slot_off;
+    const int* ne;
+    const long long* e_off;
+    const long long* binv_off;
+    const double* E;
+    const double* Binv;
+    const int* row_ptr;
+    const int* row_slot;
+    const int* row_bnd;
+    const int* tr_ptr;
+    const int* tr_ent;
+};
+
+// e[slot][b] = sum_j E_m[slot][j] x_m[j][b] for every slot of patch m (one CTA per patch)
+__global__ void edge_apply_kernel(OnArgs A, const double* x, double* e) {
+    const int m = blockIdx.x, k = A.k[m], ns = 2 * A.ne[m], B = A.B;
+    const double* Em = A.E + A.e_off[m];
+    const double* xm = x + (long long)A.c_off[m] * B;
+    double* em = e + (long long)A.slot_off[m] * B;
+    for (int w = threadIdx.x; w < ns * B; w += blockDim.x) {
+        const int s = w / B, b = w - s * B;
+        const double* er = Em + (long long)s * k;
+        double a = 0.0;
+        for (int j = 0; j < k; ++j) a += er[j] * xm[(long long)j * B + b];
+        em[w] = a;
+    }
+}
+
+__device__ __forceinline__ double row_value(const OnArgs& A, const double* e, int r, int b) {
+    double a = 0.0;
+    for (int t = A.row_ptr[r]; t < A.row_ptr[r + 1]; ++t) {
+        const unsigned v = (unsigned)A.row_slot[t];
+        const double x = e[(long long)(v & 0x7fffffffu) * A.B + b];
+        a += (v & 0x80000000u) ? -x : x;
+    }
+    return a;
+}
+
+// q = P~ x (from the edge values e), per-chunk partial sums of q.q.  If init
+// is set, r = d - q instead (d from the boundary data phi), and partials hold
+// nothing.  Rows of a chunk are reduced warp by warp, then the four warp sums in
+// order: the order does not depend on the batch size.
+__global__ void __launch_bounds__(kRowChunk) rows_apply_kernel(OnArgs A, const double* e, double* q, double* part,
+                                                               const double* phi, int n4, double* r, int init) {
+    __shared__ double sw[kRowChunk / 32][kMaxBatch];
+    const int r0 = blockIdx.x * kRowChunk, B = A.B;
+    const int row = r0 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b = 0; b < B; ++b) {
+        double v = 0.0;
+        if (row < A.n_rows) {
+            v = row_value(A, e, row, b);
+            if (init) {
+                const int rb = A.row_bnd[row];
+                const double d = rb >= 0 ? phi[(long long)b * n4 + rb] : 0.0;
+                r[(long long)row * B + b] = d - v;
+                v = 0.0;
+            } else {
+                q[(long long)row * B + b] = v;
+            }
+        }
+        const double w = warp_sum(v * v);
+        if (lane == 0) sw[warp][b] = w;
+    }
+    __syncthreads();
+    if (!init && threadIdx.x < B) {
+        double a = 0.0;
+        for (int t = 0; t < kRowChunk / 32; ++t) a += sw[t][threadIdx.x];
+        part[(long long)blockIdx.x * B + threadIdx.x] = a;
+    }
+}
+
+// fixed-order sum over chunks for every data set: one warp per data set
+__global__ void finalize_alpha_kernel(OnArgs A, const double* part, double* scal) {
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x >> 5; b < A.B; b += blockDim.x >> 5) {
+    double a = 0.0;
+    for (int c = lane; c < A.n_chunks; c += 32) a += part[(long long)c * A.B + b];
+    a = warp_sum(a);
+    if (lane == 0) {
+        double* sc = scal + 8 * b;
+        sc[6] = a;
+        sc[1] = (sc[4] != 0.0 || a == 0.0) ? 0.0 : sc[0] / a;
+    }
+    }
+}
+
+// c += alpha p, r -= alpha q
+__global__ void update_cr_kernel(OnArgs A, double* c, const double* p, double* r, const double* q, const double* scal,
+                                 long long nc, long long nr) {
+    const int B = A.B;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc + nr; t += (long long)gridDim.x * blockDim.x) {
+        if (t < nc) {
+            const int b = (int)(t % B);
+            c[t] += scal[8 * b + 1] * p[t];
+        } else {
+            const long long u = t - nc;
+            const int b = (int)(u % B);
+            r[u] -= scal[8 * b + 1] * q[u];
+        }
+    }
+}
+
+// s = P~^T r (per patch: gather the rows of every edge slot, then E_m^T), z = Binv_m s,
+// partial sums (s.z, s.s) per patch.
+__global__ void normal_precond_kernel(OnArgs A, const double* r, double* z, double* part) {
+    extern __shared__ double sm[];
+    const int m = blockIdx.x, k = A.k[m], ns = 2 * A.ne[m], B = A.B;
+    double* t = sm;                       // [ns][B]
+    double* sv = sm + (long long)ns * B;  // [k][B]
+    const int g0 = A.slot_off[m];
+    for (int w = threadIdx.x; w < ns * B; w += blockDim.x) {
+        const int s = w / B, b = w - s * B;
+        double a = 0.0;
+        for (int u = A.tr_ptr[g0 + s]; u < A.tr_ptr[g0 + s + 1]; ++u) {
+            const unsigned v = (unsigned)A.tr_ent[u];
+            const double x = r[(long long)(v & 0x7fffffffu) * B + b];
+            a += (v & 0x80000000u) ? -x : x;
+        }
+        t[w] = a;
+    }
+    __syncthreads();
+    const double* Em = A.E + A.e_off[m];
+    for (int w = threadIdx.x; w < k * B; w += blockDim.x) {
+        const int j = w / B, b = w - j * B;
+        double a = 0.0;
+        for (int s = 0; s < ns; ++s) a += Em[(long long)s * k + j] * t[s * B + b];
+        sv[w] = a;
+    }
+    __syncthreads();
+    const double* Bi = A.Binv + A.binv_off[m];
+    double* zm = z + (long long)A.c_off[m] * B;
+    for (int w = threadIdx.x; w < k * B; w += blockDim.x) {
+        const int i = w / B, b = w - i * B;
+        double a = 0.0;
+        for (int j = 0; j < k; ++j) a += Bi[i + (long long)j * k] * sv[j * B + b];
+        zm[w] = a;
+    }
+    __syncthreads();
+    // partials: thread b sums over j in order
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        double sz = 0.0, ss = 0.0;
+        for (int j = 0; j < k; ++j) {
+            sz += sv[j * B + b] * zm[(long long)j * B + b];
+            ss += sv[j * B + b] * sv[j * B + b];
+        }
+        part[((long long)m * B + b) * 2 + 0] = sz;
+        part[((long long)m * B + b) * 2 + 1] = ss;
+    }
+}
+
+// gamma' = sum_m s.z, |s| = sqrt(sum_m s.s); convergence; beta.  mode 0: first
+// call (sets gamma and |P^T d|), mode 1: iteration.  beta goes to scal[7].
+__global__ void finalize_beta_kernel(OnArgs A, const double* part, double* scal, double tol, int max_iter, int mode) {
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x >> 5; b < A.B; b += blockDim.x >> 5) {
+    double sz = 0.0, ss = 0.0;
+    for (int m = lane; m < A.np; m += 32) {
+        sz += part[((long long)m * A.B + b) * 2 + 0];
+        ss += part[((long long)m * A.B + b) * 2 + 1];
+    }
+    sz = warp_sum(sz);
+    ss = warp_sum(ss);
+    if (lane == 0) {
+        double* sc = scal + 8 * b;
+        const double ns = sqrt(ss);
+        if (mode == 0) {
+            sc[0] = sz;
+            sc[2] = ns;
+            sc[3] = ns;
+            sc[4] = (ns == 0.0) ? 1.0 : 0.0;
+            sc[5] = 0.0;
+            sc[7] = 0.0;
+        } else if (sc[4] != 0.0) {
+            sc[7] = 0.0;
+        } else {
+            sc[5] += 1.0;
+            sc[3] = ns;
+            if (ns <= tol * sc[2] || sc[5] >= max_iter) {
+                sc[4] = (ns <= tol * sc[2]) ? 1.0 : 2.0;
+                sc[7] = 0.0;
+            } else {
+                sc[7] = sz / sc[0];
+                sc[0] = sz;
+            }
+        }
+    }
+    }
+}
+
+// p = z + beta p (mode 1) or p = z (mode 0); frozen for finished data sets
+__global__ void update_p_kernel(OnArgs A, double* p, const double* z, const double* scal, long long nc, int mode) {
+    const int B = A.B;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc; t += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(t % B);
+        if (mode == 0) p[t] = z[t];
+        else if (scal[8 * b + 4] == 0.0) p[t] = z[t] + scal[8 * b + 7] * p[t];
+    }
+}
+
+// interior nodes of every K_m: u = Q_m c_m (one CTA per patch)
+__global__ void recon_interior_kernel(OnArgs A, const PatchDev* patches, const long long* q_off, const double* Q,
+                                      const double* c, double* u, int N) {
+    const int m = blockIdx.x, B = A.B, k = A.k[m];
+    const PatchDev P = patches[m];
+    const int wi = P.x1 - P.x0 - 1, hi = P.y1 - P.y0 - 1;
+    if (wi <= 0 || hi <= 0) return;
+    const int wk = P.x1 - P.x0 + 1;
+    const double* q = Q + q_off[m];
+    const double* cm = c + (long long)A.c_off[m] * B;
+    const long long nn = (long long)(N + 1) * (N + 1);
+    for (long long w = threadIdx.x; w < (long long)wi * hi * B; w += blockDim.x) {
+        const int b = (int)(w % B);
+        const long long node = w / B;
+        const int ii = (int)(node % wi) + 1, jj = (int)(node / wi) + 1;
+        const int loc = ii + jj * wk;
+        double a = 0.0;
+        for (int j = 0; j < k; ++j) a += q[loc + (long long)j * P.n_k] * cm[(long long)j * B + b];
+        u[(long long)b * nn + (long long)(P.y0 + jj) * (N + 1) + (P.x0 + ii)] = a;
+    }
+}
+
+// skeleton nodes: average of the sharing patches' values (fixed patch order);
+// domain-boundary nodes take phi
+__global__ void recon_skeleton_kernel(OnArgs A, int n_skel, const int* sk_ptr, const int* sk_slot,
+                                      const int* sk_node, const int* sk_ring, const double* e, const double* phi,
+                                      int n4, double* u, int N) {
+    const int B = A.B;
+    const long long nn = (long long)(N + 1) * (N + 1);
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n_skel * B;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(w % B), x = (int)(w / B);
+        double v;
+        if (sk_ring[x] >= 0) {
+            v = phi[(long long)b * n4 + sk_ring[x]];
+        } else {
+            double a = 0.0;
+            const int n = sk_ptr[x + 1] - sk_ptr[x];
+            for (int t = sk_ptr[x]; t < sk_ptr[x + 1]; ++t) a += e[(long long)sk_slot[t] * B + b];
+            v = a / n;
+        }
+        u[(long long)b * nn + sk_node[x]] = v;
+    }
+}
+
+__global__ void export_c_kernel(const double* c, double* out, int Np, int B) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)Np * B; t += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(t % B);
+        const long long j = t / B;
+        out[(long long)b * Np + j] = c[t];
+    }
+}
+
+}  // namespace
+
+static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, int max_iter, double* u,
+                               double* c_out, int* iters_host, cudaStream_t s, bool* not_conv) {
+    const int np = (int)Bs.patches.size();
+    const int N = Bs.N, n4 = 4 * N;
+    OnArgs A{};
+    A.np = np;
+    A.B = B;
+    A.n_rows = Bs.n_rows;
+    A.n_chunks = (Bs.n_rows + kRowChunk - 1) / kRowChunk;
+    A.c_off = Bs.d_c_off.p; A.k = Bs.d_k.p; A.slot_off = Bs.d_slot_off.p; A.ne = Bs.d_ne.p;
+    A.e_off = Bs.d_e_off.p; A.binv_off = Bs.d_binv_off.p; A.E = Bs.E.p; A.Binv = Bs.Binv.p;
+    A.row_ptr = Bs.row_ptr.p; A.row_slot = Bs.row_slot.p; A.row_bnd = Bs.row_bnd.p;
+    A.tr_ptr = Bs.tr_ptr.p; A.tr_ent = Bs.tr_ent.p;
+    if (Bs.cap_batch < B) {
+        const int cb = kMaxBatch;
+        MSP_TRY(Bs.w_c.alloc((size_t)std::max(Bs.Np, 1) * cb, s));
+        MSP_TRY(Bs.w_p.alloc((size_t)std::max(Bs.Np, 1) * cb, s));
+        MSP_TRY(Bs.w_z.alloc((size_t)std::max(Bs.Np, 1) * cb, s));
+        MSP_TRY(Bs.w_e.alloc((size_t)std::max(Bs.n_slots, 1) * cb, s));
+        MSP_TRY(Bs.w_q.alloc((size_t)std::max(Bs.n_rows, 1) * cb, s));
+        MSP_TRY(Bs.w_r.alloc((size_t)std::max(Bs.n_rows, 1) * cb, s));
+        MSP_TRY(Bs.w_part.alloc((size_t)std::max(A.n_chunks, 2 * np) * cb * 2, s));
+        MSP_TRY(Bs.w_scal.alloc((size_t)8 * cb, s));
+        Bs.cap_batch = cb;
+    }
+    const long long nc = (long long)Bs.Np * B, nr = (long long)Bs.n_rows * B;
+    int max_ns = 0, max_k = 0;
+    for (int m = 0; m < np; ++m) {
+        max_ns = std::max(max_ns, 2 * Bs.n_e[m]);
+        max_k = std::max(max_k, Bs.k[m]);
+    }
+    const size_t smem = sizeof(double) * ((size_t)max_ns * B + (size_t)max_k * B);
+    if (smem > 48 * 1024)
+        MSP_CUDA(cudaFuncSetAttribute(normal_precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int ew_grid = std::max(1, std::min<int>((int)((nc + nr + 255) / 256), num_sms() * 8));
+    MSP_CUDA(cudaMemsetAsync(Bs.w_c.p, 0, sizeof(double) * nc, s));
+    MSP_CUDA(cudaMemsetAsync(Bs.w_e.p, 0, sizeof(double) * (size_t)Bs.n_slots * B, s));
+    // r = d
+    rows_apply_kernel<<<A.n_chunks, kRowChunk, 0, s>>>(A, Bs.w_e.p, Bs.w_q.p, Bs.w_part.p, phi, n4, Bs.w_r.p, 1);
+    count_launches(1);
+    normal_precond_kernel<<<np, 256, smem, s>>>(A, Bs.w_r.p, Bs.w_z.p, Bs.w_part.p);
+    count_launches(1);
+    finalize_beta_kernel<<<1, 1024, 0, s>>>(A, Bs.w_part.p, Bs.w_scal.p, tol, max_iter, 0);
+    count_launches(1);
+    update_p_kernel<<<ew_grid, 256, 0, s>>>(A, Bs.w_p.p, Bs.w_z.p, Bs.w_scal.p, nc, 0);
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    std::vector<double> scal(8 * (size_t)B);
+    const int check_every = 16;
+    for (int it = 0; it < max_iter; ++it) {
+        edge_apply_kernel<<<np, 256, 0, s>>>(A, Bs.w_p.p, Bs.w_e.p);
+        count_launches(1);
+        rows_apply_kernel<<<A.n_chunks, kRowChunk, 0, s>>>(A, Bs.w_e.p, Bs.w_q.p, Bs.w_part.p, phi, n4, Bs.w_r.p, 0);
+        count_launches(1);
+        finalize_alpha_kernel<<<1, 1024, 0, s>>>(A, Bs.w_part.p, Bs.w_scal.p);
+        count_launches(1);
+        update_cr_kernel<<<ew_grid, 256, 0, s>>>(A, Bs.w_c.p, Bs.w_p.p, Bs.w_r.p, Bs.w_q.p, Bs.w_scal.p, nc, nr);
+        count_launches(1);
+        normal_precond_kernel<<<np, 256, smem, s>>>(A, Bs.w_r.p, Bs.w_z.p, Bs.w_part.p);
+        count_launches(1);
+        finalize_beta_kernel<<<1, 1024, 0, s>>>(A, Bs.w_part.p, Bs.w_scal.p, tol, max_iter, 1);
+        count_launches(1);
+        update_p_kernel<<<ew_grid, 256, 0, s>>>(A, Bs.w_p.p, Bs.w_z.p, Bs.w_scal.p, nc, 1);
+        count_launches(1);
+        MSP_CUDA(cudaGetLastError());
+        if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
+            MSP_CUDA(cudaMemcpyAsync(scal.data(), Bs.w_scal.p, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, s));
+            MSP_CUDA(cudaStreamSynchronize(s));
+            bool all = true;
+            for (int b = 0; b < B; ++b) all &= scal[8 * b + 4] != 0.0;
+            if (all) break;
+        }
+    }
+    // reconstruction
+    const long long nn = (long long)(N + 1) * (N + 1);
+    recon_interior_kernel<<<np, 256, 0, s>>>(A, Bs.d_patches.p, Bs.d_q_off.p, Bs.Q.p, Bs.w_c.p, u, N);
+    count_launches(1);
+    edge_apply_kernel<<<np, 256, 0, s>>>(A, Bs.w_c.p, Bs.w_e.p);
+    count_launches(1);
+    const int sk_grid = std::max(1, std::min<int>((int)(((long long)Bs.n_skel * B + 255) / 256), num_sms() * 8));
+    recon_skeleton_kernel<<<sk_grid, 256, 0, s>>>(A, Bs.n_skel, Bs.sk_ptr.p, Bs.sk_slot.p, Bs.sk_node.p, Bs.sk_ring.p,
+                                                  Bs.w_e.p, phi, n4, u, N);
+    count_launches(1);
+    if (c_out) {
+        export_c_kernel<<<ew_grid, 256, 0, s>>>(Bs.w_c.p, c_out, Bs.Np, B);
+        count_launches(1);
+    }
+    MSP_CUDA(cudaGetLastError());
+    (void)nn;
+    if (iters_host) {
+        MSP_CUDA(cudaMemcpyAsync(scal.data(), Bs.w_scal.p, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        for (int b = 0; b < B; ++b) {
+            iters_host[b] = (int)scal[8 * b + 5];
+            if (scal[8 * b + 4] != 1.0) *not_conv = true;
+        }
+    }
+    return MSP_OK;
+}
+
+int online_batch_cap(const Basis& Bs) {
+    int max_ns = 0, max_k = 0;
+    for (size_t m = 0; m < Bs.patches.size(); ++m) {
+        max_ns = std::max(max_ns, 2 * Bs.n_e[m]);
+        max_k = std::max(max_k, Bs.k[m]);
+    }
+    const long long per = (long long)(max_ns + max_k) * (long long)sizeof(double);
+    const long long cap = (200LL * 1024) / std::max<long long>(per, 1);
+    return (int)std::max<long long>(1, std::min<long long>(kMaxBatch, cap));
+}
+
+msp_status online_solve(Basis& Bs, const double* phi, int batch, double tol, int max_iter, double* u, double* c_out,
+                        int* iters_host, cudaStream_t s) {
+    const int N = Bs.N;
+    const long long nn = (long long)(N + 1) * (N + 1);
+    bool not_conv = false;
+    const int cap = online_batch_cap(Bs);
+    for (int b0 = 0; b0 < batch; b0 += cap) {
+        const int B = std::min(cap, batch - b0);
+        MSP_TRY(online_batch(Bs, phi + (long long)b0 * 4 * N, B, tol, max_iter, u + (long long)b0 * nn,
+                             c_out ? c_out + (long long)b0 * Bs.Np : nullptr, iters_host ? iters_host + b0 : nullptr, s,
+                             &not_conv));
+    }
+    if (not_conv) {
+        set_error("msp_online_solve: some data sets stopped at max_iter");
+        return MSP_ERR_NOT_CONVERGED;
+    }
+    return MSP_OK;
+}
+
+}  // namespace msp
