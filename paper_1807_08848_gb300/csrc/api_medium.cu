@@ -130,6 +130,13 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
     });
     M.n_items = (int)items.size();
     M.items_host = items;
+    for (int pi = 0; pi < 2; ++pi) {   // per precision: tile-eligible items first
+        std::vector<int2> a, b;
+        for (const int2& it : items) (tile_kernel_fits(M.patches[it.x], pi) ? a : b).push_back(it);
+        M.n_tile_items[pi] = (int)a.size();
+        a.insert(a.end(), b.begin(), b.end());
+        M.items_prec_host[pi] = a;
+    }
     msp_status st;
 #define BAIL(x)                       \
     do {                              \
@@ -153,6 +160,12 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
     BAIL(M.bpos_dev.alloc(std::max<size_t>(1, M.bpos.size()), s));
     BAIL(M.items.alloc(items.size(), s));
     BAIL(M.item_stats.alloc(3 * items.size(), s));
+    BAIL(M.counter.alloc(1, s));
+    for (int pi = 0; pi < 2; ++pi) {
+        BAIL(M.items_prec[pi].alloc(items.size(), s));
+        BAILC(cudaMemcpyAsync(M.items_prec[pi].p, M.items_prec_host[pi].data(), sizeof(int2) * items.size(),
+                              cudaMemcpyHostToDevice, s));
+    }
     BAIL(M.snaps.alloc((size_t)M.snap_elems, s));
     BAILC(cudaMemcpyAsync(M.patches_dev.p, M.patches.data(), sizeof(PatchDev) * M.patches.size(), cudaMemcpyHostToDevice, s));
     if (!M.bpos.empty())
@@ -220,8 +233,9 @@ extern "C" msp_status msp_sample_patches(msp_medium m, uint64_t seed, int precis
         MSP_CUDA(cudaStreamSynchronize(s));
         msp_solve_stats r{};
         r.n_solves = m->M.n_items;
+        const std::vector<int2>& order = m->M.items_prec_host[precision == MSP_MIXED ? 1 : 0];
         for (int i = 0; i < m->M.n_items; ++i) {
-            const PatchDev& P = m->M.patches[m->M.items_host[i].x];
+            const PatchDev& P = m->M.patches[order[i].x];
             r.unknown_iters += (long long)st[3 * i] * (P.X1 - P.X0 - 1) * (P.Y1 - P.Y0 - 1);
             r.total_iters += st[3 * i];
             r.max_iters = std::max(r.max_iters, st[3 * i]);

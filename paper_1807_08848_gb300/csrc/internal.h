@@ -86,8 +86,13 @@ struct Medium {
     DevBuf<int2> items;                 // (patch, column) work items, longest first
     std::vector<int2> items_host;
     int n_items = 0;
+    int n_tile_items[2] = {0, 0};       // per precision: leading items the tile kernel takes
+    DevBuf<int2> items_prec[2];         // per precision: items ordered tile-eligible first
+    std::vector<int2> items_prec_host[2];
+    DevBuf<int> counter;
     DevBuf<int> item_stats;             // per item: iterations, refinements, flag
-    DevBuf<double> scratch;             // local-solve workspace
+    DevBuf<double> scratch;             // tile-kernel workspace (FP64 iterate per CTA)
+    DevBuf<double> scratch_global;      // global-kernel workspace
     bool sampled = false;
     int device = 0;
 };
@@ -143,6 +148,9 @@ struct LocalSolveCfg {
 
 msp_status launch_medium_coefficients(Medium& M, const msp_medium_desc& d, cudaStream_t s);
 msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);
+bool tile_kernel_fits(const PatchDev& P, int precision);
+msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const int2* items, int n_items, int* counter,
+                                    cudaStream_t s);
 msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst, cudaStream_t s);
 msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B);
 msp_status online_solve(Basis& B, const double* phi, int batch, double tol, int max_iter, double* u, double* c_out,

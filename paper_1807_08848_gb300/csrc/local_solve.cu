@@ -294,22 +294,33 @@ SolveArgs base_args(Medium& M) {
 }  // namespace
 
 msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s) {
+    const bool mixed = cfg.precision == MSP_MIXED;
+    const int pi = mixed ? 1 : 0;
+    const int n_tile = M.n_tile_items[pi];
+    const int2* items = M.items_prec[pi].p;
+    // items whose tile fits on chip: the tile-resident kernel
+    MSP_TRY(launch_local_solves_tile(M, cfg, items, n_tile, M.counter.p, s));
+    const int n_rest = M.n_items - n_tile;
+    if (n_rest == 0) return MSP_OK;
+    // the rest: the global-scratch kernel
     SolveArgs A = base_args(M);
+    A.items = items + n_tile;
+    A.n_items = n_rest;
+    A.stats = M.item_stats.p + 3LL * n_tile;
     A.seed = cfg.seed;
     A.tol = cfg.tol;
     A.inner_tol = cfg.inner_tol;
     A.max_iter = cfg.max_iter;
     A.max_ref = cfg.max_ref;
-    const bool mixed = cfg.precision == MSP_MIXED;
     const long long tsz = mixed ? 4 : 8;
     long long slot = (long long)M.max_tile_nodes * (8 + 5 * tsz);
     slot = (slot + 255) / 256 * 256;
     const int threads = 512;
     const int per_sm = 2;
-    const int grid = std::max(1, std::min(M.n_items, num_sms() * per_sm));
+    const int grid = std::max(1, std::min(n_rest, num_sms() * per_sm));
     const size_t need = (size_t)slot * grid / sizeof(double) + 1;
-    if (M.scratch.n < need) MSP_TRY(M.scratch.alloc(need, s));
-    A.scratch = M.scratch.p;
+    if (M.scratch_global.n < need) MSP_TRY(M.scratch_global.alloc(need, s));
+    A.scratch = M.scratch_global.p;
     A.slot_bytes = slot;
     if (mixed)
         local_solve_global<float><<<grid, threads, 0, s>>>(A);
