@@ -132,7 +132,8 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
     M.items_host = items;
     for (int pi = 0; pi < 2; ++pi) {   // per precision: tile-eligible items first
         std::vector<int2> a, b;
-        for (const int2& it : items) (tile_kernel_fits(M.patches[it.x], pi) ? a : b).push_back(it);
+        const int R = tile_launch_rows(M.patches, pi);
+        for (const int2& it : items) (tile_kernel_fits(M.patches[it.x], pi, R) ? a : b).push_back(it);
         M.n_tile_items[pi] = (int)a.size();
         a.insert(a.end(), b.begin(), b.end());
         M.items_prec_host[pi] = a;

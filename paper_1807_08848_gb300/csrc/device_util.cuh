@@ -60,11 +60,11 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* buf) {
         if (lane == 0) buf[k * 32 + warp] = w;
     }
     __syncthreads();
+    // every warp adds the warp partials with the same shuffle tree
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        T t = 0;
-        for (int w = 0; w < nw; ++w) t += buf[k * 32 + w];
-        v[k] = t;
+        T t = (lane < nw) ? buf[k * 32 + lane] : T(0);
+        v[k] = warp_sum(t);
     }
 }
 

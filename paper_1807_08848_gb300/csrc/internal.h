@@ -148,7 +148,8 @@ struct LocalSolveCfg {
 
 msp_status launch_medium_coefficients(Medium& M, const msp_medium_desc& d, cudaStream_t s);
 msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);
-bool tile_kernel_fits(const PatchDev& P, int precision);
+int tile_launch_rows(const std::vector<PatchDev>& patches, int precision);
+bool tile_kernel_fits(const PatchDev& P, int precision, int R);
 msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const int2* items, int n_items, int* counter,
                                     cudaStream_t s);
 msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst, cudaStream_t s);

@@ -2,22 +2,27 @@
 // whole CG state on chip (Algorithm alg:summary, LocalPDESolver on the buffered
 // patch; Eq. elliptic_random for the ring data).
 //
-// Thread mapping: the interior nx x ny unknowns are cut into strips of 32
-// columns; each warp takes one strip and a segment of consecutive rows, so a
-// thread owns one column segment of up to kRows rows.  The search direction p
-// lives in registers and is mirrored in shared memory (zero halo) for the
-// east/west neighbours and the segment ends; north/south neighbours inside the
-// segment come from registers.  Every tile array uses the compile-time row pitch
-// kPitch, so the unrolled row loop addresses each array as one base register
-// plus immediate offsets.
+// CG runs on the symmetrically Jacobi-scaled operator  A~ = S A S,
+// S = diag(a_ii)^(-1/2): A~ has a unit diagonal, so the Jacobi preconditioner is
+// folded into the operator and the stencil reads four scaled face coefficients
+// and no diagonal.  Solving A~ d~ = S r gives the correction d = S d~.
 //
-//   T = float (mixed path): FP32 face coefficients, Jacobi scaling and the
-//     correction d in shared memory; r and A p in registers.  Outer FP64
-//     iterative refinement: r = b - A x from the FP64 iterate x and FP64
-//     coefficients, FP32 CG on r/|r|, x += |r| d.
+// Thread mapping: the interior nx x ny unknowns are cut into strips of 32
+// columns; each warp takes one strip and a segment of RPS consecutive rows, so a
+// thread owns one column segment.  The search direction p lives in registers and
+// is mirrored in shared memory (zero halo) for the east/west neighbours and the
+// segment ends; north/south neighbours inside the segment come from registers,
+// and so does the south face (the previous row's north face).  Every tile array
+// uses the compile-time row pitch kPitch, so the unrolled row loop addresses each
+// array as one base register plus immediate offsets.
+//
+//   T = float (mixed path): FP32 scaled faces in shared memory; r, A p, d and p in
+//     registers.  The tile is padded with zero faces to whole strips and segments,
+//     so the CG loop has no per-node branches (padded nodes stay exactly zero).
+//     Outer FP64 iterative refinement: r = b - A x from the FP64 iterate x and FP64
+//     coefficients, FP32 CG on S r / |S r|, x += |S r| S d~.
 //   T = double (plain FP64 path): p and A p in shared memory, r in registers,
-//     coefficients and the Jacobi scaling from a per-CTA copy in global scratch;
-//     the update d is applied to x directly.
+//     scaled faces and d~ in a per-CTA slot of global scratch.
 //
 // Items (patch, column) come from a global work counter, largest tiles first.
 #include "internal.h"
@@ -30,15 +35,14 @@ namespace msp {
 namespace {
 
 constexpr int kTileThreads = 768;
-constexpr int kRows = 12;     // max rows per thread segment
-constexpr int kPitch = 100;   // row pitch of every tile array: nx + 2 <= kPitch
+constexpr int kNumWarps = kTileThreads / 32;
+constexpr int kMaxRows = 12;  // max rows per thread segment
+constexpr int kPitch = 100;   // row pitch of every tile array: padded width + 2 <= kPitch
 
 struct TileArgs {
     int N;
     const double* aE;
     const double* aN;
-    const float* aE32;
-    const float* aN32;
     const PatchDev* patches;
     const int* bpos;
     const int2* items;
@@ -53,33 +57,35 @@ struct TileArgs {
     int* stats;
 };
 
-// per-CTA global slot (doubles, pitch kPitch):
-//   x   : (ny+2) rows  -- FP64 iterate with the ring data
-//   cE  : ny rows      -- cE[j][c] = east face of interior column c-1 (c = 0..nx)
-//   cN  : (ny+1) rows  -- cN[j][c] = north face of interior row j-1
-//   dv  : ny rows      -- Jacobi scaling (FP64 path only)
-__host__ __device__ constexpr long long slot_rows(int ny) { return (long long)(ny + 2) + ny + (ny + 1) + ny; }
-
-template <class T>
-struct SmemLayout;
-template <>
-struct SmemLayout<float> {
-    // ps (ny+2) | aE ny | aN ny+1 | dv ny | ds ny   rows of kPitch floats
-    static __host__ __device__ size_t bytes(int ny) { return sizeof(float) * (size_t)kPitch * (5 * (size_t)ny + 3); }
-};
-template <>
-struct SmemLayout<double> {
-    // ps (ny+2) | qs ny   rows of kPitch doubles
-    static __host__ __device__ size_t bytes(int ny) { return sizeof(double) * (size_t)kPitch * (2 * (size_t)ny + 2); }
+// Thread mapping of an nx x ny interior: strips of 32 columns, segments of rps rows.
+struct Mapping {
+    int nstrips, nseg, rps;
 };
 
-__host__ __device__ inline bool tile_mapping(int nx, int ny, int& nstrips, int& nseg, int& rps) {
-    const int nw = kTileThreads / 32;
-    nstrips = (nx + 31) / 32;
-    if (nx < 1 || ny < 1 || nx + 2 > kPitch || nstrips > nw) return false;
-    nseg = nw / nstrips;
-    rps = (ny + nseg - 1) / nseg;
-    return rps <= kRows;
+__host__ __device__ inline bool tile_mapping(int nx, int ny, Mapping& mp) {
+    mp.nstrips = (nx + 31) / 32;
+    if (nx < 1 || ny < 1 || 32 * mp.nstrips + 2 > kPitch || mp.nstrips > kNumWarps) return false;
+    mp.nseg = kNumWarps / mp.nstrips;
+    mp.rps = (ny + mp.nseg - 1) / mp.nseg;
+    return mp.rps <= kMaxRows;
+}
+
+// per-CTA global slot (doubles, rows of kPitch):
+//   x  : ny+2  FP64 iterate, tile node (c, rr) at rr*kPitch + c, ring data included
+//   cE : ny    cE[j][c] = east face of interior column c-1 (c = 0..nx), unscaled
+//   cN : ny+1  cN[j][c] = north face of interior row j-1, unscaled
+//   sv : ny    S = diag^(-1/2) of the interior nodes
+//   tE : ny    scaled east faces   (FP64 path)
+//   tN : ny+1  scaled north faces  (FP64 path)
+//   dd : ny    correction d~       (FP64 path)
+__host__ __device__ constexpr long long slot_rows(int ny) { return 7LL * ny + 4; }
+
+// shared memory, rows of kPitch elements, PR = padded rows
+//   float : ps (PR+2) | tE PR | tN PR+1
+//   double: ps (ny+2) | qs ny
+__host__ __device__ inline size_t smem_bytes(bool f32, int ny, int PR) {
+    return f32 ? sizeof(float) * (size_t)kPitch * (3 * (size_t)PR + 3)
+               : sizeof(double) * (size_t)kPitch * (2 * (size_t)ny + 2);
 }
 
 template <class T>
@@ -89,13 +95,13 @@ __device__ __forceinline__ T block_sum1(T v, T* buf) {
     return a[0];
 }
 
-template <class T>
+template <class T, int RPS>
 __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) {
     constexpr bool kF32 = sizeof(T) == 4;
     constexpr int PI = kPitch;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[3][64];
-    __shared__ double red64[2][32];
+    __shared__ T red[2][32];
+    __shared__ double red64[2][64];
     __shared__ int s_item;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* slot = A.scratch + (long long)blockIdx.x * A.slot_doubles;
@@ -110,51 +116,56 @@ __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) 
         const PatchDev P = A.patches[m];
         const int W = P.X1 - P.X0 + 1, H = P.Y1 - P.Y0 + 1;
         const int nx = W - 2, ny = H - 2;
-        int nstrips, nseg, rps;
-        tile_mapping(nx, ny, nstrips, nseg, rps);   // eligibility checked on the host
-        const int strip = warp % nstrips, seg = warp / nstrips;
-        const int i = strip * 32 + lane;            // owned interior column
-        const int j0 = seg * rps;                   // first owned interior row
-        const bool own = (seg < nseg) && (i < nx);
-        const int nrow = own ? max(0, min(rps, ny - j0)) : 0;
+        Mapping mp;
+        tile_mapping(nx, ny, mp);                   // eligibility checked on the host (rps <= RPS)
+        const int PR = mp.nseg * RPS;               // padded rows
+        const int PC = 32 * mp.nstrips;             // padded columns
+        const int strip = warp % mp.nstrips, seg = warp / mp.nstrips;
+        const int i = strip * 32 + lane;            // owned interior column (may be padding)
+        const int j0 = seg * RPS;                   // first owned interior row
+        const bool active = seg < mp.nseg;          // warp-uniform
+        const int nrow = (active && i < nx) ? max(0, min(RPS, ny - j0)) : 0;   // real rows owned
 
         // ---- global slot views
-        double* xg = slot;                                   // (ny+2) x PI, tile node (c, rr) at rr*PI + c
-        double* cE = xg + (long long)(ny + 2) * PI;          // ny x PI
-        double* cN = cE + (long long)ny * PI;                // (ny+1) x PI
-        double* dv64 = cN + (long long)(ny + 1) * PI;        // ny x PI
+        double* xg = slot;
+        double* cE = xg + (long long)(ny + 2) * PI;
+        double* cN = cE + (long long)ny * PI;
+        double* sv = cN + (long long)(ny + 1) * PI;
+        double* tE = sv + (long long)ny * PI;
+        double* tN = tE + (long long)ny * PI;
+        double* dd = tN + (long long)(ny + 1) * PI;
         // ---- shared views
-        T* ps = reinterpret_cast<T*>(smem_raw);              // (ny+2) x PI
-        float *aEs = nullptr, *aNs = nullptr, *dvs = nullptr, *ds = nullptr;
+        T* ps = reinterpret_cast<T*>(smem_raw);
+        float *tEs = nullptr, *tNs = nullptr;
         double* qs = nullptr;
         if constexpr (kF32) {
-            aEs = reinterpret_cast<float*>(ps) + (ny + 2) * PI;
-            aNs = aEs + ny * PI;
-            dvs = aNs + (ny + 1) * PI;
-            ds = dvs + ny * PI;
+            tEs = reinterpret_cast<float*>(ps) + (PR + 2) * PI;
+            tNs = tEs + PR * PI;
         } else {
             qs = reinterpret_cast<double*>(ps) + (ny + 2) * PI;
         }
-        // ---- stage coefficients, zero x and p
+        // ---- stage unscaled FP64 faces, zero x and p
         for (int t = threadIdx.x; t < ny * (nx + 1); t += blockDim.x) {
             const int jj = t / (nx + 1), c = t - jj * (nx + 1);
-            const long long g = (long long)(P.Y0 + 1 + jj) * N + (P.X0 + c);
-            cE[jj * PI + c] = A.aE[g];
-            if constexpr (kF32) aEs[jj * PI + c] = A.aE32[g];
+            cE[jj * PI + c] = A.aE[(long long)(P.Y0 + 1 + jj) * N + (P.X0 + c)];
         }
         for (int t = threadIdx.x; t < (ny + 1) * nx; t += blockDim.x) {
             const int jj = t / nx, c = t - jj * nx;
-            const long long g = (long long)(P.Y0 + jj) * (N + 1) + (P.X0 + 1 + c);
-            cN[jj * PI + c] = A.aN[g];
-            if constexpr (kF32) aNs[jj * PI + c] = A.aN32[g];
+            cN[jj * PI + c] = A.aN[(long long)(P.Y0 + jj) * (N + 1) + (P.X0 + 1 + c)];
+        }
+        {
+            const int prow = kF32 ? PR + 2 : H, pcol_n = kF32 ? PC + 2 : W;
+            for (int t = threadIdx.x; t < prow * pcol_n; t += blockDim.x) {
+                const int rr = t / pcol_n, c = t - rr * pcol_n;
+                ps[rr * PI + c] = T(0);
+            }
         }
         for (int t = threadIdx.x; t < H * W; t += blockDim.x) {
             const int rr = t / W, c = t - rr * W;
             xg[rr * PI + c] = 0.0;
-            ps[rr * PI + c] = T(0);
         }
         __syncthreads();
-        // ---- ring data
+        // ---- ring data; diagonal scaling S
         if (col < P.samples) {
             const int npairs = (P.n_ring + 1) >> 1;
             for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
@@ -173,160 +184,215 @@ __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) 
             ring_node(P.X0, P.X1, P.Y0, P.Y1, t0, gi, gj);
             xg[(gj - P.Y0) * PI + (gi - P.X0)] = 1.0;
         }
-        // ---- Jacobi scaling
         for (int t = threadIdx.x; t < nx * ny; t += blockDim.x) {
             const int jj = t / nx, c = t - jj * nx;
-            const double dg = cE[jj * PI + c + 1] + cE[jj * PI + c] + cN[(jj + 1) * PI + c] + cN[jj * PI + c];
-            if constexpr (kF32) dvs[jj * PI + c] = (float)(1.0 / dg);
-            else dv64[jj * PI + c] = 1.0 / dg;
+            sv[jj * PI + c] =
+                1.0 / sqrt(cE[jj * PI + c + 1] + cE[jj * PI + c] + cN[(jj + 1) * PI + c] + cN[jj * PI + c]);
+        }
+        __syncthreads();
+        // ---- scaled faces: a_f s_a s_b between two interior nodes, zero next to the ring or padding
+        if constexpr (kF32) {
+            for (int t = threadIdx.x; t < PR * (PC + 1); t += blockDim.x) {
+                const int jj = t / (PC + 1), c = t - jj * (PC + 1);
+                float v = 0.f;
+                if (jj < ny && c >= 1 && c <= nx - 1)
+                    v = (float)(cE[jj * PI + c] * sv[jj * PI + c - 1] * sv[jj * PI + c]);
+                tEs[jj * PI + c] = v;
+            }
+            for (int t = threadIdx.x; t < (PR + 1) * PC; t += blockDim.x) {
+                const int jj = t / PC, c = t - jj * PC;
+                float v = 0.f;
+                if (jj >= 1 && jj <= ny - 1 && c < nx)
+                    v = (float)(cN[jj * PI + c] * sv[(jj - 1) * PI + c] * sv[jj * PI + c]);
+                tNs[jj * PI + c] = v;
+            }
+        } else {
+            for (int t = threadIdx.x; t < ny * (nx + 1); t += blockDim.x) {
+                const int jj = t / (nx + 1), c = t - jj * (nx + 1);
+                tE[jj * PI + c] = (c >= 1 && c <= nx - 1) ? cE[jj * PI + c] * sv[jj * PI + c - 1] * sv[jj * PI + c] : 0.0;
+            }
+            for (int t = threadIdx.x; t < (ny + 1) * nx; t += blockDim.x) {
+                const int jj = t / nx, c = t - jj * nx;
+                tN[jj * PI + c] =
+                    (jj >= 1 && jj <= ny - 1) ? cN[jj * PI + c] * sv[(jj - 1) * PI + c] * sv[jj * PI + c] : 0.0;
+            }
         }
         __syncthreads();
 
         // per-thread column bases (row r of the segment at offset r * PI)
-        T* pcol = ps + (j0 + 1) * PI + (i + 1);                 // p at node (i, j0 + r)
+        T* pcol = ps + (j0 + 1) * PI + (i + 1);          // p at node (i, j0 + r)
         double* xcol = xg + (j0 + 1) * PI + (i + 1);
-        const double* e64 = cE + j0 * PI + (i + 1);              // east face; west at -1
-        const double* n64 = cN + (j0 + 1) * PI + i;              // north face; south at -PI
-        const T* dvc;
-        if constexpr (kF32) dvc = dvs + j0 * PI + i;
-        else dvc = dv64 + j0 * PI + i;
+        const double* e64 = cE + j0 * PI + (i + 1);       // unscaled east face; west at -1
+        const double* n64 = cN + (j0 + 1) * PI + i;       // unscaled north face; south at -PI
+        const double* s64 = sv + j0 * PI + i;
+        const T* te;                                      // scaled east face; west at -1
+        const T* tn;                                      // scaled north face; south at -PI
+        if constexpr (kF32) {
+            te = tEs + j0 * PI + (i + 1);
+            tn = tNs + (j0 + 1) * PI + i;
+        } else {
+            te = tE + j0 * PI + (i + 1);
+            tn = tN + (j0 + 1) * PI + i;
+        }
 
-        T rreg[kRows], qreg[kF32 ? kRows : 1], p[kRows];
+        T rreg[RPS], p[RPS];
         int total_it = 0, refs = 0, bad = 0;
         double b2 = -1.0;
         const int passes = kF32 ? A.max_ref : 1;
         for (int pass = 0; pass < passes; ++pass) {
-            // FP64 residual r = -(A x) on the owned nodes (kept unscaled in T)
-            double part = 0.0;
+            // FP64 residual r = -(A x) on the owned real nodes; r~ = S r (unnormalised)
+            double part[2] = {0.0, 0.0};
 #pragma unroll
-            for (int r = 0; r < kRows; ++r) {
+            for (int r = 0; r < RPS; ++r) {
                 rreg[r] = 0;
                 if (r < nrow) {
                     const int o = r * PI;
                     const double ae = e64[o], aw = e64[o - 1], an = n64[o], as = n64[o - PI];
                     const double v = -((ae + aw + an + as) * xcol[o] - ae * xcol[o + 1] - aw * xcol[o - 1] -
                                        an * xcol[o + PI] - as * xcol[o - PI]);
-                    rreg[r] = (T)v;
-                    part += v * v;
+                    const double vs = v * s64[o];
+                    rreg[r] = (T)vs;
+                    part[0] += v * v;
+                    part[1] += vs * vs;
                 }
             }
-            const double r2 = block_sum1<double>(part, red64[pass & 1]);
-            if (b2 < 0) b2 = r2;
-            if (b2 == 0.0 || r2 <= A.tol * A.tol * b2) break;
-            const double scale = kF32 ? sqrt(r2) : 1.0;
+            block_sum<double, 2>(part, red64[pass & 1]);
+            if (b2 < 0) b2 = part[0];
+            if (b2 == 0.0 || part[0] <= A.tol * A.tol * b2) break;
+            const double scale = kF32 ? sqrt(part[1]) : 1.0;
             const T inv = (T)(1.0 / scale);
-            // CG from d = 0: z = D^-1 r, p = z
-            T rz_part = 0, rr_part = 0;
-#pragma unroll
-            for (int r = 0; r < kRows; ++r) {
-                p[r] = 0;
-                if (r < nrow) {
-                    const int o = r * PI;
-                    const T rr_ = rreg[r] * inv;
-                    rreg[r] = rr_;
-                    p[r] = dvc[o] * rr_;
-                    rz_part += rr_ * p[r];
-                    rr_part += rr_ * rr_;
-                    pcol[o] = p[r];
-                    if constexpr (kF32) ds[(j0 + r) * PI + i] = 0.f;
-                }
-            }
-            T v0[2] = {rz_part, rr_part};
-            block_sum<T, 2>(v0, red[0]);     // also orders the p stores above
-            T rz = v0[0];
-            const T rr0 = v0[1];
-            const T stop = (T)(kF32 ? A.inner_tol * A.inner_tol : A.tol * A.tol) * rr0;
             int it = 0;
-            if (rr0 > T(0)) {
-                float* dcol = nullptr;
-                if constexpr (kF32) dcol = ds + j0 * PI + i;
-                for (; it < A.max_iter;) {
-                    // q = A p on the owned column segment, pAp
-                    T pq = 0;
-                    T south = (nrow > 0) ? pcol[-PI] : T(0);
+            if constexpr (kF32) {
+                // ---- FP32 CG on the padded tile, no per-node branches
+                float dreg[RPS], qreg[RPS];
+                float rz = 0.f;
 #pragma unroll
-                    for (int r = 0; r < kRows; ++r) {
-                        if (r < nrow) {
-                            const int o = r * PI;
-                            const T north = (r + 1 < nrow) ? p[r + 1] : pcol[o + PI];
-                            const T west = pcol[o - 1];
-                            const T east = pcol[o + 1];
-                            T ce, cw, cn, cs;
-                            if constexpr (kF32) {
-                                const float* ec = aEs + j0 * PI + (i + 1);
-                                const float* nc = aNs + (j0 + 1) * PI + i;
-                                ce = ec[o]; cw = ec[o - 1]; cn = nc[o]; cs = nc[o - PI];
-                            } else {
-                                ce = e64[o]; cw = e64[o - 1]; cn = n64[o]; cs = n64[o - PI];
-                            }
-                            const T pc = p[r];
-                            const T qq = (ce + cw + cn + cs) * pc - ce * east - cw * west - cn * north - cs * south;
-                            if constexpr (kF32) qreg[r] = qq;
-                            else qs[(j0 + r) * PI + i] = qq;
-                            pq += pc * qq;
-                            south = pc;
-                        }
-                    }
-                    const T pAp = block_sum1<T>(pq, red[1]);
-                    const T alpha = rz / pAp;
-                    T zr = 0, rr = 0;
-#pragma unroll
-                    for (int r = 0; r < kRows; ++r) {
-                        if (r < nrow) {
-                            const int o = r * PI;
-                            T qq;
-                            if constexpr (kF32) {
-                                dcol[o] += alpha * p[r];
-                                qq = qreg[r];
-                            } else {
-                                xcol[o] += alpha * p[r];
-                                qq = qs[(j0 + r) * PI + i];
-                            }
-                            const T rr_ = rreg[r] - alpha * qq;
-                            rreg[r] = rr_;
-                            const T z = dvc[o] * rr_;
-                            if constexpr (kF32) qreg[r] = z;
-                            else qs[(j0 + r) * PI + i] = z;
-                            zr += rr_ * z;
-                            rr += rr_ * rr_;
-                        }
-                    }
-                    T v2[2] = {zr, rr};
-                    block_sum<T, 2>(v2, red[2]);
-                    ++it;
-                    if (v2[1] <= stop) break;
-                    const T beta = v2[0] / rz;
-                    rz = v2[0];
-#pragma unroll
-                    for (int r = 0; r < kRows; ++r) {
-                        if (r < nrow) {
-                            const int o = r * PI;
-                            T z;
-                            if constexpr (kF32) z = qreg[r];
-                            else z = qs[(j0 + r) * PI + i];
-                            p[r] = z + beta * p[r];
-                            pcol[o] = p[r];
-                        }
-                    }
-                    __syncthreads();
+                for (int r = 0; r < RPS; ++r) {
+                    rreg[r] *= inv;
+                    p[r] = rreg[r];
+                    dreg[r] = 0.f;
+                    rz += rreg[r] * rreg[r];
+                    if (active) pcol[r * PI] = p[r];
                 }
+                rz = block_sum1<float>(rz, red[0]);      // also orders the p stores above
+                const float stop = (float)(A.inner_tol * A.inner_tol) * rz;
+                if (rz > 0.f) {
+                    for (; it < A.max_iter;) {
+                        // q = A~ p = p - (sum of scaled faces x neighbours), pAp
+                        float pq = 0.f;
+                        if (active) {
+                            float south = pcol[-PI];
+                            float cs = tn[-PI];
+#pragma unroll
+                            for (int r = 0; r < RPS; ++r) {
+                                const int o = r * PI;
+                                const float north = (r + 1 < RPS) ? p[r + 1] : pcol[o + PI];
+                                const float ce = te[o], cw = te[o - 1], cn = tn[o];
+                                const float pc = p[r];
+                                const float qq = pc - (ce * pcol[o + 1] + cw * pcol[o - 1] + cn * north + cs * south);
+                                qreg[r] = qq;
+                                pq += pc * qq;
+                                south = pc;
+                                cs = cn;
+                            }
+                        }
+                        const float alpha = rz / block_sum1<float>(pq, red[1]);
+                        float rr = 0.f;
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r) {
+                            dreg[r] += alpha * p[r];
+                            rreg[r] -= alpha * qreg[r];
+                            rr += rreg[r] * rreg[r];
+                        }
+                        rr = block_sum1<float>(rr, red[0]);
+                        ++it;
+                        if (rr <= stop) break;
+                        const float beta = rr / rz;
+                        rz = rr;
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r) {
+                            p[r] = rreg[r] + beta * p[r];
+                            if (active) pcol[r * PI] = p[r];
+                        }
+                        __syncthreads();
+                    }
+                }
+                // x += |S r| S d~ on the owned real nodes
+#pragma unroll
+                for (int r = 0; r < RPS; ++r)
+                    if (r < nrow) xcol[r * PI] += scale * s64[r * PI] * (double)dreg[r];
+            } else {
+                // ---- FP64 CG, d~ accumulated in the slot
+                double* dcol = dd + j0 * PI + i;
+                double rz = 0.0;
+#pragma unroll
+                for (int r = 0; r < RPS; ++r) {
+                    p[r] = 0;
+                    if (r < nrow) {
+                        p[r] = rreg[r];
+                        rz += rreg[r] * rreg[r];
+                        pcol[r * PI] = p[r];
+                        dcol[r * PI] = 0.0;
+                    }
+                }
+                rz = block_sum1<double>(rz, red[0]);
+                const double stop = A.tol * A.tol * rz;
+                if (rz > 0.0) {
+                    for (; it < A.max_iter;) {
+                        double pq = 0.0;
+                        double south = (nrow > 0) ? pcol[-PI] : 0.0;
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r) {
+                            if (r < nrow) {
+                                const int o = r * PI;
+                                const double north = (r + 1 < nrow) ? p[r + 1] : pcol[o + PI];
+                                const double pc = p[r];
+                                const double qq =
+                                    pc - (te[o] * pcol[o + 1] + te[o - 1] * pcol[o - 1] + tn[o] * north + tn[o - PI] * south);
+                                qs[(j0 + r) * PI + i] = qq;
+                                pq += pc * qq;
+                                south = pc;
+                            }
+                        }
+                        const double alpha = rz / block_sum1<double>(pq, red[1]);
+                        double rr = 0.0;
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r) {
+                            if (r < nrow) {
+                                dcol[r * PI] += alpha * p[r];
+                                rreg[r] -= alpha * qs[(j0 + r) * PI + i];
+                                rr += rreg[r] * rreg[r];
+                            }
+                        }
+                        rr = block_sum1<double>(rr, red[0]);
+                        ++it;
+                        if (rr <= stop) break;
+                        const double beta = rr / rz;
+                        rz = rr;
+#pragma unroll
+                        for (int r = 0; r < RPS; ++r) {
+                            if (r < nrow) {
+                                p[r] = rreg[r] + beta * p[r];
+                                pcol[r * PI] = p[r];
+                            }
+                        }
+                        __syncthreads();
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RPS; ++r)
+                    if (r < nrow) xcol[r * PI] += s64[r * PI] * dcol[r * PI];
             }
             if (it >= A.max_iter) bad = 1;
             total_it += it;
             ++refs;
-            // x += |r| d on the owned nodes (FP32 path; the FP64 path updated x in place)
-            if constexpr (kF32) {
-#pragma unroll
-                for (int r = 0; r < kRows; ++r)
-                    if (r < nrow) xcol[r * PI] += scale * (double)ds[(j0 + r) * PI + i];
-            }
             __syncthreads();
             if (bad) break;
         }
         if (kF32 && !bad && b2 > 0.0) {   // did the refinement reach tol?
             double part = 0.0;
 #pragma unroll
-            for (int r = 0; r < kRows; ++r) {
+            for (int r = 0; r < RPS; ++r) {
                 if (r < nrow) {
                     const int o = r * PI;
                     const double ae = e64[o], aw = e64[o - 1], an = n64[o], as = n64[o - PI];
@@ -354,14 +420,45 @@ __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) 
     }
 }
 
+// Rows per segment the tile needs, rounded up to an instantiated value.
+int rows_instance(int rps) {
+    for (int v : {4, 8, 12})
+        if (rps <= v) return v;
+    return 0;
+}
+
+template <class T, int RPS>
+msp_status launch_rps(const TileArgs& A, int grid, size_t smem, cudaStream_t s) {
+    MSP_CUDA(cudaFuncSetAttribute(local_solve_tile<T, RPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    local_solve_tile<T, RPS><<<grid, kTileThreads, smem, s>>>(A);
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    return MSP_OK;
+}
+
 }  // namespace
 
-bool tile_kernel_fits(const PatchDev& P, int precision) {
+// Rows per segment of one tile-kernel launch: the largest instance any patch
+// that fits on its own needs.
+int tile_launch_rows(const std::vector<PatchDev>& patches, int precision) {
+    int R = 0;
+    for (const PatchDev& P : patches) {
+        const int nx = P.X1 - P.X0 - 1, ny = P.Y1 - P.Y0 - 1;
+        Mapping mp;
+        if (!tile_mapping(nx, ny, mp)) continue;
+        const int r = rows_instance(mp.rps);
+        if (r && smem_bytes(precision == MSP_MIXED, ny, mp.nseg * r) <= 220 * 1024) R = std::max(R, r);
+    }
+    return R;
+}
+
+// Can a tile-kernel launch with R rows per segment take this patch?  Within the
+// thread mapping, with the padded shared-memory footprint under the limit.
+bool tile_kernel_fits(const PatchDev& P, int precision, int R) {
     const int nx = P.X1 - P.X0 - 1, ny = P.Y1 - P.Y0 - 1;
-    int nstrips, nseg, rps;
-    if (!tile_mapping(nx, ny, nstrips, nseg, rps)) return false;
-    const size_t sm = precision == MSP_MIXED ? SmemLayout<float>::bytes(ny) : SmemLayout<double>::bytes(ny);
-    return sm <= 220 * 1024;
+    Mapping mp;
+    if (R == 0 || !tile_mapping(nx, ny, mp) || mp.rps > R) return false;
+    return smem_bytes(precision == MSP_MIXED, ny, mp.nseg * R) <= 220 * 1024;
 }
 
 msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const int2* items, int n_items,
@@ -369,7 +466,8 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
     if (n_items == 0) return MSP_OK;
     TileArgs A{};
     A.N = M.N;
-    A.aE = M.aE.p; A.aN = M.aN.p; A.aE32 = M.aE32.p; A.aN32 = M.aN32.p;
+    A.aE = M.aE.p;
+    A.aN = M.aN.p;
     A.patches = M.patches_dev.p;
     A.bpos = M.bpos_dev.p;
     A.items = items;
@@ -383,12 +481,16 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
     A.max_ref = cfg.max_ref;
     A.stats = M.item_stats.p;
     const bool mixed = cfg.precision == MSP_MIXED;
-    size_t smem = 0;
+    // one row-count instance for the launch (eligibility was decided with the same R)
+    const int R = tile_launch_rows(M.patches, cfg.precision);
     int max_ny = 0;
+    size_t smem = 0;
     for (const PatchDev& P : M.patches) {
-        if (!tile_kernel_fits(P, cfg.precision)) continue;
+        if (!tile_kernel_fits(P, cfg.precision, R)) continue;
         const int ny = P.Y1 - P.Y0 - 1;
-        smem = std::max(smem, mixed ? SmemLayout<float>::bytes(ny) : SmemLayout<double>::bytes(ny));
+        Mapping mp;
+        tile_mapping(P.X1 - P.X0 - 1, ny, mp);
+        smem = std::max(smem, smem_bytes(mixed, ny, mp.nseg * R));
         max_ny = std::max(max_ny, ny);
     }
     smem = (smem + 15) / 16 * 16;
@@ -399,15 +501,13 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
     A.scratch = M.scratch.p;
     MSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
     if (mixed) {
-        MSP_CUDA(cudaFuncSetAttribute(local_solve_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        local_solve_tile<float><<<grid, kTileThreads, smem, s>>>(A);
-    } else {
-        MSP_CUDA(cudaFuncSetAttribute(local_solve_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        local_solve_tile<double><<<grid, kTileThreads, smem, s>>>(A);
+        if (R == 4) return launch_rps<float, 4>(A, grid, smem, s);
+        if (R == 8) return launch_rps<float, 8>(A, grid, smem, s);
+        return launch_rps<float, 12>(A, grid, smem, s);
     }
-    count_launches(1);
-    MSP_CUDA(cudaGetLastError());
-    return MSP_OK;
+    if (R == 4) return launch_rps<double, 4>(A, grid, smem, s);
+    if (R == 8) return launch_rps<double, 8>(A, grid, smem, s);
+    return launch_rps<double, 12>(A, grid, smem, s);
 }
 
 }  // namespace msp
