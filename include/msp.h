@@ -202,6 +202,24 @@ void msp_basis_destroy(msp_basis b);
 msp_status msp_basis_info(msp_basis b, int patch, int* k, double* sigma_host);
 /* Copy Q_m (n_k x k_m, column-major) to dst_dev. */
 msp_status msp_get_basis(msp_basis b, int patch, double* dst_dev, void* stream);
+/* Diagnostics of the extraction. */
+typedef struct {
+    int max_jacobi_sweeps;     /* largest sweep count of the one-sided Jacobi SVDs          */
+    int max_cholqr_tries;      /* largest number of shift attempts in Cholesky-QR           */
+    float online_shift;        /* diagonal shift the online factorisation needed (0 = none) */
+    int online_blocks;         /* rows of patches = diagonal blocks of the online factor    */
+} msp_basis_stats;
+msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out);
+
+/* Preconditioner of the online least-squares iteration:
+ *   MSP_PRECOND_BLOCK_ROWS (default): block-tridiagonal Cholesky of the scaled
+ *     normal matrix over rows of patches (FP32 factor, FP64 iteration);
+ *   MSP_PRECOND_PATCH_BLOCKS: the inverse patch blocks (P~^T P~)_mm^{-1} only
+ *     (one-level additive Schwarz). */
+#define MSP_PRECOND_BLOCK_ROWS   0
+#define MSP_PRECOND_PATCH_BLOCKS 1
+msp_status msp_basis_set_preconditioner(msp_basis b, int kind);
+
 /* Total unknowns N_p = sum k_m and rows of P~. */
 msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_rows);
 

@@ -169,6 +169,16 @@ class Basis:
     def handle(self):
         return self._h
 
+    def stats(self) -> dict:
+        st = N.BasisStats()
+        N.check(N.load().msp_basis_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def set_preconditioner(self, kind: str):
+        """'block_rows' (block-tridiagonal factor, default) or 'patch_blocks'."""
+        code = {"block_rows": 0, "patch_blocks": 1}[kind]
+        N.check(N.load().msp_basis_set_preconditioner(self._h, code))
+
     def k(self, m: int) -> int:
         k = C.c_int()
         N.check(N.load().msp_basis_info(self._h, m, C.byref(k), None))

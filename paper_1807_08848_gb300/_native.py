@@ -44,6 +44,11 @@ class PatchInfo(C.Structure):
                 ("cols", C.c_int), ("snap_offset", C.c_int64)]
 
 
+class BasisStats(C.Structure):
+    _fields_ = [("max_jacobi_sweeps", C.c_int), ("max_cholqr_tries", C.c_int), ("online_shift", C.c_float),
+                ("online_blocks", C.c_int)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("n_solves", C.c_int64), ("total_iters", C.c_int64), ("max_iters", C.c_int),
                 ("max_refinements", C.c_int), ("n_not_converged", C.c_int), ("unknown_iters", C.c_int64)]
@@ -72,6 +77,8 @@ SIGNATURES = {
     "msp_basis_info": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_d)]),
     "msp_get_basis": (_i, [_vp, _i, _vp, _vp]),
     "msp_online_counts": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
+    "msp_basis_get_stats": (_i, [_vp, C.POINTER(BasisStats)]),
+    "msp_basis_set_preconditioner": (_i, [_vp, _i]),
     "msp_online_solve": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
 }
 

@@ -66,3 +66,22 @@ extern "C" msp_status msp_online_solve(msp_basis b, const double* phi, int batch
     if (batch == 0) return MSP_OK;
     return online_solve(b->B, phi, batch, tol, max_iter, u, c_dev, iters_host, (cudaStream_t)stream);
 }
+
+extern "C" msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out) {
+    clear_error();
+    MSP_CHECK_ARG(b && out, "msp_basis_get_stats: NULL argument");
+    out->max_jacobi_sweeps = b->B.max_jacobi_sweeps;
+    out->max_cholqr_tries = b->B.max_cholqr_tries;
+    out->online_shift = b->B.bt_shift;
+    out->online_blocks = b->B.bt_q;
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_basis_set_preconditioner(msp_basis b, int kind) {
+    clear_error();
+    MSP_CHECK_ARG(b, "msp_basis_set_preconditioner: NULL basis");
+    MSP_CHECK_ARG(kind == MSP_PRECOND_BLOCK_ROWS || kind == MSP_PRECOND_PATCH_BLOCKS,
+                  "msp_basis_set_preconditioner: unknown preconditioner");
+    b->B.use_block_jacobi = (kind == MSP_PRECOND_PATCH_BLOCKS);
+    return MSP_OK;
+}

@@ -1,22 +1,34 @@
-// Batched small dense linear algebra in FP64 used by the basis extraction and
-// the online preconditioner: per-matrix descriptors, one launch per batch.
+// Batched small dense linear algebra used by the basis extraction and the online
+// factorisation: per-matrix descriptors, one launch per batch.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace msp {
 
-// C (M x N) = op(A) (M x K) * B (K x N), column-major, op(A) = A or A^T.
-struct GemmDesc {
-    const double* A;
-    const double* B;
-    double* C;
+// C (M x N) = alpha op(A) op(B) + beta C, column-major; op(X) = X or X^T.
+// op(A) is M x K, op(B) is K x N.  With beta == 0, C is not read.
+template <class T>
+struct GemmDescT {
+    const T* A;
+    const T* B;
+    T* C;
     int M, N, K;
     int lda, ldb, ldc;
+    T alpha, beta;
 };
+using GemmDesc = GemmDescT<double>;
 
-// Launch a batched GEMM.  transA selects op(A) = A^T.  max_m, max_n bound the
-// batch's M and N (grid size).  Descriptors live in device memory.
-void gemm_batched(const GemmDesc* descs_dev, int batch, int max_m, int max_n, bool transA, cudaStream_t s);
+// Launch a batched GEMM over descriptors in device memory.  max_m, max_n bound
+// the batch's M and N (grid size).  C may alias A only when every CTA covers all
+// of N (N <= 64): each output tile then reads its rows of A before writing them.
+template <class T>
+void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n, bool transA, bool transB,
+                  cudaStream_t s);
+
+// Backwards-compatible FP64 entry (op(B) = B).
+inline void gemm_batched(const GemmDesc* descs_dev, int batch, int max_m, int max_n, bool transA, cudaStream_t s) {
+    gemm_batched<double>(descs_dev, batch, max_m, max_n, transA, false, s);
+}
 
 }  // namespace msp

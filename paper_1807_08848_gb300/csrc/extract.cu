@@ -121,8 +121,11 @@ __global__ void jacobi_init_kernel(const SmallMat* mats, const double* T, double
 // every pair is orthogonal to relative level tol; V accumulates the rotations.
 // Pairs follow the round-robin tournament order (c/2 disjoint pairs per step,
 // one warp per pair).  Afterwards W = U S and T^T = U S V^T, so V holds the
-// left singular vectors of T.
-__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, double* W, double* V, int max_sweeps,
+// left singular vectors of T.  Run in FP32 first (the bulk of the sweeps at the
+// FP32 rate), then, after re-orthonormalising V in FP64, in FP64 from W = T^T V
+// (a few sweeps: the columns start orthogonal to FP32 level).
+template <class R>
+__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, R* W, R* V, int max_sweeps, R tol_rel,
                                                          int* sweeps_out) {
     const SmallMat S = mats[blockIdx.x];
     const int c = S.c;
@@ -130,11 +133,26 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
         if (threadIdx.x == 0) sweeps_out[blockIdx.x] = 0;
         return;
     }
-    double* w = W + S.off;
-    double* v = V + S.off;
+    R* w = W + S.off;
+    R* v = V + S.off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int np = c + (c & 1);   // players, even
-    const double tol = fmax(1e-15, 2.2e-16 * c);
+    const R tol = tol_rel;
+    // columns below u |T|_F are numerically zero: their mutual orthogonality is
+    // rounding noise, so pairs involving them are left alone
+    __shared__ R s_fro;
+    if (warp == 0) {
+        R a = 0;
+        for (long long e = lane; e < (long long)c * c; e += 32) a += w[e] * w[e];
+        a = warp_sum(a);
+        if (lane == 0) s_fro = a;
+    }
+    __syncthreads();
+    const R eps = sizeof(R) == 8 ? (R)1.1102230246251565e-16 : (R)5.9604645e-8;
+    const R negligible = eps * eps * s_fro;   // (u |T|_F)^2
+    // rounding floor of an inner product of columns of norms a and b: the columns
+    // carry absolute errors ~ c u |T|_F, so orthogonality below that is noise
+    const R floor_abs = R(2) * c * eps * sqrt(s_fro);
     __shared__ int s_rot;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
@@ -147,11 +165,11 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
                 else { a = (r + pr) % (np - 1); b = (r - pr + (np - 1)) % (np - 1); }
                 if (a >= c || b >= c) continue;
                 const int p = min(a, b), q = max(a, b);
-                double* wp = w + (long long)p * c;
-                double* wq = w + (long long)q * c;
-                double al = 0.0, be = 0.0, ga = 0.0;
+                R* wp = w + (long long)p * c;
+                R* wq = w + (long long)q * c;
+                R al = 0, be = 0, ga = 0;
                 for (int i = lane; i < c; i += 32) {
-                    const double x = wp[i], y = wq[i];
+                    const R x = wp[i], y = wq[i];
                     al += x * x;
                     be += y * y;
                     ga += x * y;
@@ -159,19 +177,20 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
                 al = warp_sum(al);
                 be = warp_sum(be);
                 ga = warp_sum(ga);
-                if (al == 0.0 || be == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                const R na = sqrt(al), nb = sqrt(be);
+                if (al <= negligible || be <= negligible || fabs(ga) <= tol * na * nb + floor_abs * (na + nb)) continue;
+                const R zeta = (be - al) / (R(2) * ga);
+                const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+                const R cs = R(1) / sqrt(R(1) + t * t), sn = cs * t;
                 for (int i = lane; i < c; i += 32) {
-                    const double x = wp[i], y = wq[i];
+                    const R x = wp[i], y = wq[i];
                     wp[i] = cs * x - sn * y;
                     wq[i] = sn * x + cs * y;
                 }
-                double* vp = v + (long long)p * c;
-                double* vq = v + (long long)q * c;
+                R* vp = v + (long long)p * c;
+                R* vq = v + (long long)q * c;
                 for (int i = lane; i < c; i += 32) {
-                    const double x = vp[i], y = vq[i];
+                    const R x = vp[i], y = vq[i];
                     vp[i] = cs * x - sn * y;
                     vq[i] = sn * x + cs * y;
                 }
@@ -183,6 +202,19 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
         __syncthreads();
     }
     if (threadIdx.x == 0) sweeps_out[blockIdx.x] = sweep;
+}
+
+// precision conversions of the c x c work matrices
+__global__ void to_f32_mats_kernel(const SmallMat* mats, const double* src, float* dst, int identity) {
+    const SmallMat S = mats[blockIdx.x];
+    for (long long e = threadIdx.x; e < (long long)S.c * S.c; e += blockDim.x) {
+        const int i = (int)(e % S.c), j = (int)(e / S.c);
+        dst[S.off + e] = identity ? (i == j ? 1.f : 0.f) : (float)src[S.off + e];
+    }
+}
+__global__ void to_f64_mats_kernel(const SmallMat* mats, const float* src, double* dst) {
+    const SmallMat S = mats[blockIdx.x];
+    for (long long e = threadIdx.x; e < (long long)S.c * S.c; e += blockDim.x) dst[S.off + e] = (double)src[S.off + e];
 }
 
 // Column norms of W = singular values; sort descending (rank by comparison);
@@ -380,7 +412,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         for (int m = 0; m < np; ++m) {
             const long long so_ = M.patches[m].snap_offset;
             gd[m] = GemmDesc{X + so_, X + so_, G.p + mats[m].off, mats[m].c, mats[m].c, mats[m].n,
-                             mats[m].n, mats[m].n, mats[m].c};
+                             mats[m].n, mats[m].n, mats[m].c, 1.0, 0.0};
         }
         MSP_TRY(run_gemm(true, maxc, maxc));
         chol_factor_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p, L.p, F.p, Fi.p, shift_scale.p, pass == 0, status.p);
@@ -388,6 +420,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         MSP_CUDA(cudaGetLastError());
         MSP_CUDA(cudaMemcpyAsync(hstat.data(), status.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
+        for (int m = 0; m < np; ++m) B.max_cholqr_tries = std::max(B.max_cholqr_tries, hstat[m]);
         for (int m = 0; m < np; ++m)
             if (hstat[m] < 0) {
                 set_error("msp_extract_basis: Cholesky-QR breakdown on patch " + std::to_string(m) + " (pass " +
@@ -398,7 +431,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         for (int m = 0; m < np; ++m) {
             const long long so_ = M.patches[m].snap_offset;
             gd[m] = GemmDesc{X + so_, Fi.p + mats[m].off, Y + so_, mats[m].n, mats[m].c, mats[m].c,
-                             mats[m].n, mats[m].c, mats[m].n};
+                             mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
         }
         MSP_TRY(run_gemm(false, maxn, maxc));
         // T accumulation: Tacc <- F Tacc
@@ -409,7 +442,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         } else {
             for (int m = 0; m < np; ++m)
                 gd[m] = GemmDesc{F.p + mats[m].off, Tacc + mats[m].off, Tnew + mats[m].off, mats[m].c, mats[m].c,
-                                 mats[m].c, mats[m].c, mats[m].c, mats[m].c};
+                                 mats[m].c, mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
             MSP_TRY(run_gemm(false, maxc, maxc));
             std::swap(Tacc, Tnew);
         }
@@ -418,16 +451,52 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     // ---- SVD of the triangular factor
     MSP_TRY(W.alloc(mo, s));
     MSP_TRY(V.alloc(mo, s));
-    jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
-    count_launches(1);
-    jacobi_svd_kernel<<<np, 512, 0, s>>>(d_mats.p, W.p, V.p, 60, sweeps.p);
-    count_launches(1);
+    {
+        DevBuf<float> W32, V32;
+        MSP_TRY(W32.alloc(mo, s));
+        MSP_TRY(V32.alloc(mo, s));
+        // FP32 sweeps on T^T
+        jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
+        count_launches(1);
+        to_f32_mats_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, W32.p, 0);
+        count_launches(1);
+        to_f32_mats_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, V32.p, 1);
+        count_launches(1);
+        jacobi_svd_kernel<float><<<np, 512, 0, s>>>(d_mats.p, W32.p, V32.p, 40, (float)(2.0 * maxc * 5.96e-8), sweeps.p);
+        count_launches(1);
+        // V <- V32 re-orthonormalised in FP64 (Cholesky-QR: G = V^T V, V <- V L^{-T})
+        to_f64_mats_kernel<<<np, 256, 0, s>>>(d_mats.p, V32.p, L.p);
+        count_launches(1);
+        for (int m = 0; m < np; ++m)
+            gd[m] = GemmDesc{L.p + mats[m].off, L.p + mats[m].off, G.p + mats[m].off, mats[m].c, mats[m].c, mats[m].c,
+                             mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
+        MSP_TRY(run_gemm(true, maxc, maxc));
+        chol_factor_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p, W.p, F.p, Fi.p, shift_scale.p, 0, status.p);
+        count_launches(1);
+        for (int m = 0; m < np; ++m)
+            gd[m] = GemmDesc{L.p + mats[m].off, Fi.p + mats[m].off, V.p + mats[m].off, mats[m].c, mats[m].c, mats[m].c,
+                             mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
+        MSP_TRY(run_gemm(false, maxc, maxc));
+        // W = T^T V, then FP64 sweeps
+        for (int m = 0; m < np; ++m)
+            gd[m] = GemmDesc{Tacc + mats[m].off, V.p + mats[m].off, W.p + mats[m].off, mats[m].c, mats[m].c, mats[m].c,
+                             mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
+        MSP_TRY(run_gemm(true, maxc, maxc));
+        jacobi_svd_kernel<double><<<np, 512, 0, s>>>(d_mats.p, W.p, V.p, 30, maxc * 1.12e-16, sweeps.p);
+        count_launches(1);
+    }
     sort_truncate_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, tau, sig_tmp.p, sig.p, d_sig_off.p, order.p, kdev.p);
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
     B.k.resize(np);
     B.sigma.resize(so);
     B.sigma_off = sig_off;
+    {
+        std::vector<int> sw(np);
+        MSP_CUDA(cudaMemcpyAsync(sw.data(), sweeps.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        for (int v : sw) B.max_jacobi_sweeps = std::max(B.max_jacobi_sweeps, v);
+    }
     MSP_CUDA(cudaMemcpyAsync(B.k.data(), kdev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
     MSP_CUDA(cudaMemcpyAsync(B.sigma.data(), sig.p, sizeof(double) * so, cudaMemcpyDeviceToHost, s));
     MSP_CUDA(cudaStreamSynchronize(s));
@@ -452,7 +521,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     for (int m = 0; m < np; ++m) {
         const long long so_ = M.patches[m].snap_offset;
         gd[m] = GemmDesc{X + so_, G.p + mats[m].off, B.Q.p + B.q_off[m], mats[m].n, B.k[m], mats[m].c,
-                         mats[m].n, mats[m].c, mats[m].n};
+                         mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
     }
     MSP_TRY(run_gemm(false, maxn, std::max(maxk, 1)));
 
@@ -570,6 +639,8 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
             set_error("msp_extract_basis: preconditioner block of patch " + std::to_string(m) + " is not positive definite");
             return MSP_ERR_BREAKDOWN;
         }
+    // ---- block-tridiagonal factor of the scaled normal matrix (online preconditioner)
+    MSP_TRY(build_online_factor(B, row_ptr, row_slot, s));
     return MSP_OK;
 }
 

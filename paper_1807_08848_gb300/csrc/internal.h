@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/msp.h"
+#include "dense.cuh"
 
 namespace msp {
 
@@ -133,6 +134,22 @@ struct Basis {
     int cap_batch = 0;
     DevBuf<double> w_c, w_p, w_z, w_e, w_q, w_r, w_part, w_scal;
     DevBuf<int> w_iters;
+    // block-tridiagonal FP32 factor of the scaled normal matrix (online preconditioner)
+    int bt_q = 0;
+    std::vector<int> bt_off;            // first unknown of each row of patches
+    std::vector<long long> bt_d_off;    // diagonal block offsets
+    std::vector<long long> bt_e_off;    // sub-diagonal block offsets
+    long long bt_diag_elems = 0;
+    float bt_shift = 0.f;
+    DevBuf<double> bt_Ds;               // diagonal scaling diag(H)^(-1/2)
+    DevBuf<float> bt_F;                 // L_q (diagonal blocks), C_q (sub-diagonal blocks)
+    DevBuf<float> bt_Li;                // L_q^{-1}
+    DevBuf<float> bt_FT, bt_LiT;        // transposed copies (contiguous columns for the sweeps)
+    DevBuf<float> bt_w1, bt_w2;         // sweep work vectors
+    DevBuf<GemmDescT<float>> bt_desc;
+    DevBuf<double> w_s;                 // normal-equation residual s = P^T r
+    bool use_block_jacobi = false;      // online preconditioner: patch blocks only
+    int max_jacobi_sweeps = 0, max_cholqr_tries = 0;
     int device = 0;
 };
 
@@ -156,6 +173,9 @@ msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst,
 msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B);
 msp_status online_solve(Basis& B, const double* phi, int batch, double tol, int max_iter, double* u, double* c_out,
                         int* iters_host, cudaStream_t s);
+msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const std::vector<int>& row_slot,
+                               cudaStream_t s);
+msp_status apply_online_factor(Basis& B, const double* s_in, double* z_out, int Bsz, cudaStream_t s);
 
 int num_sms();
 

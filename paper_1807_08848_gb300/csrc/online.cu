@@ -176,6 +176,49 @@ __global__ void normal_precond_kernel(OnArgs A, const double* r, double* z, doub
     }
 }
 
+// s = P~^T r per patch (gather the rows of every edge slot, then E_m^T); [element][B]
+__global__ void normal_rhs_kernel(OnArgs A, const double* r, double* sout) {
+    extern __shared__ double sm[];
+    const int m = blockIdx.x, k = A.k[m], ns = 2 * A.ne[m], B = A.B;
+    double* t = sm;   // [ns][B]
+    const int g0 = A.slot_off[m];
+    for (int w = threadIdx.x; w < ns * B; w += blockDim.x) {
+        const int s = w / B, b = w - s * B;
+        double a = 0.0;
+        for (int u = A.tr_ptr[g0 + s]; u < A.tr_ptr[g0 + s + 1]; ++u) {
+            const unsigned v = (unsigned)A.tr_ent[u];
+            const double x = r[(long long)(v & 0x7fffffffu) * B + b];
+            a += (v & 0x80000000u) ? -x : x;
+        }
+        t[w] = a;
+    }
+    __syncthreads();
+    const double* Em = A.E + A.e_off[m];
+    double* so = sout + (long long)A.c_off[m] * B;
+    for (int w = threadIdx.x; w < k * B; w += blockDim.x) {
+        const int j = w / B, b = w - j * B;
+        double a = 0.0;
+        for (int s = 0; s < ns; ++s) a += Em[(long long)s * k + j] * t[s * B + b];
+        so[w] = a;
+    }
+}
+
+// per-patch partial sums (s.z, s.s), fixed order over the patch's unknowns
+__global__ void dots_kernel(OnArgs A, const double* sv, const double* z, double* part) {
+    const int m = blockIdx.x, k = A.k[m], B = A.B;
+    const double* sm_ = sv + (long long)A.c_off[m] * B;
+    const double* zm = z + (long long)A.c_off[m] * B;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        double sz = 0.0, ss = 0.0;
+        for (int j = 0; j < k; ++j) {
+            sz += sm_[(long long)j * B + b] * zm[(long long)j * B + b];
+            ss += sm_[(long long)j * B + b] * sm_[(long long)j * B + b];
+        }
+        part[((long long)m * B + b) * 2 + 0] = sz;
+        part[((long long)m * B + b) * 2 + 1] = ss;
+    }
+}
+
 // gamma' = sum_m s.z, |s| = sqrt(sum_m s.s); convergence; beta.  mode 0: first
 // call (sets gamma and |P^T d|), mode 1: iteration.  beta goes to scal[7].
 __global__ void finalize_beta_kernel(OnArgs A, const double* part, double* scal, double tol, int max_iter, int mode) {
@@ -312,23 +355,40 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
         max_k = std::max(max_k, Bs.k[m]);
     }
     const size_t smem = sizeof(double) * ((size_t)max_ns * B + (size_t)max_k * B);
-    if (smem > 48 * 1024)
+    if (smem > 48 * 1024) {
         MSP_CUDA(cudaFuncSetAttribute(normal_precond_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MSP_CUDA(cudaFuncSetAttribute(normal_rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if (Bs.w_s.n < (size_t)nc) MSP_TRY(Bs.w_s.alloc((size_t)std::max(Bs.Np, 1) * kMaxBatch, s));
+    // z = M^{-1} P~^T r and the partial sums (s.z, s.s): block-row factor when built,
+    // patch-block (additive Schwarz) inverses otherwise
+    auto precondition = [&]() -> msp_status {
+        if (Bs.bt_q > 0 && !Bs.use_block_jacobi) {
+            normal_rhs_kernel<<<np, 256, smem, s>>>(A, Bs.w_r.p, Bs.w_s.p);
+            count_launches(1);
+            MSP_TRY(apply_online_factor(Bs, Bs.w_s.p, Bs.w_z.p, B, s));
+            dots_kernel<<<np, 64, 0, s>>>(A, Bs.w_s.p, Bs.w_z.p, Bs.w_part.p);
+            count_launches(1);
+        } else {
+            normal_precond_kernel<<<np, 256, smem, s>>>(A, Bs.w_r.p, Bs.w_z.p, Bs.w_part.p);
+            count_launches(1);
+        }
+        return MSP_OK;
+    };
     const int ew_grid = std::max(1, std::min<int>((int)((nc + nr + 255) / 256), num_sms() * 8));
     MSP_CUDA(cudaMemsetAsync(Bs.w_c.p, 0, sizeof(double) * nc, s));
     MSP_CUDA(cudaMemsetAsync(Bs.w_e.p, 0, sizeof(double) * (size_t)Bs.n_slots * B, s));
     // r = d
     rows_apply_kernel<<<A.n_chunks, kRowChunk, 0, s>>>(A, Bs.w_e.p, Bs.w_q.p, Bs.w_part.p, phi, n4, Bs.w_r.p, 1);
     count_launches(1);
-    normal_precond_kernel<<<np, 256, smem, s>>>(A, Bs.w_r.p, Bs.w_z.p, Bs.w_part.p);
-    count_launches(1);
+    MSP_TRY(precondition());
     finalize_beta_kernel<<<1, 1024, 0, s>>>(A, Bs.w_part.p, Bs.w_scal.p, tol, max_iter, 0);
     count_launches(1);
     update_p_kernel<<<ew_grid, 256, 0, s>>>(A, Bs.w_p.p, Bs.w_z.p, Bs.w_scal.p, nc, 0);
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
     std::vector<double> scal(8 * (size_t)B);
-    const int check_every = 16;
+    const int check_every = (Bs.bt_q > 0 && !Bs.use_block_jacobi) ? 2 : 16;
     for (int it = 0; it < max_iter; ++it) {
         edge_apply_kernel<<<np, 256, 0, s>>>(A, Bs.w_p.p, Bs.w_e.p);
         count_launches(1);
@@ -338,8 +398,7 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
         count_launches(1);
         update_cr_kernel<<<ew_grid, 256, 0, s>>>(A, Bs.w_c.p, Bs.w_p.p, Bs.w_r.p, Bs.w_q.p, Bs.w_scal.p, nc, nr);
         count_launches(1);
-        normal_precond_kernel<<<np, 256, smem, s>>>(A, Bs.w_r.p, Bs.w_z.p, Bs.w_part.p);
-        count_launches(1);
+        MSP_TRY(precondition());
         finalize_beta_kernel<<<1, 1024, 0, s>>>(A, Bs.w_part.p, Bs.w_scal.p, tol, max_iter, 1);
         count_launches(1);
         update_p_kernel<<<ew_grid, 256, 0, s>>>(A, Bs.w_p.p, Bs.w_z.p, Bs.w_scal.p, nc, 1);

@@ -164,14 +164,16 @@ def test_batch_invariance(small, gpu_fp64):
 
 
 def test_full_basis_reproduces_global_solve():
-    """With more samples than ring nodes and no truncation, the GPU pipeline
-    reproduces the global fine-mesh solve (the exactness of Sec. 4.2 / 5.2)."""
+    """With more samples than ring nodes and truncation only at the numerical
+    noise level (tau = 1e-10), the GPU pipeline reproduces the global fine-mesh
+    solve (the exactness of Sec. 4.2 / 5.2).  (A tau at the rounding floor would
+    keep noise directions that the edge rows do not constrain.)"""
     N = 32
     ms = synth.periodic_sin(N, 1 / 4)
     ps = synth.uniform_patches(N, 2, 2, 4, 90)
     med = msp.Medium(ms, ps)
     med.sample(3, "fp64", tol=1e-14, max_iter=5000)
-    basis = med.extract(1e-13, "fp64")
+    basis = med.extract(1e-10, "fp64")
     phi = synth.phi_fourier(N, 6, 9, kmax=3)[0]
     u, _ = basis.solve(torch.tensor(phi, device="cuda"), tol=1e-14, max_iter=50000)
     aE, aN = E.face_coefficients(ms)
