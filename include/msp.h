@@ -69,6 +69,8 @@ typedef int msp_status;
 /* Opaque handles. */
 typedef struct msp_medium_s* msp_medium;   /* medium, patches and snapshot storage  */
 typedef struct msp_basis_s* msp_basis;     /* reduced bases and online operators    */
+typedef struct msp_kmedium_s* msp_kmedium; /* kinetic slab: patches and snapshots   */
+typedef struct msp_kbasis_s* msp_kbasis;   /* kinetic reduced bases and online factor */
 
 typedef enum { MSP_FP64 = 0, MSP_MIXED = 1 } msp_precision;
 
@@ -237,6 +239,53 @@ msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_rows);
  * set hit max_iter. */
 msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
                             double* u_dev, double* c_dev, int* iters_host, void* stream);
+
+/* --------------------------------------------------------------------- kinetic */
+
+/* Slab radiative transfer with isotropic scattering (Sec. 4; Eq. RTE with the
+ * Henyey-Greenstein kernel of Eq. HG at g = 0):
+ *     v d_x f = (1/eps)(rho - f),  rho = (1/2) sum_l w_l f_l,  x in [0, 1],
+ * on nodes x_i = i/N with n_v Gauss-Legendre velocities (ascending) and implicit
+ * upwind differences; incoming data f(0, v>0) and f(1, v<0).  n_patches equal
+ * patches K_m = [m W, (m+1) W] cells (W = N/n_patches), buffered by `buffer`
+ * cells (clipped); `samples` random incoming data sets per patch.  Snapshot
+ * rows are node-major with the velocity fastest ((W+1) n_v rows).
+ * INVALID_ARG unless N is a multiple of n_patches, n_v is even in 2..256,
+ * eps > 0. */
+msp_status msp_kinetic_build(int n_cells, double eps, int n_v, int n_patches, int buffer, int samples,
+                             void* stream, msp_kmedium* out);
+void msp_kinetic_destroy(msp_kmedium k);
+/* Gauss-Legendre velocities and weights (host arrays of n_v, either may be NULL). */
+msp_status msp_kinetic_velocities(msp_kmedium k, double* v_host, double* w_host);
+
+/* RanLocalSolu for the slab (Eq. rte_random): per patch and sample, i.i.d.
+ * N(0,1) incoming data on the buffered patch (Philox4x32-10, counter = (datum
+ * pair, sample, patch, kinetic tag); data 0..n_v/2-1 are the positive velocities
+ * at the left end, the rest the negative velocities at the right end, each
+ * ascending in v), solved by source iteration (FP64 transport sweeps with the
+ * lagged density) until max|rho_new - rho| <= tol max|rho|, restricted to K_m.
+ * stats as for msp_sample_patches (synchronises when given). */
+msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, double tol, int max_iter, void* stream,
+                              msp_solve_stats* stats_host);
+/* Copy patch `patch`'s snapshot block ((W+1) n_v x samples, column-major). */
+msp_status msp_kinetic_get_snapshots(msp_kmedium k, int patch, double* dst_dev, void* stream);
+
+/* Truncated SVD bases of the snapshots (as msp_extract_basis) and the FP64
+ * block-tridiagonal factor of the normal equations of Eq. rte_cond_reduced
+ * (continuity of all velocities at every interface, incoming data at x = 0, 1).
+ * Synchronises.  BREAKDOWN if the normal matrix is not positive definite. */
+msp_status msp_kinetic_extract(msp_kmedium k, double tau, void* stream, msp_kbasis* out);
+void msp_kinetic_basis_destroy(msp_kbasis b);
+msp_status msp_kinetic_basis_info(msp_kbasis b, int patch, int* k, double* sigma_host);
+
+/* Online stage for `batch` data sets: inflow_dev [batch][2][n_v] holds, per data
+ * set, the n_v values at x = 0 (only v > 0 used) then the n_v values at x = 1
+ * (only v < 0 used).  c = argmin |P c - d| by the factorised normal equations
+ * with two corrected-semi-normal-equation steps; f_dev [batch][N+1][n_v]
+ * receives the reconstruction (patch values inside, interface averages, the
+ * incoming data at the ends); c_dev [batch][N_p] optional.  Synchronises. */
+msp_status msp_kinetic_online_solve(msp_kbasis b, const double* inflow_dev, int batch, double* f_dev, double* c_dev,
+                                    void* stream);
 
 #ifdef __cplusplus
 }

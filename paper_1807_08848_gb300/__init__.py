@@ -20,7 +20,8 @@ import torch
 from . import _native as N
 from ._native import MspError, MSP_FP64, MSP_MIXED
 
-__all__ = ["Medium", "Basis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library", "precision_code"]
+__all__ = ["Medium", "Basis", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
+           "precision_code"]
 
 
 def load_library():
@@ -216,3 +217,75 @@ class Basis:
             u = u[0]
             c = c[0] if c is not None else None
         return (u, it, c) if want_c else (u, it)
+
+
+class KineticMedium:
+    """Slab radiative transfer (isotropic scattering, discrete ordinates)."""
+
+    def __init__(self, n_cells: int, eps: float, n_v: int, n_patches: int, buffer: int, samples: int, stream=None):
+        h = C.c_void_p()
+        N.check(N.load().msp_kinetic_build(n_cells, eps, n_v, n_patches, buffer, samples, _stream_ptr(stream),
+                                           C.byref(h)))
+        self._h = h
+        self.n_cells, self.eps, self.n_v, self.n_patches, self.buffer, self.samples = (
+            n_cells, eps, n_v, n_patches, buffer, samples)
+        self.n_k = (n_cells // n_patches + 1) * n_v
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            N.load().msp_kinetic_destroy(h)
+            self._h = None
+
+    def velocities(self):
+        v = np.zeros(self.n_v); w = np.zeros(self.n_v)
+        N.check(N.load().msp_kinetic_velocities(self._h, _f64p(v), _f64p(w)))
+        return v, w
+
+    def sample(self, seed: int, tol: float = 1e-12, max_iter: int = 100000, stream=None, stats: bool = True):
+        st = N.SolveStats()
+        N.check(N.load().msp_kinetic_sample(self._h, C.c_uint64(seed), tol, max_iter, _stream_ptr(stream),
+                                            C.byref(st) if stats else None))
+        return st if stats else None
+
+    def snapshots(self, m: int, stream=None) -> torch.Tensor:
+        t = torch.empty((self.samples, self.n_k), dtype=torch.float64, device="cuda")
+        N.check(N.load().msp_kinetic_get_snapshots(self._h, m, _dptr(t), _stream_ptr(stream)))
+        return t.T
+
+    def extract(self, tau: float = 1e-6, stream=None) -> "KineticBasis":
+        h = C.c_void_p()
+        N.check(N.load().msp_kinetic_extract(self._h, tau, _stream_ptr(stream), C.byref(h)))
+        return KineticBasis(h, self)
+
+
+class KineticBasis:
+    def __init__(self, handle, medium: KineticMedium):
+        self._h = handle
+        self.n_cells, self.n_v, self.n_patches, self.samples = medium.n_cells, medium.n_v, medium.n_patches, medium.samples
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            N.load().msp_kinetic_basis_destroy(h)
+            self._h = None
+
+    def k(self, m: int) -> int:
+        k = C.c_int()
+        N.check(N.load().msp_kinetic_basis_info(self._h, m, C.byref(k), None))
+        return k.value
+
+    def sigma(self, m: int) -> np.ndarray:
+        out = np.zeros(self.samples)
+        k = C.c_int()
+        N.check(N.load().msp_kinetic_basis_info(self._h, m, C.byref(k), _f64p(out)))
+        return out
+
+    def solve(self, inflow: torch.Tensor, stream=None) -> torch.Tensor:
+        """inflow: (B, 2, n_v) or (2, n_v) -- values at x = 0 then at x = 1."""
+        squeeze = inflow.dim() == 2
+        inflow = inflow.reshape(-1, 2, self.n_v).to(dtype=torch.float64, device="cuda").contiguous()
+        B = inflow.shape[0]
+        f = torch.empty((B, self.n_cells + 1, self.n_v), dtype=torch.float64, device="cuda")
+        N.check(N.load().msp_kinetic_online_solve(self._h, _dptr(inflow), B, _dptr(f), None, _stream_ptr(stream)))
+        return f[0] if squeeze else f

@@ -79,6 +79,15 @@ SIGNATURES = {
     "msp_online_counts": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
     "msp_basis_get_stats": (_i, [_vp, C.POINTER(BasisStats)]),
     "msp_basis_set_preconditioner": (_i, [_vp, _i]),
+    "msp_kinetic_build": (_i, [_i, _d, _i, _i, _i, _i, _vp, C.POINTER(_vp)]),
+    "msp_kinetic_destroy": (None, [_vp]),
+    "msp_kinetic_velocities": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
+    "msp_kinetic_sample": (_i, [_vp, _u64, _d, _i, _vp, C.POINTER(SolveStats)]),
+    "msp_kinetic_get_snapshots": (_i, [_vp, _i, _vp, _vp]),
+    "msp_kinetic_extract": (_i, [_vp, _d, _vp, C.POINTER(_vp)]),
+    "msp_kinetic_basis_destroy": (None, [_vp]),
+    "msp_kinetic_basis_info": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_d)]),
+    "msp_kinetic_online_solve": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "msp_online_solve": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
 }
 

@@ -351,24 +351,29 @@ int domain_ring_pos(int N, int i, int j) {
 
 }  // namespace
 
-msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B) {
-    (void)precision;
-    const int np = (int)M.patches.size();
-    B.N = M.N; B.mx = M.mx; B.my = M.my; B.xb = M.xb; B.yb = M.yb; B.patches = M.patches;
-    B.device = M.device;
+// Orthonormal bases of the snapshot blocks (n_rows[m] x cols[m], column-major at
+// snaps + snap_off[m]): shifted Cholesky-QR3, SVD of the triangular factor,
+// truncation at tau sigma_1.  Outputs the kept counts, all singular values
+// (descending) and the bases (n_rows x k blocks at q_off) in Q.
+msp_status svd_bases(const double* snaps, long long snap_elems, const std::vector<long long>& snap_off,
+                     const std::vector<int>& n_rows, const std::vector<int>& cols, double tau, cudaStream_t s,
+                     DevBuf<double>& Q, std::vector<int>& k, std::vector<double>& sigma,
+                     std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries) {
+    const int np = (int)cols.size();
+    max_sweeps = 0;
+    max_tries = 0;
     // ---- small-matrix layout
     std::vector<SmallMat> mats(np);
     std::vector<long long> sig_off(np);
     long long mo = 0, so = 0;
     int maxc = 0, maxn = 0;
     for (int m = 0; m < np; ++m) {
-        const PatchDev& P = M.patches[m];
-        mats[m] = SmallMat{mo, P.cols, P.n_k};
-        mo += (long long)P.cols * P.cols;
+        mats[m] = SmallMat{mo, cols[m], n_rows[m]};
+        mo += (long long)cols[m] * cols[m];
         sig_off[m] = so;
-        so += P.cols;
-        maxc = std::max(maxc, P.cols);
-        maxn = std::max(maxn, P.n_k);
+        so += cols[m];
+        maxc = std::max(maxc, cols[m]);
+        maxn = std::max(maxn, n_rows[m]);
     }
     DevBuf<SmallMat> d_mats;
     DevBuf<long long> d_sig_off;
@@ -379,7 +384,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     DevBuf<double> shift_scale;
     MSP_TRY(G.alloc(mo, s)); MSP_TRY(L.alloc(mo, s)); MSP_TRY(F.alloc(mo, s)); MSP_TRY(Fi.alloc(mo, s));
     MSP_TRY(T0.alloc(mo, s)); MSP_TRY(T1.alloc(mo, s));
-    MSP_TRY(ping.alloc(M.snap_elems, s)); MSP_TRY(pong.alloc(M.snap_elems, s));
+    MSP_TRY(ping.alloc(snap_elems, s)); MSP_TRY(pong.alloc(snap_elems, s));
     MSP_TRY(sig_tmp.alloc(so, s)); MSP_TRY(sig.alloc(so, s));
     MSP_TRY(order.alloc(so, s)); MSP_TRY(kdev.alloc(np, s)); MSP_TRY(status.alloc(np, s)); MSP_TRY(sweeps.alloc(np, s));
     {
@@ -401,7 +406,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         MSP_CUDA(cudaStreamSynchronize(s));   // descriptors are reused
         return MSP_OK;
     };
-    const double* X = M.snaps.p;
+    const double* X = snaps;
     double* Tacc = T0.p;
     double* Tnew = T1.p;
     double* outs[3] = {ping.p, pong.p, ping.p};
@@ -410,7 +415,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         double* Y = outs[pass];
         // Gram G = X^T X
         for (int m = 0; m < np; ++m) {
-            const long long so_ = M.patches[m].snap_offset;
+            const long long so_ = snap_off[m];
             gd[m] = GemmDesc{X + so_, X + so_, G.p + mats[m].off, mats[m].c, mats[m].c, mats[m].n,
                              mats[m].n, mats[m].n, mats[m].c, 1.0, 0.0};
         }
@@ -420,16 +425,16 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         MSP_CUDA(cudaGetLastError());
         MSP_CUDA(cudaMemcpyAsync(hstat.data(), status.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
-        for (int m = 0; m < np; ++m) B.max_cholqr_tries = std::max(B.max_cholqr_tries, hstat[m]);
+        for (int m = 0; m < np; ++m) max_tries = std::max(max_tries, hstat[m]);
         for (int m = 0; m < np; ++m)
             if (hstat[m] < 0) {
-                set_error("msp_extract_basis: Cholesky-QR breakdown on patch " + std::to_string(m) + " (pass " +
+                set_error("basis extraction: Cholesky-QR breakdown on patch " + std::to_string(m) + " (pass " +
                           std::to_string(pass) + ")");
                 return MSP_ERR_BREAKDOWN;
             }
         // Y = X Fi
         for (int m = 0; m < np; ++m) {
-            const long long so_ = M.patches[m].snap_offset;
+            const long long so_ = snap_off[m];
             gd[m] = GemmDesc{X + so_, Fi.p + mats[m].off, Y + so_, mats[m].n, mats[m].c, mats[m].c,
                              mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
         }
@@ -488,42 +493,74 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     sort_truncate_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, tau, sig_tmp.p, sig.p, d_sig_off.p, order.p, kdev.p);
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
-    B.k.resize(np);
-    B.sigma.resize(so);
-    B.sigma_off = sig_off;
+    k.resize(np);
+    sigma.resize(so);
+    sigma_off = sig_off;
     {
         std::vector<int> sw(np);
         MSP_CUDA(cudaMemcpyAsync(sw.data(), sweeps.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
-        for (int v : sw) B.max_jacobi_sweeps = std::max(B.max_jacobi_sweeps, v);
+        for (int v : sw) max_sweeps = std::max(max_sweeps, v);
     }
-    MSP_CUDA(cudaMemcpyAsync(B.k.data(), kdev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
-    MSP_CUDA(cudaMemcpyAsync(B.sigma.data(), sig.p, sizeof(double) * so, cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaMemcpyAsync(k.data(), kdev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaMemcpyAsync(sigma.data(), sig.p, sizeof(double) * so, cudaMemcpyDeviceToHost, s));
     MSP_CUDA(cudaStreamSynchronize(s));
     // ---- Q_m = Q3 U_T[:, :k]
-    B.q_off.resize(np);
-    B.c_off.resize(np + 1);
+    q_off.resize(np);
     long long qo = 0;
-    int co = 0, maxk = 0;
+    int maxk = 0;
     for (int m = 0; m < np; ++m) {
-        B.q_off[m] = qo;
-        qo += (long long)M.patches[m].n_k * B.k[m];
-        B.c_off[m] = co;
-        co += B.k[m];
-        maxk = std::max(maxk, B.k[m]);
+        q_off[m] = qo;
+        qo += (long long)n_rows[m] * k[m];
+        maxk = std::max(maxk, k[m]);
     }
-    B.c_off[np] = co;
-    B.Np = co;
-    MSP_TRY(B.Q.alloc(std::max<long long>(qo, 1), s));
+    MSP_TRY(Q.alloc(std::max<long long>(qo, 1), s));
     gather_uk_kernel<<<np, 256, 0, s>>>(d_mats.p, V.p, order.p, d_sig_off.p, kdev.p, G.p);   // Uk into G
     MSP_CUDA(cudaGetLastError());
     count_launches(1);
     for (int m = 0; m < np; ++m) {
-        const long long so_ = M.patches[m].snap_offset;
-        gd[m] = GemmDesc{X + so_, G.p + mats[m].off, B.Q.p + B.q_off[m], mats[m].n, B.k[m], mats[m].c,
+        const long long so_ = snap_off[m];
+        gd[m] = GemmDesc{X + so_, G.p + mats[m].off, Q.p + q_off[m], mats[m].n, k[m], mats[m].c,
                          mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
     }
     MSP_TRY(run_gemm(false, maxn, std::max(maxk, 1)));
+    return MSP_OK;
+}
+
+msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B) {
+    (void)precision;
+    const int np = (int)M.patches.size();
+    B.N = M.N; B.mx = M.mx; B.my = M.my; B.xb = M.xb; B.yb = M.yb; B.patches = M.patches;
+    B.device = M.device;
+    {
+        std::vector<long long> snap_off(np);
+        std::vector<int> n_rows(np), cols(np);
+        for (int m = 0; m < np; ++m) {
+            snap_off[m] = M.patches[m].snap_offset;
+            n_rows[m] = M.patches[m].n_k;
+            cols[m] = M.patches[m].cols;
+        }
+        MSP_TRY(svd_bases(M.snaps.p, M.snap_elems, snap_off, n_rows, cols, tau, s, B.Q, B.k, B.sigma, B.sigma_off, B.q_off,
+                          B.max_jacobi_sweeps, B.max_cholqr_tries));
+    }
+    B.c_off.resize(np + 1);
+    int co = 0;
+    for (int m = 0; m < np; ++m) {
+        B.c_off[m] = co;
+        co += B.k[m];
+    }
+    B.c_off[np] = co;
+    B.Np = co;
+    // G as scratch for the precondtioner blocks below
+    long long mo = 0;
+    for (int m = 0; m < np; ++m) mo += (long long)M.patches[m].cols * M.patches[m].cols;
+    DevBuf<double> G, L, F, Fi, shift_scale;
+    DevBuf<int> status;
+    MSP_TRY(G.alloc(mo, s)); MSP_TRY(L.alloc(mo, s)); MSP_TRY(F.alloc(mo, s)); MSP_TRY(Fi.alloc(mo, s));
+    MSP_TRY(shift_scale.alloc(np, s));
+    MSP_TRY(status.alloc(np, s));
+    std::vector<int> hstat(np);
+
 
     // ---- online tables (host): skeleton nodes, rows of P~, transpose lists
     const int N = M.N;
