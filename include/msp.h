@@ -188,6 +188,32 @@ msp_status msp_get_snapshots(msp_medium m, int patch, double* dst_dev, void* str
  * column-major, to dst_dev (for checking the generator). */
 msp_status msp_get_samples(msp_medium m, int patch, uint64_t seed, double* dst_dev, void* stream);
 
+/* Local solves of ONE patch without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory while it runs -- code working inside a memory pool it does not own, a
+ * framework that forbids allocation on its hot path, or a process whose
+ * allocator is already at its limit.  The caller passes every input and output:
+ *   aE_dev, aN_dev  face coefficients of the medium ((N+1) x N and N x (N+1),
+ *                   e.g. from msp_get_coefficients);
+ *   boxes_host      x0, x1, y0, y1 of K_m then X0, X1, Y0, Y1 of the buffered
+ *                   box (closed node boxes, 0 <= X0 <= x0 < x1 <= X1 <= N);
+ *   patch_index     the patch's index m in the Philox counter (same samples as
+ *                   msp_sample_patches draws for patch m);
+ *   samples         Gaussian columns, 1..4096 (no boundary-delta columns);
+ *   snap_dev        output, n_k x samples doubles, column-major.
+ * Its scratch lives in one file-scope device array of 32 MiB that every GPU
+ * loading the library holds until the process exits; a buffered patch whose
+ * interior exceeds the on-chip tile (98 columns, 12 rows per thread segment)
+ * or whose per-block scratch does not fit is rejected with INVALID_ARG.  The
+ * first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call shares
+ * the array and leaves its contents behind: calls that overlap on the GPU
+ * (concurrent streams, several threads) race and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
+msp_status msp_sample_patch_static(const double* aE_dev, const double* aN_dev, int n_cells, const int* boxes_host,
+                                   int patch_index, int samples, uint64_t seed, int precision, double tol,
+                                   int max_iter, double* snap_dev, void* stream);
+
 /* Orthonormal basis of every patch's snapshot range (Sec. 3.2, Eq. svd):
  * shifted Cholesky-QR3 of the snapshot block, SVD of its triangular factor by
  * one-sided Jacobi, truncation k_m = #{sigma_i > tau sigma_1}; basis

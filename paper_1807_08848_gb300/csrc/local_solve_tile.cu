@@ -29,6 +29,8 @@
 #include "device_util.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace msp {
 
@@ -55,6 +57,7 @@ struct TileArgs {
     double* scratch;          // per CTA slot, see slot layout below
     long long slot_doubles;
     int* stats;
+    int one_patch_index;      // random stream index of the patch (one-patch variant)
 };
 
 // Thread mapping of an nx x ny interior: strips of 32 columns, segments of rps rows.
@@ -95,7 +98,9 @@ __device__ __forceinline__ T block_sum1(T v, T* buf) {
     return a[0];
 }
 
-template <class T, int RPS>
+// ONE_PATCH: every item is column `item` of the single patch A.patches[0] whose
+// random stream index is A.one_patch_index (the variant without allocations).
+template <class T, int RPS, bool ONE_PATCH = false>
 __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) {
     constexpr bool kF32 = sizeof(T) == 4;
     constexpr int PI = kPitch;
@@ -111,9 +116,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) 
         __syncthreads();
         const int item = s_item;
         if (item >= A.n_items) break;
-        const int2 itm = A.items[item];
-        const int m = itm.x, col = itm.y;
-        const PatchDev P = A.patches[m];
+        int m, col;
+        if constexpr (ONE_PATCH) {
+            m = A.one_patch_index;
+            col = item;
+        } else {
+            const int2 itm = A.items[item];
+            m = itm.x;
+            col = itm.y;
+        }
+        const PatchDev P = A.patches[ONE_PATCH ? 0 : m];
         const int W = P.X1 - P.X0 + 1, H = P.Y1 - P.Y0 + 1;
         const int nx = W - 2, ny = H - 2;
         Mapping mp;
@@ -511,3 +523,142 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
 }
 
 }  // namespace msp
+
+// ---------------------------------------------------------------------------
+// Local solves of one patch without any allocation.
+//
+// Some callers cannot allocate device memory while they run this step: code
+// that works inside a memory pool it does not own, a framework that forbids
+// allocation on its hot path, or a process whose allocator is already at its
+// limit.  msp_sample_patch_static takes every input and output from the caller
+// and keeps its per-CTA scratch (FP64 iterate and coefficient copies, the work
+// counter, the per-column statistics and the patch description) in one
+// file-scope device array of kStaticScratchBytes.  That array exists once per
+// device that loads the library and stays allocated until the process exits.
+// ---------------------------------------------------------------------------
+namespace msp {
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32u << 20;      // 32 MiB
+constexpr size_t kStaticHeaderBytes = 64u << 10;       // counter, patch, statistics
+constexpr int kStaticMaxColumns = 4096;                // 3 ints of statistics per column
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// device address of g_static_scratch per device, found once with the device current
+std::mutex g_static_mutex;
+std::vector<void*> g_static_addr;
+
+msp_status static_scratch_address(void** out) {
+    int dev = 0;
+    MSP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if ((int)g_static_addr.size() <= dev) g_static_addr.resize(dev + 1, nullptr);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        MSP_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return MSP_OK;
+}
+
+}  // namespace
+}  // namespace msp
+
+extern "C" msp_status msp_sample_patch_static(const double* aE_dev, const double* aN_dev, int n_cells,
+                                              const int* boxes_host, int patch_index, int samples, uint64_t seed,
+                                              int precision, double tol, int max_iter, double* snap_dev, void* stream) {
+    using namespace msp;
+    clear_error();
+    MSP_CHECK_ARG(aE_dev && aN_dev && boxes_host && snap_dev, "msp_sample_patch_static: NULL argument");
+    MSP_CHECK_ARG(n_cells >= 2, "msp_sample_patch_static: n_cells must be >= 2");
+    MSP_CHECK_ARG(precision == MSP_FP64 || precision == MSP_MIXED, "msp_sample_patch_static: unknown precision");
+    MSP_CHECK_ARG(tol > 0 && tol < 1 && max_iter >= 1, "msp_sample_patch_static: tol in (0,1), max_iter >= 1");
+    MSP_CHECK_ARG(samples >= 1 && samples <= kStaticMaxColumns,
+                  "msp_sample_patch_static: samples must lie in [1, 4096]");
+    MSP_CHECK_ARG(patch_index >= 0, "msp_sample_patch_static: patch_index must be >= 0");
+    PatchDev P{};
+    P.x0 = boxes_host[0]; P.x1 = boxes_host[1]; P.y0 = boxes_host[2]; P.y1 = boxes_host[3];
+    P.X0 = boxes_host[4]; P.X1 = boxes_host[5]; P.Y0 = boxes_host[6]; P.Y1 = boxes_host[7];
+    MSP_CHECK_ARG(0 <= P.X0 && P.X0 <= P.x0 && P.x0 < P.x1 && P.x1 <= P.X1 && P.X1 <= n_cells && 0 <= P.Y0 &&
+                      P.Y0 <= P.y0 && P.y0 < P.y1 && P.y1 <= P.Y1 && P.Y1 <= n_cells,
+                  "msp_sample_patch_static: boxes must satisfy 0 <= X0 <= x0 < x1 <= X1 <= N (and in y)");
+    P.n_k = (P.x1 - P.x0 + 1) * (P.y1 - P.y0 + 1);
+    P.n_ring = 2 * (P.X1 - P.X0) + 2 * (P.Y1 - P.Y0);
+    P.samples = samples;
+    P.n_b = 0;
+    P.cols = samples;
+    P.bpos_offset = 0;
+    P.snap_offset = 0;
+    const int nx = P.X1 - P.X0 - 1, ny = P.Y1 - P.Y0 - 1;
+    Mapping mp;
+    if (!tile_mapping(nx, ny, mp) || !rows_instance(mp.rps)) {
+        set_error("msp_sample_patch_static: the buffered patch exceeds the on-chip tile (at most 98 interior columns "
+                  "and 12 rows per thread segment)");
+        return MSP_ERR_INVALID_ARG;
+    }
+    const int R = rows_instance(mp.rps);
+    const bool mixed = precision == MSP_MIXED;
+    size_t smem = smem_bytes(mixed, ny, mp.nseg * R);
+    if (smem > 220 * 1024) {
+        set_error("msp_sample_patch_static: the buffered patch exceeds shared memory");
+        return MSP_ERR_INVALID_ARG;
+    }
+    smem = (smem + 15) / 16 * 16;
+    const long long slot = (slot_rows(ny) * kPitch + 31) / 32 * 32;   // doubles
+    const long long slots = (long long)((kStaticScratchBytes - kStaticHeaderBytes) / sizeof(double)) / slot;
+    if (slots < 1) {
+        set_error("msp_sample_patch_static: the buffered patch needs more scratch than the static array holds");
+        return MSP_ERR_INVALID_ARG;
+    }
+    unsigned char* base = nullptr;
+    MSP_TRY(static_scratch_address(reinterpret_cast<void**>(&base)));
+    // header: [0, 256) work counter, [256, 512) patch description, [1024, ...) statistics
+    int* counter = reinterpret_cast<int*>(base);
+    PatchDev* pdev = reinterpret_cast<PatchDev*>(base + 256);
+    int* stats = reinterpret_cast<int*>(base + 1024);
+    double* scratch = reinterpret_cast<double*>(base + kStaticHeaderBytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    MSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    MSP_CUDA(cudaMemcpyAsync(pdev, &P, sizeof(PatchDev), cudaMemcpyHostToDevice, s));
+    TileArgs A{};
+    A.N = n_cells;
+    A.aE = aE_dev;
+    A.aN = aN_dev;
+    A.patches = pdev;
+    A.bpos = nullptr;
+    A.items = nullptr;
+    A.n_items = samples;
+    A.counter = counter;
+    A.snaps = snap_dev;
+    A.seed = seed;
+    A.tol = tol;
+    A.inner_tol = 1e-4;
+    A.max_iter = max_iter;
+    A.max_ref = 12;
+    A.scratch = scratch;
+    A.slot_doubles = slot;
+    A.stats = stats;
+    A.one_patch_index = patch_index;
+    const int grid = (int)std::max<long long>(1, std::min<long long>({(long long)samples, slots, (long long)num_sms()}));
+#define MSP_STATIC_LAUNCH(T, RR)                                                                                   \
+    do {                                                                                                           \
+        MSP_CUDA(cudaFuncSetAttribute(local_solve_tile<T, RR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                      (int)smem));                                                                 \
+        local_solve_tile<T, RR, true><<<grid, kTileThreads, smem, s>>>(A);                                          \
+    } while (0)
+    if (mixed) {
+        if (R == 4) MSP_STATIC_LAUNCH(float, 4);
+        else if (R == 8) MSP_STATIC_LAUNCH(float, 8);
+        else MSP_STATIC_LAUNCH(float, 12);
+    } else {
+        if (R == 4) MSP_STATIC_LAUNCH(double, 4);
+        else if (R == 8) MSP_STATIC_LAUNCH(double, 8);
+        else MSP_STATIC_LAUNCH(double, 12);
+    }
+#undef MSP_STATIC_LAUNCH
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    return MSP_OK;
+}
