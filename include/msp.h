@@ -236,6 +236,8 @@ typedef struct {
     int max_cholqr_tries;      /* largest number of shift attempts in Cholesky-QR           */
     float online_shift;        /* diagonal shift the online factorisation needed (0 = none) */
     int online_blocks;         /* rows of patches = diagonal blocks of the online factor    */
+    int online_factor_bits;    /* 32 or 64: precision the online factor was built in; 0 if the
+                                  patch-block preconditioner is in use                         */
 } msp_basis_stats;
 msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out);
 

@@ -46,7 +46,7 @@ class PatchInfo(C.Structure):
 
 class BasisStats(C.Structure):
     _fields_ = [("max_jacobi_sweeps", C.c_int), ("max_cholqr_tries", C.c_int), ("online_shift", C.c_float),
-                ("online_blocks", C.c_int)]
+                ("online_blocks", C.c_int), ("online_factor_bits", C.c_int)]
 
 
 class SolveStats(C.Structure):

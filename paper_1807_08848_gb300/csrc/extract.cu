@@ -667,6 +667,9 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     chol_factor_kernel<<<np, 256, 0, s>>>(d_kmats.p, G.p, L.p, F.p, Fi.p, shift_scale.p, 0, status.p);
     count_launches(1);
     precond_inverse_kernel<<<np, 256, 0, s>>>(d_kmats.p, Fi.p, B.d_binv_off.p, B.Binv.p);
+    // keep L_m^{-T} of every patch block: the scaling of the online factor
+    MSP_TRY(B.bt_Fi.alloc(std::max<long long>(ko, 1), s));
+    if (ko > 0) MSP_CUDA(cudaMemcpyAsync(B.bt_Fi.p, Fi.p, sizeof(double) * ko, cudaMemcpyDeviceToDevice, s));
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
     MSP_CUDA(cudaMemcpyAsync(hstat.data(), status.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));

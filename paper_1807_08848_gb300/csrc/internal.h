@@ -107,6 +107,16 @@ __host__ __device__ inline void ring_node(int X0, int X1, int Y0, int Y1, int t,
     else { i = X0; j = Y1 - (t - 2 * wx - wy); }
 }
 
+// Block-tridiagonal factor storage in one precision: L_q and C_q (F), L_q^{-1} (Li),
+// their transposes, and the sweep work vectors.
+template <class T>
+struct BtStore {
+    DevBuf<T> F, Li, FT, LiT, w1, w2;
+    void free_all() {
+        F.free_now(); Li.free_now(); FT.free_now(); LiT.free_now(); w1.free_now(); w2.free_now();
+    }
+};
+
 // Reduced bases and the online operators of one medium.
 struct Basis {
     int N = 0, mx = 0, my = 0;
@@ -141,12 +151,10 @@ struct Basis {
     std::vector<long long> bt_e_off;    // sub-diagonal block offsets
     long long bt_diag_elems = 0;
     float bt_shift = 0.f;
-    DevBuf<double> bt_Ds;               // diagonal scaling diag(H)^(-1/2)
-    DevBuf<float> bt_F;                 // L_q (diagonal blocks), C_q (sub-diagonal blocks)
-    DevBuf<float> bt_Li;                // L_q^{-1}
-    DevBuf<float> bt_FT, bt_LiT;        // transposed copies (contiguous columns for the sweeps)
-    DevBuf<float> bt_w1, bt_w2;         // sweep work vectors
-    DevBuf<GemmDescT<float>> bt_desc;
+    DevBuf<double> bt_Fi;               // patch-block scaling R_m^{-1} = L_m^{-T} (H_mm = L_m L_m^T)
+    int bt_prec = 0;                    // 1: FP32 factor, 2: FP64 factor
+    BtStore<float> bt32;
+    BtStore<double> bt64;
     DevBuf<double> w_s;                 // normal-equation residual s = P^T r
     bool use_block_jacobi = false;      // online preconditioner: patch blocks only
     int max_jacobi_sweeps = 0, max_cholqr_tries = 0;
