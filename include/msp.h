@@ -238,6 +238,7 @@ typedef struct {
     int online_blocks;         /* rows of patches = diagonal blocks of the online factor    */
     int online_factor_bits;    /* 32 or 64: precision the online factor was built in; 0 if the
                                   patch-block preconditioner is in use                         */
+    float mean_jacobi_sweeps;  /* mean sweep count of the one-sided Jacobi SVDs over patches   */
 } msp_basis_stats;
 msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out);
 

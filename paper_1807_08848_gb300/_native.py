@@ -46,7 +46,8 @@ class PatchInfo(C.Structure):
 
 class BasisStats(C.Structure):
     _fields_ = [("max_jacobi_sweeps", C.c_int), ("max_cholqr_tries", C.c_int), ("online_shift", C.c_float),
-                ("online_blocks", C.c_int), ("online_factor_bits", C.c_int)]
+                ("online_blocks", C.c_int), ("online_factor_bits", C.c_int),
+                ("mean_jacobi_sweeps", C.c_float)]
 
 
 class SolveStats(C.Structure):

@@ -74,6 +74,7 @@ extern "C" msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out) {
     out->max_cholqr_tries = b->B.max_cholqr_tries;
     out->online_shift = b->B.bt_shift;
     out->online_blocks = b->B.bt_q;
+    out->mean_jacobi_sweeps = b->B.mean_jacobi_sweeps;
     out->online_factor_bits = b->B.use_block_jacobi ? 0 : (b->B.bt_prec == 2 ? 64 : (b->B.bt_prec == 1 ? 32 : 0));
     return MSP_OK;
 }

@@ -15,12 +15,15 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDescT<T>* d
     const int tiles_m = (D.M + TM - 1) / TM;
     if (blockIdx.x >= tiles_m * ((D.N + TN - 1) / TN)) return;
     const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    if (D.lower && tn * TN > tm * TM + TM - 1) return;   // tile strictly above the diagonal
     __shared__ T As[TK][TM + 1];
     __shared__ T Bs[TK][TN + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads
     const int m0 = tm * TM, n0 = tn * TN;
     T acc[4][4] = {};
-    for (int k0 = 0; k0 < D.K; k0 += TK) {
+    const int k_begin = D.b_lower ? (n0 / TK) * TK : 0;
+    const int k_end = D.a_lower ? min(D.K, m0 + TM) : D.K;
+    for (int k0 = k_begin; k0 < k_end; k0 += TK) {
         // stage op(A)[m0 .. m0+63][k0 .. k0+15], reading along the contiguous index
         for (int e = threadIdx.x; e < TM * TK; e += 256) {
             int mm, kk;

@@ -8,6 +8,12 @@ namespace msp {
 
 // C (M x N) = alpha op(A) op(B) + beta C, column-major; op(X) = X or X^T.
 // op(A) is M x K, op(B) is K x N.  With beta == 0, C is not read.
+// lower != 0: only output tiles that reach the diagonal or below it are computed
+// (symmetric updates whose upper triangle is never read); the others keep C.
+// b_lower != 0: op(B) is lower triangular (op(B)[k][j] = 0 for k < j), so the
+// K loop of an output tile starting at column j0 begins at j0.
+// a_lower != 0: op(A) is lower triangular (op(A)[i][k] = 0 for k > i), so the K
+// loop of an output tile ending at row i1 stops after i1.
 template <class T>
 struct GemmDescT {
     const T* A;
@@ -16,6 +22,9 @@ struct GemmDescT {
     int M, N, K;
     int lda, ldb, ldc;
     T alpha, beta;
+    int lower = 0;
+    int b_lower = 0;
+    int a_lower = 0;
 };
 using GemmDesc = GemmDescT<double>;
 

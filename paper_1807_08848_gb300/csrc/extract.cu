@@ -117,105 +117,168 @@ __global__ void jacobi_init_kernel(const SmallMat* mats, const double* T, double
     }
 }
 
-// One-sided (Hestenes) Jacobi on W (c x c): rotate column pairs (p, q) until
-// every pair is orthogonal to relative level tol; V accumulates the rotations.
-// Pairs follow the round-robin tournament order (c/2 disjoint pairs per step,
-// one warp per pair).  Afterwards W = U S and T^T = U S V^T, so V holds the
-// left singular vectors of T.  Run in FP32 first (the bulk of the sweeps at the
-// FP32 rate), then, after re-orthonormalising V in FP64, in FP64 from W = T^T V
-// (a few sweeps: the columns start orthogonal to FP32 level).
-template <class R>
-__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, R* W, R* V, int max_sweeps, R tol_rel,
-                                                         int* sweeps_out) {
+constexpr int kJacGroup = 4;       // threads per column pair
+constexpr int kJacMaxPairs = 512;  // c <= 1024
+
+// One-sided (Hestenes) Jacobi in FP64 on the columns of W = T^T (c x c): rotate
+// column pairs (p, q) until every pair is orthogonal to relative level tol; V
+// accumulates the rotations, so at the end W = Z S and T = V S Z^T: the
+// singular values are the column norms of W and V holds the left singular
+// vectors of T.  (On T^T the sweeps converge in about a third of the sweeps
+// needed on the columns of T.)  Pairs follow the round-robin tournament order,
+// c/2 disjoint pairs per round.  Each round has two phases: groups of
+// kJacGroup threads take one pair each (three inner products, the rotation
+// angle, the rotation of the two W columns), then the whole block applies the
+// round's rotations to V with coalesced row-wise accesses.  The FP64 pipe is
+// the bound, so the angle arithmetic is done once per pair, not once per lane
+// of a warp.  W lives in shared memory (leading dimension c + 1) when
+// c <= smem_c, else in global memory.
+// Skips: columns below u |T|_F are numerically zero; a pair orthogonal to the
+// rounding floor of its inner product is left alone; and a pair whose columns
+// are both below small_rel |T|_F (far under the truncation level) is left alone,
+// since rotating it only mixes directions that are dropped.
+__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, double* W, double* V, int max_sweeps,
+                                                         double tol, double small_rel, int smem_c, int* sweeps_out) {
+    extern __shared__ __align__(16) unsigned char jac_smem[];
+    __shared__ double s_cs[kJacMaxPairs], s_sn[kJacMaxPairs];
+    __shared__ int s_p[kJacMaxPairs], s_q[kJacMaxPairs];
+    __shared__ double s_red[32];
+    __shared__ double s_fro;
+    __shared__ int s_rot;
     const SmallMat S = mats[blockIdx.x];
     const int c = S.c;
-    if (c <= 1) {
+    if (c <= 1 || c > 2 * kJacMaxPairs) {
         if (threadIdx.x == 0) sweeps_out[blockIdx.x] = 0;
         return;
     }
-    R* w = W + S.off;
-    R* v = V + S.off;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int np = c + (c & 1);   // players, even
-    const R tol = tol_rel;
-    // columns below u |T|_F are numerically zero: their mutual orthogonality is
-    // rounding noise, so pairs involving them are left alone
-    __shared__ R s_fro;
-    if (warp == 0) {
-        R a = 0;
-        for (long long e = lane; e < (long long)c * c; e += 32) a += w[e] * w[e];
-        a = warp_sum(a);
-        if (lane == 0) s_fro = a;
+    const bool in_smem = c <= smem_c;
+    const int ldw = in_smem ? c + 1 : c;
+    double* w = in_smem ? reinterpret_cast<double*>(jac_smem) : W + S.off;
+    double* v = V + S.off;
+    if (in_smem) {
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            w[i + (long long)j * ldw] = W[S.off + e];
+        }
     }
-    __syncthreads();
-    const R eps = sizeof(R) == 8 ? (R)1.1102230246251565e-16 : (R)5.9604645e-8;
-    const R negligible = eps * eps * s_fro;   // (u |T|_F)^2
+    // |T|_F^2
+    {
+        double a = 0.0;
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            const double x = w[i + (long long)j * ldw];
+            a += x * x;
+        }
+        a = warp_sum(a);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t = (threadIdx.x < (blockDim.x >> 5)) ? s_red[threadIdx.x] : 0.0;
+            t = warp_sum(t);
+            if (threadIdx.x == 0) s_fro = t;
+        }
+        __syncthreads();
+    }
+    const double eps = 1.1102230246251565e-16;
+    const double negligible = eps * eps * s_fro;   // (u |T|_F)^2
     // rounding floor of an inner product of columns of norms a and b: the columns
     // carry absolute errors ~ c u |T|_F, so orthogonality below that is noise
-    const R floor_abs = R(2) * c * eps * sqrt(s_fro);
-    __shared__ int s_rot;
+    const double floor_abs = 2.0 * c * eps * sqrt(s_fro);
+    const double small2 = small_rel * small_rel * s_fro;
+    const int np = c + (c & 1);   // players, even
+    const int npairs = np / 2;
+    const int g = threadIdx.x % kJacGroup;
+    const int groups = blockDim.x / kJacGroup;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < np - 1; ++r) {
-            for (int pr = warp; pr < np / 2; pr += nw) {
-                int a, b;
-                if (pr == 0) { a = r; b = np - 1; }
-                else { a = (r + pr) % (np - 1); b = (r - pr + (np - 1)) % (np - 1); }
-                if (a >= c || b >= c) continue;
-                const int p = min(a, b), q = max(a, b);
-                R* wp = w + (long long)p * c;
-                R* wq = w + (long long)q * c;
-                R al = 0, be = 0, ga = 0;
-                for (int i = lane; i < c; i += 32) {
-                    const R x = wp[i], y = wq[i];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
+            // phase 1: one group per pair; every thread runs the same number of
+            // iterations so that the group shuffles see full warps
+            for (int base = 0; base < npairs; base += groups) {
+                const int pr = base + threadIdx.x / kJacGroup;
+                const bool live = pr < npairs;
+                int p = 0, q = 0;
+                if (live) {
+                    int a, b;
+                    if (pr == 0) { a = r; b = np - 1; }
+                    else { a = (r + pr) % (np - 1); b = (r - pr + (np - 1)) % (np - 1); }
+                    p = min(a, b);
+                    q = max(a, b);
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                const R na = sqrt(al), nb = sqrt(be);
-                if (al <= negligible || be <= negligible || fabs(ga) <= tol * na * nb + floor_abs * (na + nb)) continue;
-                const R zeta = (be - al) / (R(2) * ga);
-                const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
-                const R cs = R(1) / sqrt(R(1) + t * t), sn = cs * t;
-                for (int i = lane; i < c; i += 32) {
-                    const R x = wp[i], y = wq[i];
-                    wp[i] = cs * x - sn * y;
-                    wq[i] = sn * x + cs * y;
+                const bool real = live && q < c;
+                double* wp = w + (long long)p * ldw;
+                double* wq = w + (long long)q * ldw;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                if (real) {
+                    for (int i = g; i < c; i += kJacGroup) {
+                        const double x = wp[i], y = wq[i];
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                        ga = fma(x, y, ga);
+                    }
                 }
-                R* vp = v + (long long)p * c;
-                R* vq = v + (long long)q * c;
-                for (int i = lane; i < c; i += 32) {
-                    const R x = vp[i], y = vq[i];
-                    vp[i] = cs * x - sn * y;
-                    vq[i] = sn * x + cs * y;
+#pragma unroll
+                for (int o = kJacGroup / 2; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                if (lane == 0) atomicAdd(&s_rot, 1);
+                double cs = 1.0, sn = 0.0;
+                bool rot = false;
+                if (real) {
+                    const double na = sqrt(al), nb = sqrt(be);
+                    rot = !(al <= negligible || be <= negligible || (al < small2 && be < small2) ||
+                            fabs(ga) <= tol * na * nb + floor_abs * (na + nb));
+                }
+                if (rot) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    cs = 1.0 / sqrt(1.0 + t * t);
+                    sn = cs * t;
+                    for (int i = g; i < c; i += kJacGroup) {
+                        const double x = wp[i], y = wq[i];
+                        wp[i] = cs * x - sn * y;
+                        wq[i] = sn * x + cs * y;
+                    }
+                }
+                if (live && g == 0) {
+                    s_p[pr] = rot ? p : -1;
+                    s_q[pr] = q;
+                    s_cs[pr] = cs;
+                    s_sn[pr] = sn;
+                    if (rot) s_rot = 1;
+                }
+            }
+            __syncthreads();
+            // phase 2: the round's rotations applied to V, rows fastest
+            for (long long e = threadIdx.x; e < (long long)npairs * c; e += blockDim.x) {
+                const int pr = (int)(e / c), i = (int)(e % c);
+                const int p = s_p[pr];
+                if (p < 0) continue;
+                const int q = s_q[pr];
+                const double cs = s_cs[pr], sn = s_sn[pr];
+                double* vp = v + (long long)p * c;
+                double* vq = v + (long long)q * c;
+                const double x = vp[i], y = vq[i];
+                vp[i] = cs * x - sn * y;
+                vq[i] = sn * x + cs * y;
             }
             __syncthreads();
         }
         if (s_rot == 0) break;
         __syncthreads();
     }
+    if (in_smem) {
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            W[S.off + e] = w[i + (long long)j * ldw];
+        }
+    }
     if (threadIdx.x == 0) sweeps_out[blockIdx.x] = sweep;
 }
 
-// precision conversions of the c x c work matrices
-__global__ void to_f32_mats_kernel(const SmallMat* mats, const double* src, float* dst, int identity) {
-    const SmallMat S = mats[blockIdx.x];
-    for (long long e = threadIdx.x; e < (long long)S.c * S.c; e += blockDim.x) {
-        const int i = (int)(e % S.c), j = (int)(e / S.c);
-        dst[S.off + e] = identity ? (i == j ? 1.f : 0.f) : (float)src[S.off + e];
-    }
-}
-__global__ void to_f64_mats_kernel(const SmallMat* mats, const float* src, double* dst) {
-    const SmallMat S = mats[blockIdx.x];
-    for (long long e = threadIdx.x; e < (long long)S.c * S.c; e += blockDim.x) dst[S.off + e] = (double)src[S.off + e];
-}
 
 // Column norms of W = singular values; sort descending (rank by comparison);
 // keep k = #{s_i > tau s_1}.  Writes sigma (sorted), order, k.
@@ -358,7 +421,8 @@ int domain_ring_pos(int N, int i, int j) {
 msp_status svd_bases(const double* snaps, long long snap_elems, const std::vector<long long>& snap_off,
                      const std::vector<int>& n_rows, const std::vector<int>& cols, double tau, cudaStream_t s,
                      DevBuf<double>& Q, std::vector<int>& k, std::vector<double>& sigma,
-                     std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries) {
+                     std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries,
+                     float* mean_sweeps) {
     const int np = (int)cols.size();
     max_sweeps = 0;
     max_tries = 0;
@@ -456,39 +520,24 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
     // ---- SVD of the triangular factor
     MSP_TRY(W.alloc(mo, s));
     MSP_TRY(V.alloc(mo, s));
+    if (maxc > 2 * kJacMaxPairs) {
+        set_error("basis extraction: more than " + std::to_string(2 * kJacMaxPairs) + " snapshot columns on a patch");
+        return MSP_ERR_INVALID_ARG;
+    }
     {
-        DevBuf<float> W32, V32;
-        MSP_TRY(W32.alloc(mo, s));
-        MSP_TRY(V32.alloc(mo, s));
-        // FP32 sweeps on T^T
         jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
         count_launches(1);
-        to_f32_mats_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, W32.p, 0);
+        const int smem_max = 226 * 1024;   // leaves room for the kernel's static shared memory
+        int c64 = 0;                       // largest order whose W is held in shared memory
+        while ((long long)(c64 + 1) * (c64 + 2) * (long long)sizeof(double) <= smem_max - 10 * 1024) ++c64;
+        c64 = std::min(c64, maxc);
+        const size_t sm64 = (size_t)c64 * (c64 + 1) * sizeof(double);
+        MSP_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));
+        // pairs of columns both below 1e-3 tau sigma_1 (|T|_F / sqrt(c) <= sigma_1) are not rotated
+        const double small_rel = 1e-3 * tau / std::sqrt((double)std::max(maxc, 1));
+        jacobi_svd_kernel<<<np, 512, sm64, s>>>(d_mats.p, W.p, V.p, 40, maxc * 1.12e-16, small_rel, c64, sweeps.p);
         count_launches(1);
-        to_f32_mats_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, V32.p, 1);
-        count_launches(1);
-        jacobi_svd_kernel<float><<<np, 512, 0, s>>>(d_mats.p, W32.p, V32.p, 40, (float)(2.0 * maxc * 5.96e-8), sweeps.p);
-        count_launches(1);
-        // V <- V32 re-orthonormalised in FP64 (Cholesky-QR: G = V^T V, V <- V L^{-T})
-        to_f64_mats_kernel<<<np, 256, 0, s>>>(d_mats.p, V32.p, L.p);
-        count_launches(1);
-        for (int m = 0; m < np; ++m)
-            gd[m] = GemmDesc{L.p + mats[m].off, L.p + mats[m].off, G.p + mats[m].off, mats[m].c, mats[m].c, mats[m].c,
-                             mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
-        MSP_TRY(run_gemm(true, maxc, maxc));
-        chol_factor_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p, W.p, F.p, Fi.p, shift_scale.p, 0, status.p);
-        count_launches(1);
-        for (int m = 0; m < np; ++m)
-            gd[m] = GemmDesc{L.p + mats[m].off, Fi.p + mats[m].off, V.p + mats[m].off, mats[m].c, mats[m].c, mats[m].c,
-                             mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
-        MSP_TRY(run_gemm(false, maxc, maxc));
-        // W = T^T V, then FP64 sweeps
-        for (int m = 0; m < np; ++m)
-            gd[m] = GemmDesc{Tacc + mats[m].off, V.p + mats[m].off, W.p + mats[m].off, mats[m].c, mats[m].c, mats[m].c,
-                             mats[m].c, mats[m].c, mats[m].c, 1.0, 0.0};
-        MSP_TRY(run_gemm(true, maxc, maxc));
-        jacobi_svd_kernel<double><<<np, 512, 0, s>>>(d_mats.p, W.p, V.p, 30, maxc * 1.12e-16, sweeps.p);
-        count_launches(1);
+        MSP_CUDA(cudaGetLastError());
     }
     sort_truncate_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, tau, sig_tmp.p, sig.p, d_sig_off.p, order.p, kdev.p);
     count_launches(1);
@@ -501,6 +550,11 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         MSP_CUDA(cudaMemcpyAsync(sw.data(), sweeps.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
         for (int v : sw) max_sweeps = std::max(max_sweeps, v);
+        if (mean_sweeps) {
+            double t = 0.0;
+            for (int v : sw) t += v;
+            *mean_sweeps = np > 0 ? (float)(t / np) : 0.f;
+        }
     }
     MSP_CUDA(cudaMemcpyAsync(k.data(), kdev.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
     MSP_CUDA(cudaMemcpyAsync(sigma.data(), sig.p, sizeof(double) * so, cudaMemcpyDeviceToHost, s));
@@ -541,7 +595,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
             cols[m] = M.patches[m].cols;
         }
         MSP_TRY(svd_bases(M.snaps.p, M.snap_elems, snap_off, n_rows, cols, tau, s, B.Q, B.k, B.sigma, B.sigma_off, B.q_off,
-                          B.max_jacobi_sweeps, B.max_cholqr_tries));
+                          B.max_jacobi_sweeps, B.max_cholqr_tries, &B.mean_jacobi_sweeps));
     }
     B.c_off.resize(np + 1);
     int co = 0;

@@ -153,11 +153,13 @@ struct Basis {
     float bt_shift = 0.f;
     DevBuf<double> bt_Fi;               // patch-block scaling R_m^{-1} = L_m^{-T} (H_mm = L_m L_m^T)
     int bt_prec = 0;                    // 1: FP32 factor, 2: FP64 factor
+    std::vector<int> bt_elo, bt_ehi;    // per patch: range of coupled patches in the row above
     BtStore<float> bt32;
     BtStore<double> bt64;
     DevBuf<double> w_s;                 // normal-equation residual s = P^T r
     bool use_block_jacobi = false;      // online preconditioner: patch blocks only
     int max_jacobi_sweeps = 0, max_cholqr_tries = 0;
+    float mean_jacobi_sweeps = 0.f;
     int device = 0;
 };
 

@@ -73,7 +73,8 @@ namespace msp {
 msp_status svd_bases(const double* snaps, long long snap_elems, const std::vector<long long>& snap_off,
                      const std::vector<int>& n_rows, const std::vector<int>& cols, double tau, cudaStream_t s,
                      DevBuf<double>& Q, std::vector<int>& k, std::vector<double>& sigma,
-                     std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries);
+                     std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries,
+                     float* mean_sweeps = nullptr);
 
 namespace {
 

@@ -14,6 +14,8 @@
 // it keeps the least-squares solution at FP64 accuracy; on a non-positive pivot
 // the factorisation is repeated with a diagonal shift.
 #include "internal.h"
+
+#include <array>
 #include "dense.cuh"
 #include "device_util.cuh"
 
@@ -225,7 +227,7 @@ int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long lon
 // copies for the sweeps.  *fail_out = 1 on a non-positive pivot.
 template <class T>
 msp_status factorize(Basis& B, const double* Hs64p, long long total, double shift, int* fail_out, BtStore<T>& S,
-                     cudaStream_t s) {
+                     bool early_exit, cudaStream_t s) {
     const int Qn = B.bt_q;
     struct { const double* p; } Hs64{Hs64p};
     MSP_TRY(S.F.alloc(std::max<long long>(total, 1), s));
@@ -236,7 +238,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
     DevBuf<T> tinv, trow;
     DevBuf<int> fail;
     MSP_TRY(tinv.alloc((size_t)std::max(max_nt, 1) * kTile * kTile, s));
-    MSP_TRY(trow.alloc((size_t)kTile * std::max(max_n, 1), s));
+    MSP_TRY(trow.alloc((size_t)std::max(max_n, 1) * std::max(max_n, 1), s));
     MSP_TRY(fail.alloc(1, s));
     // temporary for C_q (E_q is read by every output tile of the product)
     long long max_e = 1;
@@ -248,7 +250,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
     {
         MSP_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int), s));
         MSP_CUDA(cudaMemsetAsync(S.Li.p, 0, sizeof(T) * std::max<long long>(B.bt_diag_elems, 1), s));
-        // scaled FP32 copies
+        // scaled copies in precision T
         for (int q = 0; q < Qn; ++q) {
             const int n = B.bt_off[q + 1] - B.bt_off[q];
             if (n == 0) continue;
@@ -267,7 +269,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         // Collect the whole factorisation's GEMMs in order, then launch them in order
         // with their descriptors resident in one device array.
         struct Step {
-            int kind;        // 0 gemm, 1 potrf tile, 2 zero upper, 3 copy tile
+            int kind;        // 0 gemm, 1 potrf tile, 2 zero upper, 3 copy tile, 4 zero fill, 5 pivot check
             GemmDescT<T> g;
             bool tA, tB;
             T* ptr;
@@ -275,14 +277,18 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
             T* inv;
             const T* src;
             int lds;
+            int group;
         };
         std::vector<Step> steps;
+        int group_id = 0;
         auto add_gemm = [&](const T* A, int lda, const T* Bm, int ldb, T* C, int ldc, int M, int N, int K,
-                            T alpha, T beta, bool tA, bool tB) {
+                            T alpha, T beta, bool tA, bool tB, int lower = 0, int b_lower = 0, int group = 0,
+                            int a_lower = 0) {
             if (M <= 0 || N <= 0 || K <= 0) return;
             Step st{};
             st.kind = 0;
-            st.g = GemmDescT<T>{A, Bm, C, M, N, K, lda, ldb, ldc, alpha, beta};
+            st.group = group;
+            st.g = GemmDescT<T>{A, Bm, C, M, N, K, lda, ldb, ldc, alpha, beta, lower, b_lower, a_lower};
             st.tA = tA;
             st.tB = tB;
             steps.push_back(st);
@@ -295,7 +301,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
             if (q > 0) {   // D_q -= C_{q-1} C_{q-1}^T
                 const int n0 = B.bt_off[q] - B.bt_off[q - 1];
                 const T* Cp = S.F.p + B.bt_e_off[q - 1];
-                add_gemm(Cp, n, Cp, n, Dq, n, n, n, n0, T(-1), T(1), false, true);
+                add_gemm(Cp, n, Cp, n, Dq, n, n, n, n0, T(-1), T(1), false, true, 1);
             }
             const int nt = (n + kTile - 1) / kTile;
             for (int kt = 0; kt < nt; ++kt) {
@@ -312,7 +318,8 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                     // panel <- panel inv(L_kk)^T (in place: one column tile)
                     add_gemm(panel, n, st.inv, kTile, panel, n, m, nb, nb, T(1), T(0), false, true);
                     // trailing -= panel panel^T
-                    add_gemm(panel, n, panel, n, Dq + (r0 + nb) + (long long)(r0 + nb) * n, n, m, m, nb, T(-1), T(1), false, true);
+                    add_gemm(panel, n, panel, n, Dq + (r0 + nb) + (long long)(r0 + nb) * n, n, m, m, nb, T(-1), T(1), false,
+                             true, 1);
                 }
             }
             Step zu{};
@@ -320,14 +327,14 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
             zu.ptr = Dq;
             zu.nb = n;
             steps.push_back(zu);
-            // Li = L^{-1} by tile rows: X[it, :it] = -inv(L_ii) L[it, :it] X[:it, :it]; X[it, it] = inv(L_ii)
+            Step pc{};
+            pc.kind = 5;
+            steps.push_back(pc);
+            // Li = L^{-1}: diagonal tiles from the tile inverses, then blocks of
+            // doubling size, inv([A 0; B C]) = [inv(A) 0; -inv(C) B inv(A) inv(C)],
+            // all pairs of one level in one batched launch per product.
             for (int it = 0; it < nt; ++it) {
                 const int r0 = it * kTile, nb = std::min(kTile, n - r0);
-                if (it > 0) {
-                    add_gemm(Dq + r0, n, Li, n, trow.p, kTile, nb, r0, r0, T(1), T(0), false, false);
-                    add_gemm(tinv.p + (size_t)it * kTile * kTile, kTile, trow.p, kTile, Li + r0, n, nb, r0, nb, T(-1), T(0),
-                             false, false);
-                }
                 Step ct{};
                 ct.kind = 3;
                 ct.src = tinv.p + (size_t)it * kTile * kTile;
@@ -338,11 +345,50 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                 ct.nc = nb;
                 steps.push_back(ct);
             }
+            for (int w = 1; w < nt; w *= 2) {
+                const int g1 = ++group_id, g2 = ++group_id;
+                std::vector<std::array<int, 5>> prs;   // a0, a1 (= c0), c1, offset in the work buffer
+                long long wo = 0;
+                for (int t0 = 0; t0 + w < nt; t0 += 2 * w) {
+                    const int a0 = t0 * kTile, a1 = std::min((t0 + w) * kTile, n), c1 = std::min((t0 + 2 * w) * kTile, n);
+                    prs.push_back({a0, a1, c1, (int)wo, 0});
+                    wo += (long long)(c1 - a1) * (a1 - a0);
+                }
+                for (auto& pr : prs) {   // Wk = L[C, A] inv(A)   (inv(A) lower triangular)
+                    const int a0 = pr[0], a1 = pr[1], c1 = pr[2];
+                    add_gemm(Dq + a1 + (long long)a0 * n, n, Li + a0 + (long long)a0 * n, n, trow.p + pr[3], c1 - a1, c1 - a1,
+                             a1 - a0, a1 - a0, T(1), T(0), false, false, 0, 1, g1);
+                }
+                for (auto& pr : prs) {   // Li[C, A] = -inv(C) Wk   (inv(C) lower triangular)
+                    const int a0 = pr[0], a1 = pr[1], c1 = pr[2];
+                    add_gemm(Li + a1 + (long long)a1 * n, n, trow.p + pr[3], c1 - a1, Li + a1 + (long long)a0 * n, n, c1 - a1,
+                             a1 - a0, c1 - a1, T(-1), T(0), false, false, 0, 0, g2, 1);
+                }
+            }
             if (q + 1 < Qn) {   // C_q = E_q Li^T
                 const int n1 = B.bt_off[q + 2] - B.bt_off[q + 1];
                 T* Eq = S.F.p + B.bt_e_off[q];
-                // C_q overwrites E_q: go through a temporary (E_q is read by every output tile)
-                add_gemm(Eq, n1, Li, n, ctmp.p, n1, n1, n, n, T(1), T(0), false, true);
+                // C_q overwrites E_q: go through a temporary (E_q is read by every output
+                // tile).  E_q couples a patch of row q+1 only with a contiguous range of
+                // patches of row q (its neighbours), so each patch's rows of C_q take a
+                // product over that range only; Li is lower triangular, so the columns
+                // left of the range stay zero.
+                Step z{};
+                z.kind = 4;
+                z.ptr = ctmp.p;
+                z.nr = n1;
+                z.nc = n;
+                steps.push_back(z);
+                const int egroup = ++group_id;
+                for (int p = 0; p < B.mx; ++p) {
+                    const int ma = (q + 1) * B.mx + p;
+                    if (ma >= (int)B.bt_elo.size() || B.bt_elo[ma] < 0 || B.k[ma] == 0) continue;
+                    const int r0 = B.c_off[ma] - B.bt_off[q + 1];
+                    const int c0 = B.c_off[B.bt_elo[ma]] - B.bt_off[q];
+                    const int c1 = B.c_off[B.bt_ehi[ma] + 1] - B.bt_off[q];
+                    add_gemm(Eq + r0 + (long long)c0 * n1, n1, Li + c0 + (long long)c0 * n, n, ctmp.p + r0 + (long long)c0 * n1,
+                             n1, B.k[ma], n - c0, c1 - c0, T(1), T(0), false, true, 0, 0, egroup);
+                }
                 Step cp{};
                 cp.kind = 3;
                 cp.src = ctmp.p;
@@ -361,20 +407,37 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         DevBuf<GemmDescT<T>> d_all;
         MSP_TRY(upload(d_all, gds, s));
         size_t gi = 0;
-        for (auto& st : steps) {
+        for (size_t si = 0; si < steps.size(); ++si) {
+            const Step& st = steps[si];
             if (st.kind == 0) {
-                gemm_batched<T>(d_all.p + gi, 1, st.g.M, st.g.N, st.tA, st.tB, s);
-                ++gi;
+                // consecutive GEMMs of one group (independent outputs) go out as one batch
+                size_t sj = si + 1;
+                int mm = st.g.M, nn = st.g.N;
+                while (st.group && sj < steps.size() && steps[sj].kind == 0 && steps[sj].group == st.group) {
+                    mm = std::max(mm, steps[sj].g.M);
+                    nn = std::max(nn, steps[sj].g.N);
+                    ++sj;
+                }
+                gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s);
+                gi += sj - si;
+                si = sj - 1;
             } else if (st.kind == 1) {
                 potrf_tile_kernel<T><<<1, 256, 0, s>>>(st.ptr, st.ld, st.nb, st.inv, fail.p);
                 count_launches(1);
             } else if (st.kind == 2) {
                 zero_upper_kernel<T><<<grid_for((long long)st.nb * st.nb), 256, 0, s>>>(st.ptr, st.nb);
                 count_launches(1);
-            } else {
+            } else if (st.kind == 3) {
                 copy_tile_kernel<T><<<std::max(1, std::min(1024, (st.nr * st.nc + 255) / 256)), 256, 0, s>>>(st.src, st.lds, st.ptr,
                                                                                                           st.ld, st.nr, st.nc);
                 count_launches(1);
+            } else if (st.kind == 4) {
+                MSP_CUDA(cudaMemsetAsync(st.ptr, 0, sizeof(T) * (size_t)st.nr * st.nc, s));
+            } else if (early_exit) {   // pivot check after a diagonal block: stop at the first breakdown
+                MSP_CUDA(cudaGetLastError());
+                MSP_CUDA(cudaMemcpyAsync(&hfail, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+                MSP_CUDA(cudaStreamSynchronize(s));
+                if (hfail) break;
             }
         }
         MSP_CUDA(cudaGetLastError());
@@ -450,6 +513,8 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
         }
     }
     std::vector<PairBlock> pb;
+    B.bt_elo.assign(np, -1);
+    B.bt_ehi.assign(np, -1);
     std::vector<int> lsa, lsb;
     std::vector<signed char> lsg;
     for (auto& kv : pairs) {
@@ -476,6 +541,10 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
             p.ld = n1;
         }
         pb.push_back(p);
+        if (qa == qb + 1) {   // patch ma (row qb+1) couples with patch mb of row qb
+            B.bt_elo[ma] = B.bt_elo[ma] < 0 ? mb : std::min(B.bt_elo[ma], mb);
+            B.bt_ehi[ma] = std::max(B.bt_ehi[ma], mb);
+        }
     }
     DevBuf<PairBlock> d_pb;
     DevBuf<int> d_lsa, d_lsb;
@@ -527,7 +596,7 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
     H64.free_now();
     // factorise in FP32; if a pivot fails, in FP64
     int fail = 0;
-    MSP_TRY(factorize<float>(B, Hs64.p, total, 0.0, &fail, B.bt32, s));
+    MSP_TRY(factorize<float>(B, Hs64.p, total, 0.0, &fail, B.bt32, true, s));
     if (!fail) {
         B.bt_prec = 1;
         return MSP_OK;
@@ -535,7 +604,7 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
     B.bt32.free_all();
     const double shifts[3] = {0.0, 1e-12, 1e-9};
     for (int a = 0; a < 3; ++a) {
-        MSP_TRY(factorize<double>(B, Hs64.p, total, shifts[a], &fail, B.bt64, s));
+        MSP_TRY(factorize<double>(B, Hs64.p, total, shifts[a], &fail, B.bt64, false, s));
         if (!fail) {
             B.bt_prec = 2;
             B.bt_shift = (float)shifts[a];
