@@ -284,11 +284,49 @@ def run_ours(args, rank, world):
         lat.append((time.perf_counter() - a) * 1e3)
     lat.sort()
 
-    # ---- roofline of the dominant kernel: FP32 (mixed) / FP64 arithmetic of the CG
-    # iterations.  Algorithmic flops per CG iteration and unknown: 9 for the
-    # 5-point apply (5 mul + 4 add with the diagonal precomputed as a sum), 2 each
-    # for the dots, 2 each for the three axpys, 1 for the Jacobi scaling: 22.
-    flops = 22.0 * float(stats.unknown_iters)
+    # ---- per-stage device times of one step (outside the timed region)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    evs[0].record(stream)
+    smed = msp.Medium(w["medium"], w["patches"])
+    evs[1].record(stream)
+    smed.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
+    evs[2].record(stream)
+    sbasis = smed.extract(w["tau"], prec)
+    evs[3].record(stream)
+    try:
+        sbasis.solve(phi_dev, tol=w["online_tol"], max_iter=args.online_iters, want_iters=False)
+    except _native.MspError:
+        pass
+    evs[4].record(stream)
+    torch.cuda.synchronize()
+    stages = {nm: evs[i].elapsed_time(evs[i + 1]) for i, nm in
+              enumerate(("build_medium_ms", "sample_patches_ms", "extract_basis_ms", "online_solve_ms"))}
+    stages["basis_stats"] = sbasis.stats()
+    del smed, sbasis
+
+    # ---- the plain FP64 path's local solves on the same medium, for comparison
+    fp64_rate = None
+    if args.compare_fp64 and prec == "mixed":
+        med64 = msp.Medium(w["medium"], w["patches"])
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        st64 = med64.sample(w["seed"], "fp64", tol=tol, max_iter=20000)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_rate = {"solves_per_s": int(st64.n_solves) / (f0.elapsed_time(f1) / 1e3),
+                     "avg_cg_iters": st64.total_iters / max(1, int(st64.n_solves))}
+        del med64
+
+    # ---- roofline of the dominant kernel: the CG arithmetic of the tile-resident
+    # local solves.  Algorithmic flops per CG iteration and unknown of the
+    # symmetrically scaled operator (unit diagonal): 9 for the 5-point apply
+    # (4 products, 4 adds, 1 subtract), 2 for p.Ap, 2 + 2 for the x and r
+    # updates, 2 for r.r, 2 for the p update: 19.
+    flops = 19.0 * float(stats.unknown_iters)
+    # DRAM bytes per local solve of local_solve_tile<float, 12>, from one ncu
+    # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 513^2 case,
+    # whose buffered tiles have the same sizes: 1012.35 MB / 11164 solves.
+    traffic_per_solve = (22942720 + 989403648) / 11164.0
     achieved = flops / t_kernel / 1e12
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
@@ -313,9 +351,13 @@ def run_ours(args, rank, world):
         "local_solve": {"seconds": t_kernel, "solves_per_s": n_solves / t_kernel,
                         "avg_cg_iters": stats.total_iters / max(1, n_solves),
                         "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged},
+        "fp64_path_local_solve": fp64_rate,
+        "stages": stages,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "local_solve_global<float>" if prec == "mixed" else "local_solve_global<double>",
+                     "frac": achieved / peak,
+                     "traffic": traffic_per_solve * n_solves if prec == "mixed" else None,
+                     "traffic_source": "ncu capture of the 513^2 case scaled by solves" if prec == "mixed" else None,
+                     "kernel": "local_solve_tile<float, 12>" if prec == "mixed" else "local_solve_tile<double, 12>",
                      "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"
                                     + ("" if prec == "mixed" else " / 64 (FP64 rate)")},
         "clocks": clk,
@@ -337,6 +379,8 @@ def main():
     ap.add_argument("--online-reqs", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
+                    help="skip timing the plain FP64 local solves beside the mixed ones")
     ap.add_argument("--case", default="full", choices=["full", "profile513"],
                     help="profile513: one pass of the small 513^2 case for profiler captures")
     args = ap.parse_args()
