@@ -180,6 +180,127 @@ def run_profile_case(args):
                       "online_iters": oi}))
 
 
+def run_serving(args):
+    """Serving workload: three prebuilt log-normal media (513^2, 1025^2, 2049^2;
+    64-cell patches, 16-cell buffers, 128 samples), bases and boundary-to-
+    coefficient maps on the device, Poisson arrivals (mean args.rate req/s, seed
+    3) of 16-mode Fourier boundary data on a uniformly chosen medium, served by
+    the request loop.  Reports p50/p99 latency (submit to result on the device)
+    and the throughput, and checks a seeded 1% sample against the FP64 iterative
+    online solve of the same data (relative L2 <= 1e-6)."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    wl = synth.workload_serving()
+    t0 = time.time()
+    bases, meds = [], []
+    for md in wl["media"]:
+        med = msp.Medium(md["medium"], md["patches"])
+        med.sample(1, "mixed", tol=1e-10, max_iter=20000, stats=False)
+        b = med.extract(1e-6, "mixed")
+        meds.append(med)
+        bases.append(b)
+    t_offline = time.time() - t0
+    t0 = time.time()
+    for b in bases:
+        b.build_map(tol=1e-10, max_iter=5000)
+    torch.cuda.synchronize()
+    t_map = time.time() - t0
+    rng = np.random.default_rng(wl["seed"])
+    n_req = args.requests
+    gaps = rng.exponential(1.0 / args.rate, n_req)
+    arrivals = np.cumsum(gaps)
+    which = rng.integers(0, len(bases), n_req)
+    pool = [synth.phi_fourier(b.n_cells, 16, 3000 + i, batch=64) for i, b in enumerate(bases)]
+    check = set(rng.choice(n_req, max(1, n_req // 100), replace=False).tolist())
+    srv = msp.Server(bases, mem_budget_bytes=int(args.serve_mem_gb * (1 << 30)), max_slots=4096,
+                     max_batch=32, n_workers=args.serve_workers)
+    pending = {}
+    lat = np.full(n_req, np.nan)
+    fetched = {}
+    lock = threading.Lock()
+    finished = threading.Event()
+
+    def poller():
+        while not finished.is_set() or pending:
+            with lock:
+                items = list(pending.items())
+            for rid, j in items:
+                d, l = srv.poll(rid)
+                if d == 0:
+                    continue
+                lat[j] = l
+                if j in check:
+                    fetched[j] = srv.fetch(rid, int(which[j]))
+                else:
+                    srv.release(rid)
+                with lock:
+                    pending.pop(rid, None)
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t_start = time.perf_counter()
+    for j in range(n_req):
+        dt = arrivals[j] - (time.perf_counter() - t_start)
+        if dt > 0:
+            time.sleep(dt)
+        i = int(which[j])
+        rid = srv.submit(i, pool[i][j % 64])
+        with lock:
+            pending[rid] = j
+    finished.set()
+    th.join(timeout=600)
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    # accuracy of the sampled requests against the FP64 iterative online solve
+    worst = 0.0
+    for j, u in fetched.items():
+        i = int(which[j])
+        b = bases[i]
+        b.set_preconditioner("block_rows_fp64")
+        ref, _ = b.solve(torch.tensor(pool[i][j % 64], device="cuda"), tol=1e-12, max_iter=5000)
+        b.set_preconditioner("block_rows")
+        worst = max(worst, float(np.linalg.norm(u - ref.cpu().numpy()) / np.linalg.norm(ref.cpu().numpy())))
+    # single-request latency per medium: the plain FP64 path (iterative online
+    # solve, FP64 factor sweeps) beside the map solve, device-resident data
+    single = []
+    for i, b in enumerate(bases):
+        phi_d = torch.tensor(pool[i][0], device="cuda")
+        rec = {}
+        for name in ("fp64_iterative", "map"):
+            ts = []
+            for _ in range(6):
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                if name == "map":
+                    b.solve_map(phi_d)
+                else:
+                    b.set_preconditioner("block_rows_fp64")
+                    b.solve(phi_d, tol=1e-8, max_iter=5000, want_iters=False)
+                    b.set_preconditioner("block_rows")
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - a) * 1e3)
+            rec[name + "_ms"] = float(np.median(ts[1:]))
+        single.append({"n_nodes": b.n_cells + 1, **rec})
+    ok = lat[~np.isnan(lat)]
+    line = {"metric": "online solve latency p50/p99 ms (serving)", "value": float(np.percentile(ok, 99)),
+            "unit": "ms (p99)", "higher_is_better": False, "n_gpus": 1,
+            "p50_ms": float(np.percentile(ok, 50)), "p99_ms": float(np.percentile(ok, 99)),
+            "requests": int(n_req), "completed": int(st["completed"]), "failed": int(st["failed"]),
+            "offered_rate_hz": args.rate, "throughput_hz": float(st["completed"] / (t_end - t_start)),
+            "batches": int(st["batches"]), "max_batch_seen": int(st["max_batch_seen"]),
+            "mem_peak_bytes": int(st["mem_peak"]), "workers": args.serve_workers,
+            "sample_checked": len(fetched), "sample_max_rel_err_vs_fp64": worst,
+            "single_request": single,
+            "setup_s": {"offline_3_media": t_offline, "maps": t_map},
+            "config": {"workload": wl["name"], "media": ["513^2 eps 2^-5", "1025^2 eps 2^-6", "2049^2 eps 2^-7"],
+                       "patch_cells": 64, "buffer": 16, "samples": 128,
+                       "data": "16-mode Fourier data, 64 distinct sets per medium, seeded"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1807_08848_gb300 as msp
@@ -381,11 +502,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "profile513"],
-                    help="profile513: one pass of the small 513^2 case for profiler captures")
+    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving"],
+                    help="profile513: one pass of the small 513^2 case for profiler captures; "
+                         "serving: the request loop over three prebuilt media")
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-mem-gb", type=float, default=16.0)
     args = ap.parse_args()
     if args.case == "profile513":
         run_profile_case(args)
+        return
+    if args.case == "serving":
+        run_serving(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -239,16 +239,27 @@ typedef struct {
     int online_factor_bits;    /* 32 or 64: precision the online factor was built in; 0 if the
                                   patch-block preconditioner is in use                         */
     float mean_jacobi_sweeps;  /* mean sweep count of the one-sided Jacobi SVDs over patches   */
+    int online_apply_bits;     /* 32 or 64: precision the factor sweeps run in; 0 if it depends
+                                  on the batch size (FP64 below 4 data sets) or as above       */
 } msp_basis_stats;
 msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out);
 
-/* Preconditioner of the online least-squares iteration:
+/* Preconditioner of the online least-squares iteration (the iteration itself,
+ * its residuals and iterates are FP64 in every case):
  *   MSP_PRECOND_BLOCK_ROWS (default): block-tridiagonal Cholesky of the scaled
- *     normal matrix over rows of patches (FP32 factor, FP64 iteration);
+ *     normal matrix over rows of patches.  Factorised in FP32 when that succeeds,
+ *     else in FP64.  An FP64 factor is applied in FP64 for batches of fewer than
+ *     4 data sets and through an FP32 rounded copy for larger batches (a few more
+ *     iterations, each sweep at the FP32 rate);
  *   MSP_PRECOND_PATCH_BLOCKS: the inverse patch blocks (P~^T P~)_mm^{-1} only
- *     (one-level additive Schwarz). */
-#define MSP_PRECOND_BLOCK_ROWS   0
-#define MSP_PRECOND_PATCH_BLOCKS 1
+ *     (one-level additive Schwarz);
+ *   MSP_PRECOND_BLOCK_ROWS_FP64: as BLOCK_ROWS, an FP64 factor always applied in FP64;
+ *   MSP_PRECOND_BLOCK_ROWS_FP32: as BLOCK_ROWS, an FP64 factor always applied
+ *     through its FP32 copy. */
+#define MSP_PRECOND_BLOCK_ROWS      0
+#define MSP_PRECOND_PATCH_BLOCKS    1
+#define MSP_PRECOND_BLOCK_ROWS_FP64 2
+#define MSP_PRECOND_BLOCK_ROWS_FP32 3
 msp_status msp_basis_set_preconditioner(msp_basis b, int kind);
 
 /* Total unknowns N_p = sum k_m and rows of P~. */
@@ -265,9 +276,65 @@ msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_rows);
  * max_iter; every data set's iteration is independent of the others in the
  * batch (fixed-order reductions).  iters_host (optional, [batch]) receives the
  * iteration counts and makes the call synchronise; NOT_CONVERGED if any data
- * set hit max_iter. */
+ * set hit max_iter.  u_dev may be NULL when c_dev is given (coefficients only,
+ * no reconstruction). */
 msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
                             double* u_dev, double* c_dev, int* iters_host, void* stream);
+
+/* Boundary-to-coefficient map.  The data of Eq. elliptic_cond_reduced enter only
+ * through the boundary rows, linearly, so c = G phi with G = P~^+ S (N_p x 4N; S
+ * places the ring values phi into the boundary rows).  msp_basis_build_map
+ * computes G column by column (online solves of the 4N unit ring vectors, to
+ * tolerance tol, in batches) and keeps it on the device in FP32 together with an
+ * FP32 copy of the bases; it synchronises and owns the memory until the basis
+ * is destroyed.  NOT_CONVERGED if a column stopped at max_iter.
+ * msp_online_solve_map then gives u for `batch` data sets phi_dev [batch][4N]
+ * (FP64) as u_dev [batch][N+1][N+1] (FP64): one FP32 GEMM c = G phi, the FP32
+ * reconstruction inside the patches and the FP64 skeleton average; stream
+ * ordered, and each data set's result does not depend on the rest of the batch.
+ * INVALID_ARG if the map has not been built.  The paper has no counterpart of
+ * the map; it is the serving form of the same least-squares solution. */
+msp_status msp_basis_build_map(msp_basis b, double tol, int max_iter, void* stream);
+msp_status msp_online_solve_map(msp_basis b, const double* phi_dev, int batch, double* u_dev, void* stream);
+
+/* -------------------------------------------------------------------- serving */
+
+/* A request loop over several prebuilt media (bases with their maps built):
+ * requests (a medium and its boundary data phi, host FP64 [4N]) are queued on
+ * submit; worker threads, each on its own CUDA stream, admit queued requests
+ * into batches of one medium, oldest request first, as long as the slot count
+ * (requests admitted and not yet released) stays within max_slots and the
+ * device memory they hold (phi and u of each request) within mem_budget_bytes;
+ * each batch is one msp_online_solve_map call.  Batches of different workers run
+ * on the device at the same time, and a request that arrives while others are on
+ * the device is admitted as soon as slots and memory allow.  A result stays on
+ * the device until it is fetched or released.  Latency = submit to the host
+ * seeing the batch complete.  n_workers = 0: no threads; msp_server_step runs
+ * one admit + solve + retire cycle on the caller's stream.
+ * The server borrows the bases: they must outlive it. */
+typedef struct msp_server_s* msp_server;
+typedef struct {
+    long long submitted, completed, released, failed, batches;
+    int queued, in_flight, held, max_batch_seen;
+    long long mem_in_use, mem_peak;
+} msp_server_stats;
+msp_status msp_server_create(const msp_basis* media, int n_media, long long mem_budget_bytes, int max_slots,
+                             int max_batch, int n_workers, msp_server* out);
+/* Non-blocking: copies phi_host (4N values of the medium's ring). INVALID_ARG on a
+ * bad medium index; OOM if one request alone exceeds the memory budget. */
+msp_status msp_server_submit(msp_server s, int medium, const double* phi_host, uint64_t* req_id);
+/* Never blocks: done = 1 when the result is on the device (latency_ms optional),
+ * done = -1 if its batch failed (the status is returned). */
+msp_status msp_server_poll(msp_server s, uint64_t req_id, int* done, double* latency_ms);
+/* Copies a finished result to u_host ([N+1][N+1], host) and releases it. */
+msp_status msp_server_fetch(msp_server s, uint64_t req_id, double* u_host);
+/* Releases a finished result without copying it. */
+msp_status msp_server_release(msp_server s, uint64_t req_id);
+/* Manual mode (n_workers = 0): one admit + solve + retire cycle; *n_done (optional)
+ * receives the number of requests it completed. */
+msp_status msp_server_step(msp_server s, void* stream, int* n_done);
+msp_status msp_server_get_stats(msp_server s, msp_server_stats* out);
+void msp_server_destroy(msp_server s);
 
 /* --------------------------------------------------------------------- kinetic */
 

@@ -20,7 +20,7 @@ import torch
 from . import _native as N
 from ._native import MspError, MSP_FP64, MSP_MIXED
 
-__all__ = ["Medium", "Basis", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
+__all__ = ["Medium", "Basis", "Server", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
            "precision_code"]
 
 
@@ -176,8 +176,10 @@ class Basis:
         return {f: getattr(st, f) for f, _ in st._fields_}
 
     def set_preconditioner(self, kind: str):
-        """'block_rows' (block-tridiagonal factor, default) or 'patch_blocks'."""
-        code = {"block_rows": 0, "patch_blocks": 1}[kind]
+        """'block_rows' (block-tridiagonal factor, default), 'patch_blocks',
+        'block_rows_fp64' (an FP64 factor always applied in FP64) or
+        'block_rows_fp32' (an FP64 factor always applied through its FP32 copy)."""
+        code = {"block_rows": 0, "patch_blocks": 1, "block_rows_fp64": 2, "block_rows_fp32": 3}[kind]
         N.check(N.load().msp_basis_set_preconditioner(self._h, code))
 
     def k(self, m: int) -> int:
@@ -217,6 +219,83 @@ class Basis:
             u = u[0]
             c = c[0] if c is not None else None
         return (u, it, c) if want_c else (u, it)
+
+
+    def build_map(self, tol: float = 1e-10, max_iter: int = 5000, stream=None):
+        """Boundary-to-coefficient map c = G phi (FP32 on the device) for serving."""
+        N.check(N.load().msp_basis_build_map(self._h, tol, max_iter, _stream_ptr(stream)))
+
+    def solve_map(self, phi: torch.Tensor, stream=None, u: torch.Tensor | None = None) -> torch.Tensor:
+        """u for phi of shape (B, 4N) (or (4N,)) through the map."""
+        squeeze = phi.dim() == 1
+        phi = phi.reshape(-1, 4 * self.n_cells).to(dtype=torch.float64, device="cuda").contiguous()
+        B = phi.shape[0]
+        n = self.n_cells + 1
+        if u is None:
+            u = torch.empty((B, n, n), dtype=torch.float64, device="cuda")
+        N.check(N.load().msp_online_solve_map(self._h, _dptr(phi), B, _dptr(u), _stream_ptr(stream)))
+        return u[0] if squeeze else u
+
+
+class Server:
+    """Request loop over prebuilt media (bases with maps): submit boundary data,
+    poll, fetch.  Worker threads batch requests of one medium under slot and
+    device-memory limits; n_workers = 0 runs batches only on step()."""
+
+    def __init__(self, media: list, mem_budget_bytes: int, max_slots: int = 256, max_batch: int = 32,
+                 n_workers: int = 2):
+        arr = (C.c_void_p * len(media))(*[b._h.value if isinstance(b._h, C.c_void_p) else b._h for b in media])
+        h = C.c_void_p()
+        N.check(N.load().msp_server_create(arr, len(media), int(mem_budget_bytes), max_slots, max_batch, n_workers,
+                                           C.byref(h)))
+        self._h = h
+        self._media = list(media)   # keep the bases alive
+        self._n = [b.n_cells for b in media]
+
+    def submit(self, medium: int, phi) -> int:
+        phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(-1))
+        if phi.size != 4 * self._n[medium]:
+            raise ValueError("phi must hold the 4N ring values of the medium")
+        rid = C.c_uint64()
+        N.check(N.load().msp_server_submit(self._h, medium, phi.ctypes.data_as(C.POINTER(C.c_double)),
+                                           C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int):
+        """(done, latency_ms): done = 1 finished, 0 pending."""
+        d, lat = C.c_int(), C.c_double()
+        N.check(N.load().msp_server_poll(self._h, rid, C.byref(d), C.byref(lat)))
+        return d.value, lat.value
+
+    def fetch(self, rid: int, medium: int) -> np.ndarray:
+        n = self._n[medium] + 1
+        u = np.empty((n, n), dtype=np.float64)
+        N.check(N.load().msp_server_fetch(self._h, rid, u.ctypes.data_as(C.POINTER(C.c_double))))
+        return u
+
+    def release(self, rid: int):
+        N.check(N.load().msp_server_release(self._h, rid))
+
+    def step(self, stream=None) -> int:
+        n = C.c_int()
+        N.check(N.load().msp_server_step(self._h, _stream_ptr(stream), C.byref(n)))
+        return n.value
+
+    def stats(self) -> dict:
+        st = N.ServerStats()
+        N.check(N.load().msp_server_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if self._h:
+            N.load().msp_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class KineticMedium:

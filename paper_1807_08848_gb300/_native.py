@@ -47,7 +47,14 @@ class PatchInfo(C.Structure):
 class BasisStats(C.Structure):
     _fields_ = [("max_jacobi_sweeps", C.c_int), ("max_cholqr_tries", C.c_int), ("online_shift", C.c_float),
                 ("online_blocks", C.c_int), ("online_factor_bits", C.c_int),
-                ("mean_jacobi_sweeps", C.c_float)]
+                ("mean_jacobi_sweeps", C.c_float), ("online_apply_bits", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("released", C.c_int64),
+                ("failed", C.c_int64), ("batches", C.c_int64), ("queued", C.c_int), ("in_flight", C.c_int),
+                ("held", C.c_int), ("max_batch_seen", C.c_int), ("mem_in_use", C.c_int64),
+                ("mem_peak", C.c_int64)]
 
 
 class SolveStats(C.Structure):
@@ -91,6 +98,16 @@ SIGNATURES = {
     "msp_kinetic_basis_info": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_d)]),
     "msp_kinetic_online_solve": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "msp_online_solve": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
+    "msp_basis_build_map": (_i, [_vp, _d, _i, _vp]),
+    "msp_online_solve_map": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "msp_server_create": (_i, [C.POINTER(_vp), _i, C.c_int64, _i, _i, _i, C.POINTER(_vp)]),
+    "msp_server_submit": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_u64)]),
+    "msp_server_poll": (_i, [_vp, _u64, C.POINTER(_i), C.POINTER(_d)]),
+    "msp_server_fetch": (_i, [_vp, _u64, C.POINTER(_d)]),
+    "msp_server_release": (_i, [_vp, _u64]),
+    "msp_server_step": (_i, [_vp, _vp, C.POINTER(_i)]),
+    "msp_server_get_stats": (_i, [_vp, C.POINTER(ServerStats)]),
+    "msp_server_destroy": (None, [_vp]),
 }
 
 _lib = None

@@ -59,12 +59,28 @@ extern "C" msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_row
 extern "C" msp_status msp_online_solve(msp_basis b, const double* phi, int batch, double tol, int max_iter, double* u,
                                        double* c_dev, int* iters_host, void* stream) {
     clear_error();
-    MSP_CHECK_ARG(b && phi && u, "msp_online_solve: NULL argument");
+    MSP_CHECK_ARG(b && phi && (u || c_dev), "msp_online_solve: NULL argument");
     MSP_CHECK_ARG(batch >= 0, "msp_online_solve: negative batch");
     MSP_CHECK_ARG(tol > 0 && tol < 1, "msp_online_solve: tol must lie in (0, 1)");
     MSP_CHECK_ARG(max_iter >= 1, "msp_online_solve: max_iter must be >= 1");
     if (batch == 0) return MSP_OK;
     return online_solve(b->B, phi, batch, tol, max_iter, u, c_dev, iters_host, (cudaStream_t)stream);
+}
+
+extern "C" msp_status msp_basis_build_map(msp_basis b, double tol, int max_iter, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(b, "msp_basis_build_map: NULL basis");
+    MSP_CHECK_ARG(tol > 0 && tol < 1, "msp_basis_build_map: tol must lie in (0, 1)");
+    MSP_CHECK_ARG(max_iter >= 1, "msp_basis_build_map: max_iter must be >= 1");
+    return build_online_map(b->B, tol, max_iter, (cudaStream_t)stream);
+}
+
+extern "C" msp_status msp_online_solve_map(msp_basis b, const double* phi, int batch, double* u, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(b && phi && u, "msp_online_solve_map: NULL argument");
+    MSP_CHECK_ARG(batch >= 0, "msp_online_solve_map: negative batch");
+    if (batch == 0) return MSP_OK;
+    return online_solve_map(b->B, phi, batch, u, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out) {
@@ -75,6 +91,11 @@ extern "C" msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out) {
     out->online_shift = b->B.bt_shift;
     out->online_blocks = b->B.bt_q;
     out->mean_jacobi_sweeps = b->B.mean_jacobi_sweeps;
+    out->online_apply_bits = b->B.use_block_jacobi ? 0
+                             : (b->B.bt_prec == 1 ? 32
+                                                  : (b->B.bt_prec == 2 ? (b->B.bt_apply_mode == 1 ? 64
+                                                                          : b->B.bt_apply_mode == 2 ? 32 : 0)
+                                                                       : 0));
     out->online_factor_bits = b->B.use_block_jacobi ? 0 : (b->B.bt_prec == 2 ? 64 : (b->B.bt_prec == 1 ? 32 : 0));
     return MSP_OK;
 }
@@ -82,8 +103,10 @@ extern "C" msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out) {
 extern "C" msp_status msp_basis_set_preconditioner(msp_basis b, int kind) {
     clear_error();
     MSP_CHECK_ARG(b, "msp_basis_set_preconditioner: NULL basis");
-    MSP_CHECK_ARG(kind == MSP_PRECOND_BLOCK_ROWS || kind == MSP_PRECOND_PATCH_BLOCKS,
+    MSP_CHECK_ARG(kind == MSP_PRECOND_BLOCK_ROWS || kind == MSP_PRECOND_PATCH_BLOCKS ||
+                      kind == MSP_PRECOND_BLOCK_ROWS_FP64 || kind == MSP_PRECOND_BLOCK_ROWS_FP32,
                   "msp_basis_set_preconditioner: unknown preconditioner");
     b->B.use_block_jacobi = (kind == MSP_PRECOND_PATCH_BLOCKS);
+    b->B.bt_apply_mode = kind == MSP_PRECOND_BLOCK_ROWS_FP64 ? 1 : (kind == MSP_PRECOND_BLOCK_ROWS_FP32 ? 2 : 0);
     return MSP_OK;
 }

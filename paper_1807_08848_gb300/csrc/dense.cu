@@ -10,8 +10,7 @@ namespace {
 constexpr int TM = 64, TN = 64, TK = 16;
 
 template <class T, bool TRANS_A, bool TRANS_B>
-__global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDescT<T>* descs) {
-    const GemmDescT<T> D = descs[blockIdx.z];
+__device__ __forceinline__ void gemm_tile(const GemmDescT<T>& D) {
     const int tiles_m = (D.M + TM - 1) / TM;
     if (blockIdx.x >= tiles_m * ((D.N + TN - 1) / TN)) return;
     const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
@@ -71,6 +70,17 @@ __global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDescT<T>* d
         }
 }
 
+template <class T, bool TRANS_A, bool TRANS_B>
+__global__ void __launch_bounds__(256) gemm_batched_kernel(const GemmDescT<T>* descs) {
+    gemm_tile<T, TRANS_A, TRANS_B>(descs[blockIdx.z]);
+}
+
+// one GEMM whose descriptor travels as a kernel parameter (no device copy)
+template <class T, bool TRANS_A, bool TRANS_B>
+__global__ void __launch_bounds__(256) gemm_one_kernel(const GemmDescT<T> D) {
+    gemm_tile<T, TRANS_A, TRANS_B>(D);
+}
+
 template <class T, bool TA, bool TB>
 void launch(const GemmDescT<T>* d, int nb, dim3 grid, cudaStream_t s) {
     gemm_batched_kernel<T, TA, TB><<<grid, 256, 0, s>>>(d);
@@ -94,6 +104,19 @@ void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n
     }
 }
 
+template <class T>
+void gemm_one(const GemmDescT<T>& d, bool transA, bool transB, cudaStream_t s) {
+    if (d.M <= 0 || d.N <= 0) return;
+    const dim3 grid(((d.M + TM - 1) / TM) * ((d.N + TN - 1) / TN));
+    if (transA && transB) gemm_one_kernel<T, true, true><<<grid, 256, 0, s>>>(d);
+    else if (transA) gemm_one_kernel<T, true, false><<<grid, 256, 0, s>>>(d);
+    else if (transB) gemm_one_kernel<T, false, true><<<grid, 256, 0, s>>>(d);
+    else gemm_one_kernel<T, false, false><<<grid, 256, 0, s>>>(d);
+    count_launches(1);
+}
+
+template void gemm_one<float>(const GemmDescT<float>&, bool, bool, cudaStream_t);
+template void gemm_one<double>(const GemmDescT<double>&, bool, bool, cudaStream_t);
 template void gemm_batched<double>(const GemmDescT<double>*, int, int, int, bool, bool, cudaStream_t);
 template void gemm_batched<float>(const GemmDescT<float>*, int, int, int, bool, bool, cudaStream_t);
 

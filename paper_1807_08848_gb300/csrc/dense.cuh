@@ -35,6 +35,10 @@ template <class T>
 void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n, bool transA, bool transB,
                   cudaStream_t s);
 
+// One GEMM, descriptor passed by value (no device-side descriptor array).
+template <class T>
+void gemm_one(const GemmDescT<T>& d, bool transA, bool transB, cudaStream_t s);
+
 // Backwards-compatible FP64 entry (op(B) = B).
 inline void gemm_batched(const GemmDesc* descs_dev, int batch, int max_m, int max_n, bool transA, cudaStream_t s) {
     gemm_batched<double>(descs_dev, batch, max_m, max_n, transA, false, s);

@@ -153,7 +153,14 @@ struct Basis {
     float bt_shift = 0.f;
     DevBuf<double> bt_Fi;               // patch-block scaling R_m^{-1} = L_m^{-T} (H_mm = L_m L_m^T)
     int bt_prec = 0;                    // 1: FP32 factor, 2: FP64 factor
+    int bt_apply_mode = 0;              // FP64 factor applied: 0 by batch size, 1 in FP64, 2 through bt32
     std::vector<int> bt_elo, bt_ehi;    // per patch: range of coupled patches in the row above
+    DevBuf<int> d_bt_off;               // device copies of the block offsets (sweep kernel)
+    DevBuf<long long> d_bt_d_off, d_bt_e_off;
+    DevBuf<unsigned int> d_bt_bar;      // grid barrier of the sweep kernel: arrivals, generation, error
+    // boundary-to-coefficient map (serving): G (N_p x 4N, FP32) and FP32 bases
+    DevBuf<float> G32, Q32, E32;
+    bool map_built = false;
     BtStore<float> bt32;
     BtStore<double> bt64;
     DevBuf<double> w_s;                 // normal-equation residual s = P^T r
@@ -181,6 +188,17 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
                                     cudaStream_t s);
 msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst, cudaStream_t s);
 msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B);
+// boundary-to-coefficient map (serving)
+struct MapWork {
+    float* phi32 = nullptr;
+    float* c32 = nullptr;
+    double* e = nullptr;
+    int cap = 0;
+};
+msp_status map_work_alloc(const Basis& Bs, int max_batch, MapWork& w);
+void map_work_free(MapWork& w);
+msp_status build_online_map(Basis& Bs, double tol, int max_iter, cudaStream_t s);
+msp_status online_solve_map(const Basis& Bs, const double* phi, int batch, double* u, cudaStream_t s, MapWork* work);
 msp_status online_solve(Basis& B, const double* phi, int batch, double tol, int max_iter, double* u, double* c_out,
                         int* iters_host, cudaStream_t s);
 msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const std::vector<int>& row_slot,

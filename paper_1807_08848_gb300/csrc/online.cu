@@ -9,6 +9,7 @@
 // gets bit-identical results alone or inside any batch.
 #include "internal.h"
 #include "device_util.cuh"
+#include "dense.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -268,24 +269,32 @@ __global__ void update_p_kernel(OnArgs A, double* p, const double* z, const doub
     }
 }
 
-// interior nodes of every K_m: u = Q_m c_m (one CTA per patch)
-__global__ void recon_interior_kernel(OnArgs A, const PatchDev* patches, const long long* q_off, const double* Q,
-                                      const double* c, double* u, int N) {
+// interior nodes of every K_m: u = Q_m c_m (one CTA per patch); Q in FP64, or in
+// FP32 for the map-based serving path (FP32 products, FP32 accumulation)
+template <class TQ, class TC>
+__global__ void recon_interior_kernel(OnArgs A, const PatchDev* patches, const long long* q_off, const TQ* Q,
+                                      const TC* c, double* u, int N) {
     const int m = blockIdx.x, B = A.B, k = A.k[m];
     const PatchDev P = patches[m];
     const int wi = P.x1 - P.x0 - 1, hi = P.y1 - P.y0 - 1;
     if (wi <= 0 || hi <= 0) return;
     const int wk = P.x1 - P.x0 + 1;
-    const double* q = Q + q_off[m];
-    const double* cm = c + (long long)A.c_off[m] * B;
+    const TQ* q = Q + q_off[m];
+    const TC* cm = c + (long long)A.c_off[m] * B;
     const long long nn = (long long)(N + 1) * (N + 1);
     for (long long w = threadIdx.x; w < (long long)wi * hi * B; w += blockDim.x) {
         const int b = (int)(w % B);
         const long long node = w / B;
         const int ii = (int)(node % wi) + 1, jj = (int)(node / wi) + 1;
         const int loc = ii + jj * wk;
+        // products and partial sums of 16 terms in TQ, the partial sums added in FP64
         double a = 0.0;
-        for (int j = 0; j < k; ++j) a += q[loc + (long long)j * P.n_k] * cm[(long long)j * B + b];
+        for (int j0 = 0; j0 < k; j0 += 16) {
+            TQ part = TQ(0);
+            const int j1 = min(k, j0 + 16);
+            for (int j = j0; j < j1; ++j) part += q[loc + (long long)j * P.n_k] * (TQ)cm[(long long)j * B + b];
+            a += (double)part;
+        }
         u[(long long)b * nn + (long long)(P.y0 + jj) * (N + 1) + (P.x0 + ii)] = a;
     }
 }
@@ -321,14 +330,115 @@ __global__ void export_c_kernel(const double* c, double* out, int Np, int B) {
     }
 }
 
+
+// columns j0 .. j0+B-1 of the identity on the boundary ring: phi[b][i] = (i == j0 + b)
+__global__ void unit_ring_kernel(double* phi, int n4, int j0, int B) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n4 * B;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(t / n4), i = (int)(t % n4);
+        phi[t] = (i == j0 + b) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void to_f32_kernel(const double* src, float* dst, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
+}
+
+
+// c[j][b] = sum_k G[j][k] phi32[b][k] (G: Np x n4 column-major; phi32: [b][n4];
+// c element-major, as the reconstruction reads it).  64 x 64 output tiles (64
+// unknowns x up to 64 data sets; columns past the batch are skipped per 16-wide
+// group), 16-deep K slices staged in shared memory; products and sums of 128
+// consecutive terms in FP32, those partial sums accumulated in FP64 (at a
+// sixty-fourth of the FP32 work, so the FP64 pipe keeps pace), so the rounding of
+// the long K sum does not grow with the ring length; the total is rounded to FP32.
+__global__ void __launch_bounds__(256) map_gemm_kernel(const float* G, const float* phi32, float* c, int Np, int n4,
+                                                       int B) {
+    constexpr int TM = 64, TN = 64, TK = 16, KF = 8;   // KF slices per FP64 accumulation
+    __shared__ float Gs[TK][TM + 1];
+    __shared__ float Ps[TK][TN + 1];
+    const int tiles_m = (Np + TM - 1) / TM;
+    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+    const int m0 = tm * TM, n0 = tn * TN;
+    if (n0 >= B) return;
+    const int jmax = min(4, (B - n0 + 15) / 16);   // 16-wide column groups holding data sets (uniform per CTA)
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    float part[4][4] = {};
+    int slice = 0;
+    for (int k0 = 0; k0 < n4; k0 += TK) {
+        for (int e = threadIdx.x; e < TM * TK; e += 256) {
+            const int mm = e % TM, kk = e / TM;
+            const int gm = m0 + mm, gk = k0 + kk;
+            Gs[kk][mm] = (gm < Np && gk < n4) ? G[(long long)gk * Np + gm] : 0.f;
+        }
+        for (int e = threadIdx.x; e < jmax * 16 * TK; e += 256) {
+            const int kk = e % TK, nn = e / TK;
+            const int gk = k0 + kk, gn = n0 + nn;
+            Ps[kk][nn] = (gk < n4 && gn < B) ? phi32[(long long)gn * n4 + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Gs[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = (j < jmax) ? Ps[kk][ty + 16 * j] : 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j < jmax) part[i][j] = fmaf(a[i], b[j], part[i][j]);
+        }
+        if (++slice == KF || k0 + TK >= n4) {
+            slice = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (j < jmax) acc[i][j] += (double)part[i][j];
+                    part[i][j] = 0.f;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + tx + 16 * i, gn = n0 + ty + 16 * j;
+            if (j < jmax && gm < Np && gn < B) c[(long long)gm * B + gn] = (float)acc[i][j];
+        }
+}
+// Value slots of the edge operators for the map path: e[slot][b] for the even
+// (value) slots of every patch, from FP32 operators and coefficients, partial
+// sums of 16 terms in FP32 added in FP64.  Only the skeleton averages read them.
+__global__ void edge_values_map_kernel(OnArgs A, const float* E32, const float* c32, double* e) {
+    const int m = blockIdx.x, k = A.k[m], nt = A.ne[m], B = A.B;
+    const float* Em = E32 + A.e_off[m];
+    const float* xm = c32 + (long long)A.c_off[m] * B;
+    double* em = e + (long long)A.slot_off[m] * B;
+    for (int w = threadIdx.x; w < nt * B; w += blockDim.x) {
+        const int t = w / B, b = w - t * B;
+        const float* er = Em + (long long)(2 * t) * k;
+        double a = 0.0;
+        for (int j0 = 0; j0 < k; j0 += 16) {
+            float part = 0.f;
+            const int j1 = min(k, j0 + 16);
+            for (int j = j0; j < j1; ++j) part = fmaf(er[j], xm[(long long)j * B + b], part);
+            a += (double)part;
+        }
+        em[(long long)(2 * t) * B + b] = a;
+    }
+}
+
 }  // namespace
 
-static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, int max_iter, double* u,
-                               double* c_out, int* iters_host, cudaStream_t s, bool* not_conv) {
-    const int np = (int)Bs.patches.size();
-    const int N = Bs.N, n4 = 4 * N;
+static OnArgs make_args(const Basis& Bs, int B) {
     OnArgs A{};
-    A.np = np;
+    A.np = (int)Bs.patches.size();
     A.B = B;
     A.n_rows = Bs.n_rows;
     A.n_chunks = (Bs.n_rows + kRowChunk - 1) / kRowChunk;
@@ -336,6 +446,14 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
     A.e_off = Bs.d_e_off.p; A.binv_off = Bs.d_binv_off.p; A.E = Bs.E.p; A.Binv = Bs.Binv.p;
     A.row_ptr = Bs.row_ptr.p; A.row_slot = Bs.row_slot.p; A.row_bnd = Bs.row_bnd.p;
     A.tr_ptr = Bs.tr_ptr.p; A.tr_ent = Bs.tr_ent.p;
+    return A;
+}
+
+static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, int max_iter, double* u,
+                               double* c_out, int* iters_host, cudaStream_t s, bool* not_conv) {
+    const int np = (int)Bs.patches.size();
+    const int N = Bs.N, n4 = 4 * N;
+    OnArgs A = make_args(Bs, B);
     if (Bs.cap_batch < B) {
         const int cb = kMaxBatch;
         MSP_TRY(Bs.w_c.alloc((size_t)std::max(Bs.Np, 1) * cb, s));
@@ -412,9 +530,10 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
             if (all) break;
         }
     }
-    // reconstruction
+    // reconstruction (skipped when only the coefficients are asked for)
     const long long nn = (long long)(N + 1) * (N + 1);
-    recon_interior_kernel<<<np, 256, 0, s>>>(A, Bs.d_patches.p, Bs.d_q_off.p, Bs.Q.p, Bs.w_c.p, u, N);
+    if (u) {
+    recon_interior_kernel<double, double><<<np, 256, 0, s>>>(A, Bs.d_patches.p, Bs.d_q_off.p, Bs.Q.p, Bs.w_c.p, u, N);
     count_launches(1);
     edge_apply_kernel<<<np, 256, 0, s>>>(A, Bs.w_c.p, Bs.w_e.p);
     count_launches(1);
@@ -422,6 +541,7 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
     recon_skeleton_kernel<<<sk_grid, 256, 0, s>>>(A, Bs.n_skel, Bs.sk_ptr.p, Bs.sk_slot.p, Bs.sk_node.p, Bs.sk_ring.p,
                                                   Bs.w_e.p, phi, n4, u, N);
     count_launches(1);
+    }
     if (c_out) {
         export_c_kernel<<<ew_grid, 256, 0, s>>>(Bs.w_c.p, c_out, Bs.Np, B);
         count_launches(1);
@@ -434,6 +554,16 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
         for (int b = 0; b < B; ++b) {
             iters_host[b] = (int)scal[8 * b + 5];
             if (scal[8 * b + 4] != 1.0) *not_conv = true;
+        }
+    }
+    if (Bs.d_bt_bar.p) {   // the sweep kernel's grid barrier reports a timeout here
+        unsigned int h[4] = {0, 0, 0, 0};
+        MSP_CUDA(cudaMemcpyAsync(h, Bs.d_bt_bar.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        MSP_CUDA(cudaStreamSynchronize(s));
+        if (h[2] != 0) {
+            MSP_CUDA(cudaMemsetAsync(Bs.d_bt_bar.p, 0, sizeof(h), s));
+            set_error("msp_online_solve: grid barrier of the factor sweeps timed out");
+            return MSP_ERR_TIMEOUT;
         }
     }
     return MSP_OK;
@@ -458,7 +588,7 @@ msp_status online_solve(Basis& Bs, const double* phi, int batch, double tol, int
     const int cap = online_batch_cap(Bs);
     for (int b0 = 0; b0 < batch; b0 += cap) {
         const int B = std::min(cap, batch - b0);
-        MSP_TRY(online_batch(Bs, phi + (long long)b0 * 4 * N, B, tol, max_iter, u + (long long)b0 * nn,
+        MSP_TRY(online_batch(Bs, phi + (long long)b0 * 4 * N, B, tol, max_iter, u ? u + (long long)b0 * nn : nullptr,
                              c_out ? c_out + (long long)b0 * Bs.Np : nullptr, iters_host ? iters_host + b0 : nullptr, s,
                              &not_conv));
     }
@@ -467,6 +597,123 @@ msp_status online_solve(Basis& Bs, const double* phi, int batch, double tol, int
         return MSP_ERR_NOT_CONVERGED;
     }
     return MSP_OK;
+}
+
+// Boundary-to-coefficient map.  The data of Eq. elliptic_cond_reduced enter only
+// through the boundary rows and linearly, so c = G phi with G = P~^+ S (S puts the
+// ring values into the boundary rows).  Column j of G is the online solution for
+// the j-th unit vector of the ring; the columns are computed in batches by the
+// FP64 iteration above, to tolerance tol, and stored in FP32 (N_p x 4N,
+// column-major), with an FP32 copy of the bases for the reconstruction.
+msp_status build_online_map(Basis& Bs, double tol, int max_iter, cudaStream_t s) {
+    const int N = Bs.N, n4 = 4 * N, Np = Bs.Np;
+    MSP_TRY(Bs.G32.alloc(std::max<long long>((long long)Np * n4, 1), s));
+    const int cap = online_batch_cap(Bs);
+    DevBuf<double> phi, c64;
+    MSP_TRY(phi.alloc((size_t)n4 * cap, s));
+    MSP_TRY(c64.alloc((size_t)std::max(Np, 1) * cap, s));
+    std::vector<int> iters(cap);
+    for (int j0 = 0; j0 < n4; j0 += cap) {
+        const int B = std::min(cap, n4 - j0);
+        unit_ring_kernel<<<std::max(1, std::min(1024, (n4 * B + 255) / 256)), 256, 0, s>>>(phi.p, n4, j0, B);
+        count_launches(1);
+        bool not_conv = false;
+        MSP_TRY(online_batch(Bs, phi.p, B, tol, max_iter, nullptr, c64.p, iters.data(), s, &not_conv));
+        if (not_conv) {
+            set_error("msp_basis_build_map: a ring unit vector stopped at max_iter");
+            return MSP_ERR_NOT_CONVERGED;
+        }
+        const long long n = (long long)Np * B;
+        to_f32_kernel<<<std::max(1, (int)std::min<long long>(2048, (n + 255) / 256)), 256, 0, s>>>(
+            c64.p, Bs.G32.p + (long long)j0 * Np, n);
+        count_launches(1);
+    }
+    long long nq = 0;
+    for (size_t m = 0; m < Bs.patches.size(); ++m) nq = std::max<long long>(nq, Bs.q_off[m] + (long long)Bs.patches[m].n_k * Bs.k[m]);
+    MSP_TRY(Bs.E32.alloc(std::max<size_t>(Bs.E.n, 1), s));
+    to_f32_kernel<<<std::max(1, (int)std::min<long long>(4096, ((long long)Bs.E.n + 255) / 256)), 256, 0, s>>>(
+        Bs.E.p, Bs.E32.p, (long long)Bs.E.n);
+    count_launches(1);
+    MSP_TRY(Bs.Q32.alloc(std::max<long long>(nq, 1), s));
+    to_f32_kernel<<<std::max(1, (int)std::min<long long>(4096, (nq + 255) / 256)), 256, 0, s>>>(Bs.Q.p, Bs.Q32.p, nq);
+    count_launches(1);
+    MSP_CUDA(cudaGetLastError());
+    MSP_CUDA(cudaStreamSynchronize(s));
+    Bs.map_built = true;
+    return MSP_OK;
+}
+
+// u = reconstruction of c = G phi for a batch (map built).  The work buffers are
+// the caller's (MapWork, sized for max_batch data sets) or the call's own; with
+// its own MapWork per stream, calls on different streams run at the same time.
+// Each data set's result does not depend on the others in the batch.
+msp_status map_work_alloc(const Basis& Bs, int max_batch, MapWork& w) {
+    const int n4 = 4 * Bs.N;
+    const size_t B = (size_t)std::max(1, max_batch);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.phi32, sizeof(float) * n4 * B);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.c32, sizeof(float) * std::max(Bs.Np, 1) * B);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.e, sizeof(double) * std::max(Bs.n_slots, 1) * B);
+    w.cap = (int)B;
+    if (e != cudaSuccess) {
+        map_work_free(w);
+        set_error(std::string("map work buffers: ") + cudaGetErrorString(e));
+        return MSP_ERR_OOM;
+    }
+    return MSP_OK;
+}
+
+void map_work_free(MapWork& w) {
+    if (w.phi32) cudaFree(w.phi32);
+    if (w.c32) cudaFree(w.c32);
+    if (w.e) cudaFree(w.e);
+    w = MapWork{};
+}
+
+msp_status online_solve_map(const Basis& Bs, const double* phi, int batch, double* u, cudaStream_t s, MapWork* work) {
+    if (!Bs.map_built) {
+        set_error("msp_online_solve_map: the boundary-to-coefficient map has not been built");
+        return MSP_ERR_INVALID_ARG;
+    }
+    const int N = Bs.N, n4 = 4 * N, Np = Bs.Np, np = (int)Bs.patches.size();
+    const long long nn = (long long)(N + 1) * (N + 1);
+    MapWork own{};
+    if (!work) {
+        MSP_TRY(map_work_alloc(Bs, std::min(batch, kMaxBatch), own));
+        work = &own;
+    }
+    msp_status st = MSP_OK;
+    for (int b0 = 0; b0 < batch && st == MSP_OK; b0 += work->cap) {
+        const int B = std::min(work->cap, batch - b0);
+        const double* ph = phi + (long long)b0 * n4;
+        to_f32_kernel<<<std::max(1, std::min(1024, (n4 * B + 255) / 256)), 256, 0, s>>>(ph, work->phi32, (long long)n4 * B);
+        count_launches(1);
+        {
+            const int tiles = ((Np + 63) / 64) * ((B + 63) / 64);
+            map_gemm_kernel<<<tiles, 256, 0, s>>>(Bs.G32.p, work->phi32, work->c32, Np, n4, B);
+            count_launches(1);
+        }
+        OnArgs A = make_args(Bs, B);
+        double* ub = u + (long long)b0 * nn;
+        recon_interior_kernel<float, float><<<np, 256, 0, s>>>(A, Bs.d_patches.p, Bs.d_q_off.p, Bs.Q32.p, work->c32, ub, N);
+        count_launches(1);
+        edge_values_map_kernel<<<np, 256, 0, s>>>(A, Bs.E32.p, work->c32, work->e);
+        count_launches(1);
+        const int sk_grid = std::max(1, std::min<int>((int)(((long long)Bs.n_skel * B + 255) / 256), num_sms() * 8));
+        recon_skeleton_kernel<<<sk_grid, 256, 0, s>>>(A, Bs.n_skel, Bs.sk_ptr.p, Bs.sk_slot.p, Bs.sk_node.p,
+                                                      Bs.sk_ring.p, work->e, ph, n4, ub, N);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error(std::string("msp_online_solve_map: ") + cudaGetErrorString(e));
+            st = MSP_ERR_CUDA;
+        }
+    }
+    if (work == &own) {
+        cudaStreamSynchronize(s);
+        map_work_free(own);
+    }
+    return st;
 }
 
 }  // namespace msp

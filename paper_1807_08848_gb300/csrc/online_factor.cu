@@ -69,6 +69,11 @@ __global__ void scale_convert_kernel(const double* src, T* dst, int nr, int nc, 
     }
 }
 
+__global__ void round_kernel(const double* src, float* dst, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
+}
+
 // per-patch products with R_m^{-1} = F_m (upper, k x k column-major):
 // y = F^T s (FP64 in, FP32 out) before the sweeps, z = F x (FP32 in, FP64 out) after
 template <class T>
@@ -192,6 +197,146 @@ __global__ void sb_gemm_kernel(const T* X, const T* M, int ldm, T* Y, int K, int
                 *y = (beta == T(0)) ? alpha * v : alpha * v + beta * (*y);
             }
         }
+    }
+}
+
+// Both triangular sweeps of the block-row factor in one persistent cooperative
+// launch.  Each sweep is a chain of products Y = alpha X M + beta Y (X: [K][B]
+// rows of the work vector, M: K x ncols column-major) whose steps depend on one
+// another, so every product is spread over all warps of the grid (one output
+// column per warp at a time, lanes along K) and a grid barrier separates the
+// steps.  The barrier spins with a bound: on timeout it raises *err and every
+// CTA leaves at its next barrier.
+template <class T>
+struct SweepArgs {
+    int Qn, B;
+    const int* off;            // [Qn + 1] element offsets of the blocks
+    const long long* d_off;    // [Qn] offsets of L_q^{-1} (and its transpose)
+    const long long* e_off;    // [Qn - 1] offsets of C_q (and its transpose)
+    const T* LiT;
+    const T* FT;
+    const T* Li;
+    const T* F;
+    T* y;
+    T* x;
+    unsigned int* bar;         // [0] arrivals, [1] generation
+    int* err;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int& gen, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int target = gen + 1;
+        if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], target);
+        } else {
+            const volatile unsigned int* g = bar + 1;
+            const volatile int* e = err;
+            long long spins = 0;
+            while (*g != target) {
+                if (++spins > (1LL << 24) || *e != 0) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    ++gen;
+    __syncthreads();
+    return *((volatile int*)err) == 0;
+}
+
+// Y[j][b] = alpha sum_k M[k][j] X[k][b] + beta Y[j][b] for b < B, spread over the
+// whole grid: one output column per warp and round, lanes along K.  The rows of X
+// needed by a K chunk are staged in shared memory by every CTA (all CTAs run the
+// same rounds and chunks, so the block barriers are uniform).
+constexpr int kSweepKC = 1024;
+template <class T, int BT>
+__device__ __forceinline__ void sweep_product(const T* X, const T* M, int ldm, T* Y, int K, int ncols, int B, T alpha,
+                                              T beta, int gw, int nw, int lane, T* xs) {
+    for (int j0 = 0; j0 < ncols; j0 += nw) {
+        const int j = j0 + gw;
+        const bool live = j < ncols;
+        const T* mj = M + (long long)(live ? j : 0) * ldm;
+        for (int b0 = 0; b0 < B; b0 += BT) {
+            const int bt = min(BT, B - b0);
+            T acc[BT];
+#pragma unroll
+            for (int t = 0; t < BT; ++t) acc[t] = T(0);
+            for (int kc = 0; kc < K; kc += kSweepKC) {
+                const int kn = min(kSweepKC, K - kc);
+                __syncthreads();
+                for (int e = threadIdx.x; e < kn * bt; e += blockDim.x) {
+                    const int kk = e / bt, t = e - kk * bt;
+                    xs[t * kSweepKC + kk] = __ldcg(X + (long long)(kc + kk) * B + b0 + t);
+                }
+                __syncthreads();
+                if (live) {
+#pragma unroll 8
+                    for (int kk = lane; kk < kn; kk += 32) {
+                        const T m = mj[kc + kk];
+#pragma unroll
+                        for (int t = 0; t < BT; ++t) acc[t] = fma(m, xs[t * kSweepKC + kk], acc[t]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < BT; ++t) {
+                const T v = warp_sum(acc[t]);
+                if (live && lane == 0 && t < bt) {
+                    T* yp = Y + (long long)j * B + b0 + t;
+                    *yp = (beta == T(0)) ? alpha * v : alpha * v + beta * __ldcg(yp);
+                }
+            }
+        }
+    }
+}
+
+template <class T, int BT>
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char sweep_smem[];
+    T* xs = reinterpret_cast<T*>(sweep_smem);   // kSweepKC x BT
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+    unsigned int gen = atomicAdd(&A.bar[1], 0u);
+    const int B = A.B;
+    // forward: y_q -= x_{q-1} C_{q-1}^T;  x_q = y_q Li_q^T
+    for (int q = 0; q < A.Qn; ++q) {
+        const int o = A.off[q], nq = A.off[q + 1] - o;
+        if (nq == 0) continue;
+        if (q > 0) {
+            const int o0 = A.off[q - 1], n0 = o - o0;
+            if (n0 > 0) {
+                sweep_product<T, BT>(A.x + (long long)o0 * B, A.FT + A.e_off[q - 1], n0, A.y + (long long)o * B, n0, nq,
+                                     B, T(-1), T(1), gw, nw, lane, xs);
+                if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+            }
+        }
+        sweep_product<T, BT>(A.y + (long long)o * B, A.LiT + A.d_off[q], nq, A.x + (long long)o * B, nq, nq, B, T(1),
+                             T(0), gw, nw, lane, xs);
+        if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+    }
+    // backward: x_q -= z_{q+1} C_q;  z_q = x_q Li_q   (z into y)
+    for (int q = A.Qn - 1; q >= 0; --q) {
+        const int o = A.off[q], nq = A.off[q + 1] - o;
+        if (nq == 0) continue;
+        if (q + 1 < A.Qn) {
+            const int o1 = A.off[q + 1], n1 = A.off[q + 2] - o1;
+            if (n1 > 0) {
+                sweep_product<T, BT>(A.y + (long long)o1 * B, A.F + A.e_off[q], n1, A.x + (long long)o * B, n1, nq, B,
+                                     T(-1), T(1), gw, nw, lane, xs);
+                if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+            }
+        }
+        sweep_product<T, BT>(A.x + (long long)o * B, A.Li + A.d_off[q], nq, A.y + (long long)o * B, nq, nq, B, T(1), T(0),
+                             gw, nw, lane, xs);
+        if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
     }
 }
 
@@ -608,6 +753,21 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
         if (!fail) {
             B.bt_prec = 2;
             B.bt_shift = (float)shifts[a];
+            // FP32 rounded copy of the factor for the sweeps: the rounded factor is a
+            // preconditioner within about u32 kappa(L) = u32 kappa(H)^(1/2) of the
+            // exact one, so the FP64 iteration needs a few more steps, each sweep at
+            // the FP32 rate
+            const long long nd = std::max<long long>(B.bt_diag_elems, 1), nt = std::max<long long>(total, 1);
+            MSP_TRY(B.bt32.F.alloc(nt, s));
+            MSP_TRY(B.bt32.FT.alloc(nt, s));
+            MSP_TRY(B.bt32.Li.alloc(nd, s));
+            MSP_TRY(B.bt32.LiT.alloc(nd, s));
+            round_kernel<<<grid_for(nt), 256, 0, s>>>(B.bt64.F.p, B.bt32.F.p, nt);
+            round_kernel<<<grid_for(nt), 256, 0, s>>>(B.bt64.FT.p, B.bt32.FT.p, nt);
+            round_kernel<<<grid_for(nd), 256, 0, s>>>(B.bt64.Li.p, B.bt32.Li.p, nd);
+            round_kernel<<<grid_for(nd), 256, 0, s>>>(B.bt64.LiT.p, B.bt32.LiT.p, nd);
+            count_launches(4);
+            MSP_CUDA(cudaGetLastError());
             return MSP_OK;
         }
     }
@@ -616,6 +776,60 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
 }
 
 // z = S (L L^T)^{-1} S s for a batch of Bsz vectors ([element][B] layout, FP64 in and out)
+// Cooperative launch of sweep_kernel: the grid is as many CTAs as are resident
+// at once (at most two per SM), so the grid barrier cannot wait on an unscheduled CTA.
+template <class T, int BT>
+msp_status launch_sweeps_bt(SweepArgs<T> A, cudaStream_t s) {
+    static int grid = 0;
+    const size_t smem = sizeof(T) * kSweepKC * BT;
+    if (grid == 0) {
+        MSP_CUDA(cudaFuncSetAttribute(sweep_kernel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        MSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<T, BT>, 512, smem));
+        if (occ < 1) {
+            set_error("online sweeps: the sweep kernel does not fit on an SM");
+            return MSP_ERR_CUDA;
+        }
+        grid = num_sms() * std::min(occ, 2);
+    }
+    void* params[] = {&A};
+    MSP_CUDA(cudaLaunchCooperativeKernel((const void*)sweep_kernel<T, BT>, dim3(grid), dim3(512), params, smem, s));
+    count_launches(1);
+    return MSP_OK;
+}
+
+template <class T>
+msp_status launch_sweeps(Basis& B, BtStore<T>& S, T* y, T* x, int Bsz, cudaStream_t s) {
+    if (B.bt_q <= 0) return MSP_OK;
+    if (!B.d_bt_off.p) {
+        std::vector<long long> eo(B.bt_e_off);
+        if (eo.empty()) eo.push_back(0);
+        MSP_TRY(upload(B.d_bt_off, B.bt_off, s));
+        MSP_TRY(upload(B.d_bt_d_off, B.bt_d_off, s));
+        MSP_TRY(upload(B.d_bt_e_off, eo, s));
+        MSP_TRY(B.d_bt_bar.alloc(4, s));
+        MSP_CUDA(cudaMemsetAsync(B.d_bt_bar.p, 0, sizeof(unsigned int) * 4, s));
+    }
+    SweepArgs<T> A{};
+    A.Qn = B.bt_q;
+    A.B = Bsz;
+    A.off = B.d_bt_off.p;
+    A.d_off = B.d_bt_d_off.p;
+    A.e_off = B.d_bt_e_off.p;
+    A.LiT = S.LiT.p;
+    A.FT = S.FT.p;
+    A.Li = S.Li.p;
+    A.F = S.F.p;
+    A.y = y;
+    A.x = x;
+    A.bar = B.d_bt_bar.p;
+    A.err = reinterpret_cast<int*>(B.d_bt_bar.p + 2);
+    if (Bsz <= 1) return launch_sweeps_bt<T, 1>(A, s);
+    if (Bsz <= 2) return launch_sweeps_bt<T, 2>(A, s);
+    if (Bsz <= 4) return launch_sweeps_bt<T, 4>(A, s);
+    return launch_sweeps_bt<T, 8>(A, s);
+}
+
 template <class T>
 msp_status apply_factor(Basis& B, BtStore<T>& S, const double* s_in, double* z_out, int Bsz, cudaStream_t s) {
     const long long n = B.Np;
@@ -629,37 +843,7 @@ msp_status apply_factor(Basis& B, BtStore<T>& S, const double* s_in, double* z_o
     const int np = (int)B.patches.size();
     patch_pre_kernel<T><<<np, 256, 0, s>>>(B.bt_Fi.p, B.d_binv_off.p, B.d_k.p, B.d_c_off.p, s_in, y, Bsz);
     count_launches(1);
-    const int Qn = B.bt_q;
-    const int wpb = 8;   // warps per block of the small-batch products
-    auto prod = [&](const T* X, const T* M, int ldm, T* Y, int K, int ncols, T alpha, T beta) {
-        if (K <= 0 || ncols <= 0) return;
-        sb_gemm_kernel<T><<<(ncols + wpb - 1) / wpb, 32 * wpb, 0, s>>>(X, M, ldm, Y, K, ncols, Bsz, alpha, beta);
-        count_launches(1);
-    };
-    // forward: y_q -= x_{q-1} C_{q-1}^T;  x_q = y_q Li_q^T   (row vectors, [element][B])
-    for (int q = 0; q < Qn; ++q) {
-        const int nq = B.bt_off[q + 1] - B.bt_off[q];
-        if (nq == 0) continue;
-        T* yq = y + (long long)B.bt_off[q] * Bsz;
-        T* xq = x + (long long)B.bt_off[q] * Bsz;
-        if (q > 0) {
-            const int n0 = B.bt_off[q] - B.bt_off[q - 1];
-            prod(x + (long long)B.bt_off[q - 1] * Bsz, S.FT.p + B.bt_e_off[q - 1], n0, yq, n0, nq, T(-1), T(1));
-        }
-        prod(yq, S.LiT.p + B.bt_d_off[q], nq, xq, nq, nq, T(1), T(0));
-    }
-    // backward: x_q -= z_{q+1} C_q;  z_q = x_q Li_q   (z written into y)
-    for (int q = Qn - 1; q >= 0; --q) {
-        const int nq = B.bt_off[q + 1] - B.bt_off[q];
-        if (nq == 0) continue;
-        T* xq = x + (long long)B.bt_off[q] * Bsz;
-        T* zq = y + (long long)B.bt_off[q] * Bsz;
-        if (q + 1 < Qn) {
-            const int n1 = B.bt_off[q + 2] - B.bt_off[q + 1];
-            prod(y + (long long)B.bt_off[q + 1] * Bsz, S.F.p + B.bt_e_off[q], n1, xq, n1, nq, T(-1), T(1));
-        }
-        prod(xq, S.Li.p + B.bt_d_off[q], nq, zq, nq, nq, T(1), T(0));
-    }
+    MSP_TRY(launch_sweeps<T>(B, S, y, x, Bsz, s));
     patch_post_kernel<T><<<np, 256, 0, s>>>(B.bt_Fi.p, B.d_binv_off.p, B.d_k.p, B.d_c_off.p, y, z_out, Bsz);
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
@@ -667,8 +851,14 @@ msp_status apply_factor(Basis& B, BtStore<T>& S, const double* s_in, double* z_o
 }
 
 
+constexpr int kApply32MinBatch = 4;
+
 msp_status apply_online_factor(Basis& B, const double* s_in, double* z_out, int Bsz, cudaStream_t s) {
-    if (B.bt_prec == 2) return apply_factor<double>(B, B.bt64, s_in, z_out, Bsz, s);
+    // an FP64 factor: applied in FP64 for small batches (fewest iterations, the
+    // sweeps are latency-bound there), through its FP32 copy for larger ones (the
+    // sweeps become arithmetic-bound)
+    if (B.bt_prec == 2 && (B.bt_apply_mode == 1 || (B.bt_apply_mode == 0 && Bsz < kApply32MinBatch)))
+        return apply_factor<double>(B, B.bt64, s_in, z_out, Bsz, s);
     return apply_factor<float>(B, B.bt32, s_in, z_out, Bsz, s);
 }
 
