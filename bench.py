@@ -425,6 +425,29 @@ def run_ours(args, rank, world):
     stages["basis_stats"] = sbasis.stats()
     del smed, sbasis
 
+    # ---- the streaming matrix-free operator on the same tiles (every patch x every
+    # Gaussian sample, FP32): HBM-bound, reported against the measured copy bandwidth
+    stencil = None
+    if args.stencil:
+        omed = msp.Medium(w["medium"], w["patches"])
+        rows, cols = omed.tile_shape()
+        pitch = (cols + 3) // 4 * 4
+        S = int(w["patches"].samples[0])
+        xs = torch.randn((omed.n_patches, S, rows, pitch), dtype=torch.float32, device="cuda")
+        ys = torch.empty_like(xs)
+        for _ in range(3):
+            omed.apply_operator(xs, "mixed", y=ys)
+        times = [omed.apply_operator(xs, "mixed", y=ys, timed=True)[1] for _ in range(5)]
+        t_st = float(np.median(times)) / 1e3
+        nodes = sum((p.X1 - p.X0 + 1) * (p.Y1 - p.Y0 + 1) for p in (omed.patch(m) for m in range(omed.n_patches)))
+        alg = nodes * S * 8.0 + nodes * 8.0          # x read + y written per sample; faces once per patch
+        hbm = peaks().get("hbm_gbs", 6800.0)
+        stencil = {"kernel": "stencil_apply_kernel<float>", "tiles": omed.n_patches * S,
+                   "tile": f"{rows}x{pitch} (pitch)", "ms": t_st * 1e3, "algorithmic_bytes": alg,
+                   "achieved_gbs": alg / t_st / 1e9, "peak_gbs": hbm, "frac": alg / t_st / 1e9 / hbm,
+                   "l2": "inputs 5 GB > L2"}
+        del xs, ys, omed
+
     # ---- the plain FP64 path's local solves on the same medium, for comparison
     fp64_rate = None
     if args.compare_fp64 and prec == "mixed":
@@ -473,6 +496,7 @@ def run_ours(args, rank, world):
                         "avg_cg_iters": stats.total_iters / max(1, n_solves),
                         "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged},
         "fp64_path_local_solve": fp64_rate,
+        "stencil_apply": stencil,
         "stages": stages,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -500,6 +524,8 @@ def main():
     ap.add_argument("--online-reqs", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-stencil", dest="stencil", action="store_false",
+                    help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
     ap.add_argument("--case", default="full", choices=["full", "profile513", "serving"],

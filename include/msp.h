@@ -265,6 +265,24 @@ msp_status msp_basis_set_preconditioner(msp_basis b, int kind);
 /* Total unknowns N_p = sum k_m and rows of P~. */
 msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_rows);
 
+/* Matrix-free 5-point operator of the local problems (Sec. 5; the finite-
+ * difference reading: (A u)_ij = sum over the faces f of node (i, j) of
+ * a_f (u_ij - u_nbr(f))) applied to a stack of tiles: for every patch m and sample
+ * s < samples, y = A x on the interior nodes of the buffered box K~_m, with the
+ * ring values taken from x; y = 0 on the ring and in the padding.
+ *   x_dev, y_dev: [patch][sample][rows][pitch] device arrays of float
+ *     (precision MSP_MIXED) or double (MSP_FP64); node (i, j) of patch m at row
+ *     j - Y0, column i - X0; x_dev 16-byte aligned;
+ *   pitch: multiple of 4, >= the widest buffered box; rows >= the tallest
+ *     (msp_operator_tile_shape gives both maxima);
+ *   ms_out: optional device time of the launch (CUDA events), synchronising.
+ * This is the streaming form of the operator (each tile read and written once);
+ * the local solves use a tile-resident form inside their kernels.  INVALID_ARG
+ * on a bad shape, TIMEOUT if a tile copy does not complete. */
+msp_status msp_operator_tile_shape(msp_medium m, int* rows, int* cols);
+msp_status msp_apply_operator(msp_medium m, int samples, int precision, const void* x_dev, void* y_dev, int pitch,
+                              int rows, double* ms_out, void* stream);
+
 /* --------------------------------------------------------------------- online */
 
 /* Online stage for `batch` Dirichlet data sets (Eq. elliptic_cond_reduced):

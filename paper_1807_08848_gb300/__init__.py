@@ -112,6 +112,26 @@ class Medium:
         N.check(N.load().msp_medium_patch(self._h, m, C.byref(info)))
         return info
 
+    def tile_shape(self):
+        """(rows, cols) of the largest buffered box."""
+        r, c = C.c_int(), C.c_int()
+        N.check(N.load().msp_operator_tile_shape(self._h, C.byref(r), C.byref(c)))
+        return r.value, c.value
+
+    def apply_operator(self, x: torch.Tensor, precision="mixed", y: torch.Tensor | None = None, stream=None,
+                       timed: bool = False):
+        """y = A x on every tile of x, shape (n_patches, S, rows, pitch); float32 for
+        'mixed', float64 for 'fp64'.  With timed, returns (y, device ms)."""
+        dt = torch.float32 if precision_code(precision) == MSP_MIXED else torch.float64
+        assert x.dtype == dt and x.is_cuda and x.is_contiguous() and x.dim() == 4
+        if y is None:
+            y = torch.empty_like(x)
+        ms = C.c_double(0.0)
+        N.check(N.load().msp_apply_operator(self._h, x.shape[1], precision_code(precision), _dptr(x), _dptr(y),
+                                            x.shape[3], x.shape[2], C.byref(ms) if timed else None,
+                                            _stream_ptr(stream)))
+        return (y, ms.value) if timed else y
+
     def coefficients(self, stream=None):
         n = self.n_cells
         aE = torch.empty((n + 1, n), dtype=torch.float64, device="cuda")

@@ -98,6 +98,8 @@ SIGNATURES = {
     "msp_kinetic_basis_info": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_d)]),
     "msp_kinetic_online_solve": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "msp_online_solve": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
+    "msp_operator_tile_shape": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
+    "msp_apply_operator": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, C.POINTER(_d), _vp]),
     "msp_basis_build_map": (_i, [_vp, _d, _i, _vp]),
     "msp_online_solve_map": (_i, [_vp, _vp, _i, _vp, _vp]),
     "msp_server_create": (_i, [C.POINTER(_vp), _i, C.c_int64, _i, _i, _i, C.POINTER(_vp)]),
