@@ -448,6 +448,25 @@ def run_ours(args, rank, world):
                    "l2": "inputs 5 GB > L2"}
         del xs, ys, omed
 
+    # ---- the kinetic slab workload (8192 cells, 64 GL velocities, 64 patches x 96
+    # samples): local solves per second, mixed (FP32 corrections) and plain FP64
+    kinetic = None
+    if args.kinetic:
+        kw = synth.workload_kinetic()
+        kinetic = {"workload": kw["name"]}
+        for kp in ("mixed", "fp64"):
+            km = msp.KineticMedium(kw["n_cells"], kw["eps"], kw["n_v"], kw["n_patches"], kw["buffer"], kw["samples"])
+            km.sample(kw["seed"], tol=1e-13, max_iter=200000, precision=kp, stats=False)
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            kst = km.sample(kw["seed"], tol=1e-13, max_iter=200000, precision=kp)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            kt = k0.elapsed_time(k1) / 1e3
+            kinetic[kp] = {"solves_per_s": int(kst.n_solves) / kt, "ms": kt * 1e3,
+                           "sweeps_per_solve": kst.total_iters / max(1, int(kst.n_solves))}
+            del km
+
     # ---- the plain FP64 path's local solves on the same medium, for comparison
     fp64_rate = None
     if args.compare_fp64 and prec == "mixed":
@@ -497,6 +516,7 @@ def run_ours(args, rank, world):
                         "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged},
         "fp64_path_local_solve": fp64_rate,
         "stencil_apply": stencil,
+        "kinetic_local_solve": kinetic,
         "stages": stages,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -524,6 +544,8 @@ def main():
     ap.add_argument("--online-reqs", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-kinetic", dest="kinetic", action="store_false",
+                    help="skip timing the kinetic slab local solves")
     ap.add_argument("--no-stencil", dest="stencil", action="store_false",
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",

@@ -376,10 +376,13 @@ msp_status msp_kinetic_velocities(msp_kmedium k, double* v_host, double* w_host)
  * N(0,1) incoming data on the buffered patch (Philox4x32-10, counter = (datum
  * pair, sample, patch, kinetic tag); data 0..n_v/2-1 are the positive velocities
  * at the left end, the rest the negative velocities at the right end, each
- * ascending in v), solved by source iteration (FP64 transport sweeps with the
- * lagged density) until max|rho_new - rho| <= tol max|rho|, restricted to K_m.
- * stats as for msp_sample_patches (synchronises when given). */
-msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, double tol, int max_iter, void* stream,
+ * ascending in v), restricted to K_m.  precision MSP_FP64: source iteration
+ * (FP64 transport sweeps with the lagged density) until max|rho_new - rho| <=
+ * tol max|rho|.  MSP_MIXED: FP64 residuals of the density with FP32 source-
+ * iteration corrections (each to a relative 1e-6, at most max_iter sweeps),
+ * stopped on the same criterion; iterations in the stats count FP32 and FP64
+ * sweeps.  stats as for msp_sample_patches (synchronises when given). */
+msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, int precision, double tol, int max_iter, void* stream,
                               msp_solve_stats* stats_host);
 /* Copy patch `patch`'s snapshot block ((W+1) n_v x samples, column-major). */
 msp_status msp_kinetic_get_snapshots(msp_kmedium k, int patch, double* dst_dev, void* stream);

@@ -341,10 +341,11 @@ class KineticMedium:
         N.check(N.load().msp_kinetic_velocities(self._h, _f64p(v), _f64p(w)))
         return v, w
 
-    def sample(self, seed: int, tol: float = 1e-12, max_iter: int = 100000, stream=None, stats: bool = True):
+    def sample(self, seed: int, tol: float = 1e-12, max_iter: int = 100000, stream=None, stats: bool = True,
+               precision="fp64"):
         st = N.SolveStats()
-        N.check(N.load().msp_kinetic_sample(self._h, C.c_uint64(seed), tol, max_iter, _stream_ptr(stream),
-                                            C.byref(st) if stats else None))
+        N.check(N.load().msp_kinetic_sample(self._h, C.c_uint64(seed), precision_code(precision), tol, max_iter,
+                                            _stream_ptr(stream), C.byref(st) if stats else None))
         return st if stats else None
 
     def snapshots(self, m: int, stream=None) -> torch.Tensor:

@@ -91,7 +91,7 @@ SIGNATURES = {
     "msp_kinetic_build": (_i, [_i, _d, _i, _i, _i, _i, _vp, C.POINTER(_vp)]),
     "msp_kinetic_destroy": (None, [_vp]),
     "msp_kinetic_velocities": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
-    "msp_kinetic_sample": (_i, [_vp, _u64, _d, _i, _vp, C.POINTER(SolveStats)]),
+    "msp_kinetic_sample": (_i, [_vp, _u64, _i, _d, _i, _vp, C.POINTER(SolveStats)]),
     "msp_kinetic_get_snapshots": (_i, [_vp, _i, _vp, _vp]),
     "msp_kinetic_extract": (_i, [_vp, _d, _vp, C.POINTER(_vp)]),
     "msp_kinetic_basis_destroy": (None, [_vp]),

@@ -243,6 +243,152 @@ __global__ void kinetic_si_kernel(KSolveArgs A) {
     }
 }
 
+// Mixed precision: source iteration on the density with FP64 residuals and FP32
+// corrections.  With K the density of a transport sweep driven by the source
+// b2 rho (zero inflow) and q the density of the sweep of the inflow alone, the
+// converged density solves (I - K) rho = q.  Each outer step does one FP64
+// sweep with the current rho (giving q + K rho and the residual
+// res = q + K rho - rho), then solves (I - K) delta = res by FP32 source
+// iteration to a relative 1e-6 and adds delta to rho in FP64.  Stops when
+// |res| <= tol |q + K rho|; the final angular flux comes from one more FP64
+// sweep with the converged density, as in the FP64 kernel.
+__global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
+    extern __shared__ double ksm[];
+    __shared__ double red[32];
+    __shared__ float redf[32];
+    const int m = blockIdx.x;
+    const KPatchDev P = A.patches[m];
+    const int nn = P.X1 - P.X0 + 1, nv = A.n_v, G = A.G;
+    double* f = ksm;                                   // G x nn x nv (FP64 sweeps)
+    float* f32 = reinterpret_cast<float*>(ksm);        // the same storage for the FP32 sweeps
+    double* rho = ksm + (long long)G * nn * nv;        // G x nn
+    double* res = rho + (long long)G * nn;             // G x nn
+    float* del = reinterpret_cast<float*>(res + (long long)G * nn);   // G x nn
+    const int g = threadIdx.x / nv, l = threadIdx.x % nv;
+    const int s = blockIdx.y * G + g;
+    const bool live = g < G && s < A.S;
+    const double dx = 1.0 / A.N, ie = 1.0 / A.eps;
+    double vl = 0.0, a2 = 0.0, b2 = 0.0, inflow = 0.0;
+    if (live) {
+        vl = A.v[l];
+        const double a = fabs(vl) / dx, inv = 1.0 / (a + ie);
+        a2 = a * inv;
+        b2 = ie * inv;
+        const int t = (vl > 0.0) ? l - nv / 2 : nv / 2 + l;
+        const double2 z = gaussian_pair(A.seed, (uint32_t)(t >> 1), (uint32_t)s, (uint32_t)m, kTagKinetic);
+        inflow = (t & 1) ? z.y : z.x;
+    }
+    const float a2f = (float)a2, b2f = (float)b2;
+    for (int t = threadIdx.x; t < G * nn; t += blockDim.x) rho[t] = 0.0;
+    __syncthreads();
+    double* fg = f + (long long)(live ? g : 0) * nn * nv;
+    float* fg32 = f32 + (long long)(live ? g : 0) * nn * nv;
+    const double* rg = rho + (live ? g : 0) * nn;
+    const float* dg = del + (live ? g : 0) * nn;
+    auto sweep64 = [&]() {
+        if (!live) return;
+        if (vl > 0.0) {
+            double fp = inflow;
+            fg[l] = fp;
+            for (int i = 1; i < nn; ++i) {
+                fp = a2 * fp + b2 * rg[i];
+                fg[(long long)i * nv + l] = fp;
+            }
+        } else {
+            double fp = inflow;
+            fg[(long long)(nn - 1) * nv + l] = fp;
+            for (int i = nn - 2; i >= 0; --i) {
+                fp = a2 * fp + b2 * rg[i];
+                fg[(long long)i * nv + l] = fp;
+            }
+        }
+    };
+    int inner_total = 0, outer = 0;
+    bool done = false;
+    for (; outer < 64 && !done; ++outer) {
+        sweep64();
+        __syncthreads();
+        // residual of the density and its size
+        double rmax = 0.0, smax = 0.0;
+        for (int t = threadIdx.x; t < G * nn; t += blockDim.x) {
+            const int gg = t / nn, i = t - gg * nn;
+            if (blockIdx.y * G + gg >= A.S) continue;
+            const double* fi = f + ((long long)gg * nn + i) * nv;
+            double r = 0.0;
+            for (int ll = 0; ll < nv; ++ll) r += A.w[ll] * fi[ll];
+            r *= 0.5;
+            res[t] = r - rho[t];
+            rmax = fmax(rmax, fabs(r - rho[t]));
+            smax = fmax(smax, fabs(r));
+        }
+        rmax = block_max1(rmax, red);
+        smax = block_max1(smax, red);
+        if (rmax <= A.tol * smax) {
+            for (int t = threadIdx.x; t < G * nn; t += blockDim.x) rho[t] += res[t];
+            done = true;
+            __syncthreads();
+            break;
+        }
+        // (I - K) delta = res by FP32 source iteration
+        for (int t = threadIdx.x; t < G * nn; t += blockDim.x) del[t] = (float)res[t];
+        __syncthreads();
+        bool inner_done = false;
+        for (int it = 0; it < A.max_iter && !inner_done; ++it) {
+            if (live) {
+                if (vl > 0.0) {
+                    float fp = 0.f;
+                    fg32[l] = fp;
+                    for (int i = 1; i < nn; ++i) {
+                        fp = a2f * fp + b2f * dg[i];
+                        fg32[(long long)i * nv + l] = fp;
+                    }
+                } else {
+                    float fp = 0.f;
+                    fg32[(long long)(nn - 1) * nv + l] = fp;
+                    for (int i = nn - 2; i >= 0; --i) {
+                        fp = a2f * fp + b2f * dg[i];
+                        fg32[(long long)i * nv + l] = fp;
+                    }
+                }
+            }
+            __syncthreads();
+            float dmax = 0.f, vmax = 0.f;
+            for (int t = threadIdx.x; t < G * nn; t += blockDim.x) {
+                const int gg = t / nn, i = t - gg * nn;
+                if (blockIdx.y * G + gg >= A.S) continue;
+                const float* fi = f32 + ((long long)gg * nn + i) * nv;
+                float r = 0.f;
+                for (int ll = 0; ll < nv; ++ll) r = fmaf((float)A.w[ll], fi[ll], r);
+                r = 0.5f * r + (float)res[t];
+                dmax = fmaxf(dmax, fabsf(r - del[t]));
+                vmax = fmaxf(vmax, fabsf(r));
+                del[t] = r;
+            }
+            dmax = block_max1(dmax, redf);
+            vmax = block_max1(vmax, redf);
+            inner_done = dmax <= 1e-6f * vmax;
+            ++inner_total;
+        }
+        for (int t = threadIdx.x; t < G * nn; t += blockDim.x) rho[t] += (double)del[t];
+        __syncthreads();
+    }
+    // the angular flux of the converged density
+    sweep64();
+    __syncthreads();
+    const int i0 = P.x0 - P.X0, nk_nodes = P.x1 - P.x0 + 1;
+    for (int gg = 0; gg < G; ++gg) {
+        const int ss = blockIdx.y * G + gg;
+        if (ss >= A.S) break;
+        double* out = A.snaps + P.snap_offset + (long long)ss * P.n_k;
+        const double* fs = f + (long long)gg * nn * nv;
+        for (int t = threadIdx.x; t < nk_nodes * nv; t += blockDim.x) out[t] = fs[(long long)i0 * nv + t];
+        if (threadIdx.x == 0) {
+            A.stats[2 * (m * A.S + ss) + 0] = inner_total + outer;
+            A.stats[2 * (m * A.S + ss) + 1] = done ? 0 : 1;
+        }
+    }
+}
+
 // ---- online: block-tridiagonal normal equations along the chain of patches
 // rows of Q_m at the first (left) and last (right) node of K_m
 __device__ __forceinline__ const double* qrow(const double* Q, const KPatchDev& P, int node, int l, int nv) {
@@ -568,16 +714,19 @@ extern "C" msp_status msp_kinetic_velocities(msp_kmedium k, double* v_host, doub
     return MSP_OK;
 }
 
-extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, double tol, int max_iter, void* stream,
-                                         msp_solve_stats* stats) {
+extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, int precision, double tol, int max_iter,
+                                         void* stream, msp_solve_stats* stats) {
     clear_error();
     MSP_CHECK_ARG(k, "msp_kinetic_sample: NULL medium");
+    MSP_CHECK_ARG(precision == MSP_FP64 || precision == MSP_MIXED, "msp_kinetic_sample: unknown precision");
+    const bool mixed = precision == MSP_MIXED;
     MSP_CHECK_ARG(tol > 0 && tol < 1 && max_iter >= 1, "msp_kinetic_sample: tol in (0,1), max_iter >= 1");
     KMedium& K = k->K;
     cudaStream_t s = (cudaStream_t)stream;
     int max_nn = 0;
     for (auto& P : K.patches) max_nn = std::max(max_nn, P.nn);
-    const size_t per = sizeof(double) * ((size_t)max_nn * K.n_v + max_nn);
+    const size_t per = sizeof(double) * ((size_t)max_nn * K.n_v + max_nn) +
+                       (mixed ? (sizeof(double) + sizeof(float)) * (size_t)max_nn : 0);
     int G = (int)std::min<size_t>(std::max(1, 256 / K.n_v), (200 * 1024) / per);
     if (G < 1) {
         set_error("msp_kinetic_sample: buffered patch too long for on-chip sweeps");
@@ -588,9 +737,14 @@ extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, double to
     A.N = K.N; A.n_v = K.n_v; A.S = K.S; A.G = G; A.eps = K.eps; A.tol = tol; A.max_iter = max_iter; A.seed = seed;
     A.v = K.d_v.p; A.w = K.d_w.p; A.patches = K.d_patches.p; A.snaps = K.snaps.p; A.stats = K.stats.p;
     const size_t smem = per * G;
-    MSP_CUDA(cudaFuncSetAttribute(kinetic_si_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(K.M, (K.S + G - 1) / G);
-    kinetic_si_kernel<<<grid, G * K.n_v, smem, s>>>(A);
+    if (mixed) {
+        MSP_CUDA(cudaFuncSetAttribute(kinetic_si_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kinetic_si_mixed_kernel<<<grid, G * K.n_v, smem, s>>>(A);
+    } else {
+        MSP_CUDA(cudaFuncSetAttribute(kinetic_si_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kinetic_si_kernel<<<grid, G * K.n_v, smem, s>>>(A);
+    }
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
     K.sampled = true;
@@ -606,7 +760,7 @@ extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, double to
             r.n_not_converged += h[2 * i + 1];
             r.unknown_iters += (long long)h[2 * i] * K.patches[i / K.S].nn * K.n_v;
         }
-        r.max_refinements = 1;
+        r.max_refinements = mixed ? 0 : 1;
         *stats = r;
         if (r.n_not_converged) {
             set_error("msp_kinetic_sample: source iteration stopped at max_iter for some samples");

@@ -96,3 +96,27 @@ def test_slab_workload_sampled_patches():
     np.testing.assert_array_equal(f[0, v > 0], 3 + np.sin(2 * np.pi * v[v > 0]))
     rho = 0.5 * (f * K.velocities(64)[1]).sum(1)
     assert 1.0 < rho[4096] < 4.0
+
+
+def test_mixed_precision_sweeps_match_the_oracle():
+    """FP32 source-iteration corrections inside FP64 residual iteration reach the
+    FP64 path's accuracy (relative L2 <= 1e-8 against the direct oracle)."""
+    c = SMALL
+    off = K.offline(c["n_cells"], c["eps"], c["n_v"], c["n_patches"], c["buffer"], c["samples"], 7, 1e-10)
+    km = msp.KineticMedium(**c)
+    st = km.sample(7, tol=1e-14, max_iter=200000, precision="mixed")
+    assert st.n_not_converged == 0
+    for m in range(c["n_patches"]):
+        assert rel(km.snapshots(m).cpu().numpy(), off.R[m]) <= 1e-8, m
+
+
+def test_mixed_precision_slab_workload():
+    """The 8192-cell workload: mixed and FP64 snapshots agree to 1e-8."""
+    c = dict(n_cells=8192, eps=2.0 ** -8, n_v=64, n_patches=64, buffer=32, samples=96)
+    km64 = msp.KineticMedium(**c)
+    km64.sample(4, tol=1e-13, max_iter=200000)
+    kmx = msp.KineticMedium(**c)
+    st = kmx.sample(4, tol=1e-13, max_iter=200000, precision="mixed")
+    assert st.n_not_converged == 0
+    for m in (0, 31, 63):
+        assert rel(kmx.snapshots(m).cpu().numpy(), km64.snapshots(m).cpu().numpy()) <= 1e-8, m
