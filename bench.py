@@ -105,6 +105,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- multi-rank host logic
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value over all ranks (the slowest replica's time); x at one rank.
+    NCCL reduces a device tensor, gloo a host tensor."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput of N independent replicas: all ranks' units over the
+    slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 # ---------------------------------------------------------------- CPU oracle arm
 
 def oracle_sample(budget_s: float = 15.0):
@@ -373,11 +394,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize(); barrier()
     clk = clocks.stop()
     launches = (lib.msp_kernel_launches() - launches0) / args.steps
-    t = e0.elapsed_time(e1) / 1e3 / args.steps
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps, world)
 
     # ---- end to end through host buffers (medium description and phi from the
     # host, the reconstructed field back to the host), wall clock with syncs
@@ -386,7 +403,7 @@ def run_ours(args, rank, world):
     for _ in range(max(1, args.steps // 2)):
         step(True)
     torch.cuda.synchronize(); barrier()
-    t_e2e = (time.perf_counter() - t0) / max(1, args.steps // 2)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / max(1, args.steps // 2), world)
     h2d = int(w["medium"].modes.nbytes + 4 * 4 * (33 + 33 + 1024 + 1024) + phi_host.numel() * 8)
     d2h = int(n * n * 8)
 
@@ -495,7 +512,7 @@ def run_ours(args, rank, world):
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     peak = fp32_peak if prec == "mixed" else fp32_peak / 64.0
-    value = n_solves * world / t
+    value = aggregate_rate(n_solves, world, t)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -505,7 +522,7 @@ def run_ours(args, rank, world):
                    "precision": prec, "local_tol": tol, "tau": w["tau"], "online_tol": w["online_tol"],
                    "l2": "working set > L2 (4.7 GB snapshots rebuilt every step)",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": n_solves * world / t_e2e, "unit": METRIC, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": aggregate_rate(n_solves, world, t_e2e), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches)),
         "online": {"p50_ms": lat[len(lat) // 2] if lat else None,

@@ -54,6 +54,25 @@ def test_null_arguments_are_rejected(lib):
     assert lib.msp_sample_patches(None, 0, 0, 1e-8, 10, None, None) == N.MSP_ERR_INVALID_ARG
     assert lib.msp_extract_basis(None, 1e-6, 0, None, C.byref(out)) == N.MSP_ERR_INVALID_ARG
     assert lib.msp_online_solve(None, None, 1, 1e-8, 10, None, None, None, None) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_basis_build_map(None, 1e-10, 10, None) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_online_solve_map(None, None, 1, None, None) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_apply_operator(None, 1, 1, None, None, 4, 4, None, None) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_kinetic_sample(None, 0, 0, 1e-8, 10, None, None) == N.MSP_ERR_INVALID_ARG
+
+
+def test_server_arguments_are_checked_without_a_device(lib):
+    from paper_1807_08848_gb300 import _native as N
+    out = C.c_void_p()
+    media = (C.c_void_p * 1)(None)
+    # no media, a NULL basis, a bad batch size: rejected before any device call
+    assert lib.msp_server_create(media, 0, 1 << 20, 4, 8, 1, C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_server_create(media, 1, 1 << 20, 4, 8, 1, C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_server_create(media, 1, 1 << 20, 4, 0, 1, C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    rid = C.c_uint64()
+    assert lib.msp_server_submit(None, 0, None, C.byref(rid)) == N.MSP_ERR_INVALID_ARG
+    done = C.c_int()
+    assert lib.msp_server_poll(None, 1, C.byref(done), None) == N.MSP_ERR_INVALID_ARG
+    lib.msp_server_destroy(None)   # a NULL server is ignored
 
 
 def test_bad_partition_rejected_before_any_device_work(lib):
