@@ -313,6 +313,13 @@ msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, doubl
  * INVALID_ARG if the map has not been built.  The paper has no counterpart of
  * the map; it is the serving form of the same least-squares solution. */
 msp_status msp_basis_build_map(msp_basis b, double tol, int max_iter, void* stream);
+/* Engine of the map GEMM c = G phi: MSP_MAP_TENSOR_CORES (default) uses the fifth-
+ * generation tensor cores (tcgen05, TF32 inputs with the three-term split G_hi phi_hi
+ * + G_hi phi_lo + G_lo phi_hi, FP32 accumulation per 128 terms, FP64 across them);
+ * MSP_MAP_CUDA_CORES the FP32 FMA kernel with the same accumulation scheme. */
+#define MSP_MAP_TENSOR_CORES 0
+#define MSP_MAP_CUDA_CORES   1
+msp_status msp_basis_set_map_engine(msp_basis b, int engine);
 msp_status msp_online_solve_map(msp_basis b, const double* phi_dev, int batch, double* u_dev, void* stream);
 
 /* -------------------------------------------------------------------- serving */

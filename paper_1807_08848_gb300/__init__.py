@@ -245,6 +245,10 @@ class Basis:
         """Boundary-to-coefficient map c = G phi (FP32 on the device) for serving."""
         N.check(N.load().msp_basis_build_map(self._h, tol, max_iter, _stream_ptr(stream)))
 
+    def set_map_engine(self, engine: str):
+        """'tensor_cores' (tcgen05, default) or 'cuda_cores' for the map GEMM."""
+        N.check(N.load().msp_basis_set_map_engine(self._h, {"tensor_cores": 0, "cuda_cores": 1}[engine]))
+
     def solve_map(self, phi: torch.Tensor, stream=None, u: torch.Tensor | None = None) -> torch.Tensor:
         """u for phi of shape (B, 4N) (or (4N,)) through the map."""
         squeeze = phi.dim() == 1

@@ -102,6 +102,7 @@ SIGNATURES = {
     "msp_apply_operator": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, C.POINTER(_d), _vp]),
     "msp_basis_build_map": (_i, [_vp, _d, _i, _vp]),
     "msp_online_solve_map": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "msp_basis_set_map_engine": (_i, [_vp, _i]),
     "msp_server_create": (_i, [C.POINTER(_vp), _i, C.c_int64, _i, _i, _i, C.POINTER(_vp)]),
     "msp_server_submit": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_u64)]),
     "msp_server_poll": (_i, [_vp, _u64, C.POINTER(_i), C.POINTER(_d)]),

@@ -75,6 +75,14 @@ extern "C" msp_status msp_basis_build_map(msp_basis b, double tol, int max_iter,
     return build_online_map(b->B, tol, max_iter, (cudaStream_t)stream);
 }
 
+extern "C" msp_status msp_basis_set_map_engine(msp_basis b, int engine) {
+    clear_error();
+    MSP_CHECK_ARG(b, "msp_basis_set_map_engine: NULL basis");
+    MSP_CHECK_ARG(engine == MSP_MAP_TENSOR_CORES || engine == MSP_MAP_CUDA_CORES, "msp_basis_set_map_engine: unknown engine");
+    b->B.map_engine = engine;
+    return MSP_OK;
+}
+
 extern "C" msp_status msp_online_solve_map(msp_basis b, const double* phi, int batch, double* u, void* stream) {
     clear_error();
     MSP_CHECK_ARG(b && phi && u, "msp_online_solve_map: NULL argument");

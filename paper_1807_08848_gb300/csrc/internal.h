@@ -160,7 +160,9 @@ struct Basis {
     DevBuf<unsigned int> d_bt_bar;      // grid barrier of the sweep kernel: arrivals, generation, error
     // boundary-to-coefficient map (serving): G (N_p x 4N, FP32) and FP32 bases
     DevBuf<float> G32, Q32, E32;
+    DevBuf<float> Gt_hi, Gt_lo;         // G tiled for the tensor-core GEMM (TF32 high part, FP32 remainder)
     bool map_built = false;
+    int map_engine = 0;                 // 0: tensor cores (tcgen05, split TF32), 1: CUDA cores (FP32 FMA)
     BtStore<float> bt32;
     BtStore<double> bt64;
     DevBuf<double> w_s;                 // normal-equation residual s = P^T r
@@ -193,8 +195,13 @@ struct MapWork {
     float* phi32 = nullptr;
     float* c32 = nullptr;
     double* e = nullptr;
+    float* b_hi = nullptr;      // phi tiled for the tensor-core GEMM
+    float* b_lo = nullptr;
+    int* err = nullptr;         // timed-out waits of the tensor-core GEMM
     int cap = 0;
 };
+// nonzero if a map GEMM on this workspace reported a timed-out wait (synchronises the stream)
+msp_status map_work_check(MapWork& w, cudaStream_t s);
 msp_status map_work_alloc(const Basis& Bs, int max_batch, MapWork& w);
 void map_work_free(MapWork& w);
 msp_status build_online_map(Basis& Bs, double tol, int max_iter, cudaStream_t s);

@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "device_util.cuh"
 #include "dense.cuh"
+#include "tc_gemm.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -630,6 +631,10 @@ msp_status build_online_map(Basis& Bs, double tol, int max_iter, cudaStream_t s)
     }
     long long nq = 0;
     for (size_t m = 0; m < Bs.patches.size(); ++m) nq = std::max<long long>(nq, Bs.q_off[m] + (long long)Bs.patches[m].n_k * Bs.k[m]);
+    // G tiled and split for the tensor-core GEMM (element (j, k) at j + k Np)
+    MSP_TRY(Bs.Gt_hi.alloc((size_t)tc_a_floats(Np, n4), s));
+    MSP_TRY(Bs.Gt_lo.alloc((size_t)tc_a_floats(Np, n4), s));
+    tc_tile_split(Bs.G32.p, 1, Np, Np, n4, true, Bs.Gt_hi.p, Bs.Gt_lo.p, s);
     MSP_TRY(Bs.E32.alloc(std::max<size_t>(Bs.E.n, 1), s));
     to_f32_kernel<<<std::max(1, (int)std::min<long long>(4096, ((long long)Bs.E.n + 255) / 256)), 256, 0, s>>>(
         Bs.E.p, Bs.E32.p, (long long)Bs.E.n);
@@ -654,6 +659,10 @@ msp_status map_work_alloc(const Basis& Bs, int max_batch, MapWork& w) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.phi32, sizeof(float) * n4 * B);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.c32, sizeof(float) * std::max(Bs.Np, 1) * B);
     if (e == cudaSuccess) e = cudaMalloc((void**)&w.e, sizeof(double) * std::max(Bs.n_slots, 1) * B);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.b_hi, sizeof(float) * tc_b_floats((int)B, n4));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.b_lo, sizeof(float) * tc_b_floats((int)B, n4));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&w.err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(w.err, 0, sizeof(int));
     w.cap = (int)B;
     if (e != cudaSuccess) {
         map_work_free(w);
@@ -667,7 +676,23 @@ void map_work_free(MapWork& w) {
     if (w.phi32) cudaFree(w.phi32);
     if (w.c32) cudaFree(w.c32);
     if (w.e) cudaFree(w.e);
+    if (w.b_hi) cudaFree(w.b_hi);
+    if (w.b_lo) cudaFree(w.b_lo);
+    if (w.err) cudaFree(w.err);
     w = MapWork{};
+}
+
+msp_status map_work_check(MapWork& w, cudaStream_t s) {
+    if (!w.err) return MSP_OK;
+    int h = 0;
+    MSP_CUDA(cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        MSP_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+        set_error("map solve: a wait of the tensor-core GEMM timed out");
+        return MSP_ERR_TIMEOUT;
+    }
+    return MSP_OK;
 }
 
 msp_status online_solve_map(const Basis& Bs, const double* phi, int batch, double* u, cudaStream_t s, MapWork* work) {
@@ -688,7 +713,21 @@ msp_status online_solve_map(const Basis& Bs, const double* phi, int batch, doubl
         const double* ph = phi + (long long)b0 * n4;
         to_f32_kernel<<<std::max(1, std::min(1024, (n4 * B + 255) / 256)), 256, 0, s>>>(ph, work->phi32, (long long)n4 * B);
         count_launches(1);
-        {
+        if (Bs.map_engine == 0 && Bs.Gt_hi.p) {
+            // tensor cores: phi split and tiled, then the tcgen05 GEMM
+            tc_tile_split(work->phi32, n4, 1, B, n4, false, work->b_hi, work->b_lo, s);
+            TcMapArgs ta{};
+            ta.a_hi = Bs.Gt_hi.p;
+            ta.a_lo = Bs.Gt_lo.p;
+            ta.b_hi = work->b_hi;
+            ta.b_lo = work->b_lo;
+            ta.M = Np;
+            ta.B = B;
+            ta.n_slabs = tc_slabs(n4);
+            ta.c = work->c32;
+            ta.err = work->err;
+            MSP_TRY(tc_map_gemm(ta, s));
+        } else {
             const int tiles = ((Np + 63) / 64) * ((B + 63) / 64);
             map_gemm_kernel<<<tiles, 256, 0, s>>>(Bs.G32.p, work->phi32, work->c32, Np, n4, B);
             count_launches(1);
@@ -710,6 +749,7 @@ msp_status online_solve_map(const Basis& Bs, const double* phi, int batch, doubl
         }
     }
     if (work == &own) {
+        if (st == MSP_OK) st = map_work_check(own, s);
         cudaStreamSynchronize(s);
         map_work_free(own);
     }

@@ -175,6 +175,7 @@ msp_status run_batch(Server& S, Worker& W, cudaStream_t stream, int medium, cons
             st = MSP_ERR_CUDA;
         }
     }
+    if (st == MSP_OK) st = map_work_check(W.work[medium], stream);
     const double t = now_ms();
     std::lock_guard<std::mutex> lk(S.mu);
     S.st.batches += 1;

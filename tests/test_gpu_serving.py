@@ -74,6 +74,25 @@ def test_map_matches_the_iterative_solve(media):
             assert rel(u_map[k], u_it[k]) <= MIXED_TOL, k
 
 
+def test_tensor_core_and_cuda_core_map_engines_agree(media):
+    """The tcgen05 split-TF32 GEMM and the FP32 FMA GEMM give the same map solve
+    to FP32 level, and both meet the mixed-path bound against the FP64 solve."""
+    for w, _, b in media:
+        N = b.n_cells
+        phis = torch.tensor(synth.phi_fourier(N, 16, 13, batch=37), device="cuda")   # two N tiles, ragged
+        b.set_map_engine("cuda_cores")
+        u_cc = b.solve_map(phis).cpu().numpy()
+        b.set_map_engine("tensor_cores")
+        u_tc = b.solve_map(phis).cpu().numpy()
+        b.set_preconditioner("block_rows_fp64")
+        u_it, _ = b.solve(phis, tol=1e-13, max_iter=5000)
+        b.set_preconditioner("block_rows")
+        u_it = u_it.cpu().numpy()
+        for k in (0, 17, 31, 32, 36):
+            assert rel(u_tc[k], u_cc[k]) <= 1e-6, k
+            assert rel(u_tc[k], u_it[k]) <= MIXED_TOL, k
+
+
 def test_map_matches_the_oracle(media):
     w, _, b = media[0]
     off = E.offline(w["medium"], w["patches"], w["seed"], w["tau"])
