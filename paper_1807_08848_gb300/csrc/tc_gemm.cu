@@ -3,9 +3,9 @@
 // the three-term split X = X_hi + X_lo (X_hi = X rounded to TF32, X_lo the FP32
 // remainder): G phi ~ G_hi phi_hi + G_hi phi_lo + G_lo phi_hi, all three products
 // accumulated by the tensor core in FP32 in tensor memory.  The K sum is cut into
-// chunks of kChunkSlabs x 32; each chunk's FP32 accumulator is read out of tensor
-// memory and added into FP64 registers, so the rounding of the long sum does not
-// grow with the ring length.
+// slabs of 32 terms; each slab's FP32 accumulator is read out of tensor memory and
+// added into a compensated FP32 sum (two-sum per term), so the rounding of the
+// long sum does not grow with the ring length.
 //
 // Operands are stored pre-tiled in the no-swizzle K-major layout the MMA reads:
 // 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart (leading
@@ -15,8 +15,9 @@
 //
 // One CTA of 128 threads per 128-row tile; N = 32 data sets per launch tile.
 // Thread 0 issues the bulk copies (four stages, mbarriers) and the MMAs; tcgen05
-// commits release the stages and signal the chunk accumulator; the four warps read
-// their 32 tensor-memory lanes each.  Every wait is bounded: on timeout the CTA
+// commits release the stages and signal the slab accumulator; the four warps read
+// their 32 tensor-memory lanes each, from one of two accumulators while the MMAs
+// of the next slab fill the other.  Every wait is bounded: on timeout the CTA
 // records the failure in *err, stops issuing work, frees its tensor memory and
 // leaves.
 #include "internal.h"
@@ -30,7 +31,6 @@ constexpr int kRows = 128;             // MMA M
 constexpr int kN = 32;                 // MMA N (data sets per tile)
 constexpr int kSlab = 32;              // K elements per staged slab
 constexpr int kStages = 4;
-constexpr int kChunkSlabs = 1;         // slabs per FP64 accumulation (32 terms)
 constexpr int kAFloats = kRows * kSlab;   // one operand half of a slab
 constexpr int kBFloats = kN * kSlab;
 constexpr unsigned kStageBytes = (unsigned)(2 * (kAFloats + kBFloats) * sizeof(float));
@@ -92,9 +92,35 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
                  : "memory");
 }
 
+// bounded wait that also gives up as soon as another thread of the CTA has failed
+__device__ __forceinline__ bool mbar_wait_or_fail(unsigned long long* bar, unsigned parity, volatile int* fail) {
+    for (long long spin = 0; spin < (1LL << 26); ++spin) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((spin & 255) == 255 && *fail) return false;
+    }
+    return false;
+}
+
+// s + e = a + b exactly (Knuth's two-sum, six FP32 operations, no branches)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Two accumulators in tensor memory (columns 0-31 and 32-63): the MMAs of slab s
+// go to accumulator s & 1 while the four warps read slab s - 1 out of the other,
+// add it into a compensated FP32 sum (value + running error, two-sum per term)
+// and release it (acc_free, 128 arrivals).  Thread 0 issues the copies and MMAs.
 __global__ void __launch_bounds__(128, 1) tc_map_gemm_kernel(TcMapArgs A) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], accb;
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], accb[2], accfree[2];
     __shared__ unsigned s_tmem;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -105,13 +131,16 @@ __global__ void __launch_bounds__(128, 1) tc_map_gemm_kernel(TcMapArgs A) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accb[b], 1);
+            mbar_init(&accfree[b], 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(32)
+                     "r"(64)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -119,6 +148,7 @@ __global__ void __launch_bounds__(128, 1) tc_map_gemm_kernel(TcMapArgs A) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
+    volatile int* fail = &s_fail;
     const int n_slabs = A.n_slabs;
     const float* ahi = A.a_hi + (long long)tile * n_slabs * kAFloats;
     const float* alo = A.a_lo + (long long)tile * n_slabs * kAFloats;
@@ -134,67 +164,55 @@ __global__ void __launch_bounds__(128, 1) tc_map_gemm_kernel(TcMapArgs A) {
         bulk_g2s(p + 2 * kAFloats, bhi + (long long)slab * kBFloats, kBFloats * 4, &full[st]);
         bulk_g2s(p + 2 * kAFloats + kBFloats, blo + (long long)slab * kBFloats, kBFloats * 4, &full[st]);
     };
-    double acc[kN];
-#pragma unroll
-    for (int t = 0; t < kN; ++t) acc[t] = 0.0;
-    if (tid == 0)
-        for (int sl = 0; sl < kStages - 1 && sl < n_slabs; ++sl) issue_copy(sl);
-    const int n_chunks = (n_slabs + kChunkSlabs - 1) / kChunkSlabs;
-    int committed = -1;   // thread 0: last chunk whose accumulator commit was issued
     // leading byte offset: K-adjacent core matrices; stride byte offset: next 8 rows
     const unsigned lbo = 128, sbo = (kSlab / 4) * 128;
-    for (int c = 0; c < n_chunks; ++c) {
-        if (tid == 0 && !s_fail) {
-            const int s_end = min(n_slabs, (c + 1) * kChunkSlabs);
-            for (int sl = c * kChunkSlabs; sl < s_end; ++sl) {
-                // refill the stage the previous slab used, once its MMAs are done
-                const int nxt = sl + kStages - 1;
-                if (nxt < n_slabs) {
-                    if (sl >= 1 && !mbar_wait(&empty[(sl - 1) % kStages], (unsigned)(((sl - 1) / kStages) & 1))) {
-                        s_fail = 1;
-                        break;
-                    }
-                    issue_copy(nxt);
-                }
-                const int st = sl % kStages;
-                if (!mbar_wait(&full[st], (unsigned)((sl / kStages) & 1))) {
-                    s_fail = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const float* p = stage_ptr(st);
+    int last_issued[2] = {-1, -1};   // thread 0: last slab committed to each accumulator
+    // thread 0: MMAs of one slab into accumulator (slab & 1); false on a timed-out wait
+    auto mma_slab = [&](int sl) -> bool {
+        const int nxt = sl + kStages - 1;   // refill the stage the previous slab used
+        if (nxt < n_slabs) {
+            if (sl >= 1 && !mbar_wait_or_fail(&empty[(sl - 1) % kStages], (unsigned)(((sl - 1) / kStages) & 1), fail))
+                return false;
+            issue_copy(nxt);
+        }
+        const int st = sl % kStages, ab = sl & 1;
+        if (!mbar_wait_or_fail(&full[st], (unsigned)((sl / kStages) & 1), fail)) return false;
+        if (sl >= 2 && !mbar_wait_or_fail(&accfree[ab], (unsigned)(((sl - 2) >> 1) & 1), fail)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float* p = stage_ptr(st);
+        const unsigned d = tmem + (unsigned)(ab * kN);
 #pragma unroll
-                for (int ks = 0; ks < kSlab / 8; ++ks) {   // one MMA covers K = 8 (two core matrices)
-                    const unsigned off = ks * 2 * 128;
-                    const unsigned long long dah = smem_desc(reinterpret_cast<const char*>(p) + off, lbo, sbo);
-                    const unsigned long long dal =
-                        smem_desc(reinterpret_cast<const char*>(p + kAFloats) + off, lbo, sbo);
-                    const unsigned long long dbh =
-                        smem_desc(reinterpret_cast<const char*>(p + 2 * kAFloats) + off, lbo, sbo);
-                    const unsigned long long dbl =
-                        smem_desc(reinterpret_cast<const char*>(p + 2 * kAFloats + kBFloats) + off, lbo, sbo);
-                    const unsigned first = (sl == c * kChunkSlabs && ks == 0) ? 0u : 1u;
-                    mma_tf32(tmem, dah, dbh, first);
-                    mma_tf32(tmem, dah, dbl, 1u);
-                    mma_tf32(tmem, dal, dbh, 1u);
-                }
-                mma_commit(&empty[st]);
-            }
-            mma_commit(&accb);   // the chunk's products are in tensor memory once this arrives
-            committed = c;
+        for (int ks = 0; ks < kSlab / 8; ++ks) {   // one MMA covers K = 8 (two core matrices)
+            const unsigned off = ks * 2 * 128;
+            const unsigned long long dah = smem_desc(reinterpret_cast<const char*>(p) + off, lbo, sbo);
+            const unsigned long long dal = smem_desc(reinterpret_cast<const char*>(p + kAFloats) + off, lbo, sbo);
+            const unsigned long long dbh = smem_desc(reinterpret_cast<const char*>(p + 2 * kAFloats) + off, lbo, sbo);
+            const unsigned long long dbl =
+                smem_desc(reinterpret_cast<const char*>(p + 2 * kAFloats + kBFloats) + off, lbo, sbo);
+            mma_tf32(d, dah, dbh, ks == 0 ? 0u : 1u);
+            mma_tf32(d, dah, dbl, 1u);
+            mma_tf32(d, dal, dbh, 1u);
         }
-        __syncwarp();
-        __syncthreads();
-        if (s_fail) break;
-        if (!mbar_wait(&accb, (unsigned)(c & 1))) {
-            s_fail = 1;
-            atomicExch(A.err, 1);
+        mma_commit(&empty[st]);
+        mma_commit(&accb[ab]);
+        last_issued[ab] = sl;
+        return true;
+    };
+    float sum[kN], cmp[kN];
+#pragma unroll
+    for (int t = 0; t < kN; ++t) sum[t] = cmp[t] = 0.f;
+    // all threads: read slab sl's accumulator, add it, release the accumulator
+    // (warp-uniform result: the tensor-memory load below is a warp-collective)
+    auto epilogue = [&](int sl) -> bool {
+        const int ab = sl & 1;
+        const bool got = mbar_wait_or_fail(&accb[ab], (unsigned)((sl >> 1) & 1), fail);
+        if (!__all_sync(0xffffffffu, got)) {
+            *fail = 1;
+            return false;
         }
-        __syncthreads();
-        if (s_fail) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         unsigned r[kN];
-        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(ab * kN);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
             "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -205,28 +223,54 @@ __global__ void __launch_bounds__(128, 1) tc_map_gemm_kernel(TcMapArgs A) {
             : "r"(taddr)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int t = 0; t < kN; ++t) acc[t] += (double)__uint_as_float(r[t]);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accfree[ab])) : "memory");
+#pragma unroll
+        for (int t = 0; t < kN; ++t) {
+            float s2, e2;
+            two_sum(sum[t], __uint_as_float(r[t]), s2, e2);
+            sum[t] = s2;
+            cmp[t] += e2;
+        }
+        return true;
+    };
+    if (tid == 0)
+        for (int sl = 0; sl < kStages - 1 && sl < n_slabs; ++sl) issue_copy(sl);
+    bool ok = true;   // warp-uniform
+    for (int sl = 0; sl < n_slabs; ++sl) {
+        bool f = false;
+        if (tid == 0) f = !mma_slab(sl);
+        if (f) *fail = 1;
+        if (__any_sync(0xffffffffu, f || *fail != 0)) {
+            ok = false;
+            break;
+        }
+        if (sl >= 1 && !epilogue(sl - 1)) {
+            ok = false;
+            break;
+        }
     }
-    if (s_fail && tid == 0) {
-        atomicExch(A.err, 1);
-        // bounded wait for the MMAs already issued before the tensor memory is freed
-        if (committed >= 0) mbar_wait(&accb, (unsigned)(committed & 1));
-    }
+    if (ok && n_slabs >= 1 && !epilogue(n_slabs - 1)) ok = false;
+    if (!ok) *fail = 1;
+    __syncthreads();
+    const bool failed = *fail != 0;
+    if (failed && tid == 0) atomicExch(A.err, 1);
     // output row j of the tile: c[j][b] for the data sets of this N tile
     const int j = tile * kRows + warp * 32 + lane;
-    if (!s_fail && j < A.M) {
+    if (!failed && j < A.M) {
         const int b0 = ntile * kN;
 #pragma unroll
         for (int t = 0; t < kN; ++t)
-            if (b0 + t < A.B) A.c[(long long)j * A.B + b0 + t] = (float)acc[t];
+            if (b0 + t < A.B) A.c[(long long)j * A.B + b0 + t] = sum[t] + cmp[t];
+    }
+    if (failed && tid == 0) {
+        // bounded waits for MMAs already issued before the tensor memory is freed
+        for (int b = 0; b < 2; ++b)
+            if (last_issued[b] >= 0) mbar_wait(&accb[b], (unsigned)((last_issued[b] >> 1) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
-    (void)lane;
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
 }
 
 // Scatter of a row-major matrix X (rows x K, leading dimension ld, element (r, k) at
