@@ -283,6 +283,43 @@ msp_status msp_operator_tile_shape(msp_medium m, int* rows, int* cols);
 msp_status msp_apply_operator(msp_medium m, int samples, int precision, const void* x_dev, void* y_dev, int pitch,
                               int rows, double* ms_out, void* stream);
 
+/* Launch of the local solves of msp_sample_patches, per precision.
+ *   MSP_LAUNCH_SPLIT (default): the tile-resident kernel for the buffered patches
+ *     whose tile fits on chip, then the global-scratch kernel for the rest;
+ *   MSP_LAUNCH_FUSED: one persistent launch for every (patch, column): the CTAs
+ *     take the large tiles first (global-scratch path), then the on-chip tiles.
+ *   rows: rows per thread segment of the tile kernel, 4, 8 or 12 (0: the smallest
+ *     that every eligible tile fits); INVALID_ARG if below that.
+ * Results do not depend on the launch: each column's arithmetic is the same. */
+#define MSP_LAUNCH_SPLIT 0
+#define MSP_LAUNCH_FUSED 1
+msp_status msp_medium_set_launch(msp_medium m, int precision, int mode, int rows);
+
+/* Autotuner of that launch: every candidate (split or fused, each rows instance
+ * the eligible tiles fit) runs an even-strided subset of at most max_probe_items
+ * of the medium's columns, once to warm up and once timed (CUDA events); the
+ * fastest is kept for msp_sample_patches of that precision and reported.  The
+ * probe writes the subset's snapshot columns with the values a full run writes.
+ * Synchronises. */
+#define MSP_TUNE_MAX_CANDIDATES 8
+typedef struct {
+    int mode, rows;
+    float ms;          /* device time of the probe; -1 if the configuration does not fit */
+} msp_tune_candidate;
+typedef struct {
+    int probe_items, n_candidates;
+    msp_tune_candidate candidates[MSP_TUNE_MAX_CANDIDATES];
+    int best_mode, best_rows;
+    float best_ms;
+} msp_tune_report;
+msp_status msp_medium_autotune(msp_medium m, int precision, uint64_t seed, double tol, int max_iter,
+                               int max_probe_items, void* stream, msp_tune_report* out);
+
+/* enable != 0: msp_sample_patches replays its launches from a CUDA graph, captured
+ * on the first call of each configuration (precision, seed, tolerances, launch);
+ * the stream must not be capturing when that first call is made. */
+msp_status msp_medium_set_graph(msp_medium m, int enable);
+
 /* --------------------------------------------------------------------- online */
 
 /* Online stage for `batch` Dirichlet data sets (Eq. elliptic_cond_reduced):

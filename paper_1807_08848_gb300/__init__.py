@@ -112,6 +112,27 @@ class Medium:
         N.check(N.load().msp_medium_patch(self._h, m, C.byref(info)))
         return info
 
+    def set_launch(self, precision="mixed", mode="split", rows: int = 0):
+        """Launch of the local solves: 'split' (tile kernel + global kernel) or 'fused'
+        (one persistent launch); rows per thread segment 4/8/12 (0: smallest that fits)."""
+        N.check(N.load().msp_medium_set_launch(self._h, precision_code(precision), {"split": 0, "fused": 1}[mode],
+                                               rows))
+
+    def set_graph(self, enable: bool = True):
+        """Replay the local-solve launches from a CUDA graph (captured on first use)."""
+        N.check(N.load().msp_medium_set_graph(self._h, 1 if enable else 0))
+
+    def autotune(self, seed: int, precision="mixed", tol: float = 1e-10, max_iter: int = 20000,
+                 max_probe_items: int = 2048, stream=None) -> dict:
+        """Time every launch configuration on a subset of the columns and keep the fastest."""
+        r = N.TuneReport()
+        N.check(N.load().msp_medium_autotune(self._h, precision_code(precision), C.c_uint64(seed), tol, max_iter,
+                                             max_probe_items, _stream_ptr(stream), C.byref(r)))
+        return {"probe_items": r.probe_items, "best_mode": ["split", "fused"][r.best_mode],
+                "best_rows": r.best_rows, "best_ms": r.best_ms,
+                "candidates": [{"mode": ["split", "fused"][c.mode], "rows": c.rows, "ms": c.ms}
+                               for c in r.candidates[:r.n_candidates]]}
+
     def tile_shape(self):
         """(rows, cols) of the largest buffered box."""
         r, c = C.c_int(), C.c_int()

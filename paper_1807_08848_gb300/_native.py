@@ -57,6 +57,15 @@ class ServerStats(C.Structure):
                 ("mem_peak", C.c_int64)]
 
 
+class TuneCandidate(C.Structure):
+    _fields_ = [("mode", C.c_int), ("rows", C.c_int), ("ms", C.c_float)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("probe_items", C.c_int), ("n_candidates", C.c_int), ("candidates", TuneCandidate * 8),
+                ("best_mode", C.c_int), ("best_rows", C.c_int), ("best_ms", C.c_float)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("n_solves", C.c_int64), ("total_iters", C.c_int64), ("max_iters", C.c_int),
                 ("max_refinements", C.c_int), ("n_not_converged", C.c_int), ("unknown_iters", C.c_int64)]
@@ -99,6 +108,9 @@ SIGNATURES = {
     "msp_kinetic_online_solve": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "msp_online_solve": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
     "msp_operator_tile_shape": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
+    "msp_medium_set_launch": (_i, [_vp, _i, _i, _i]),
+    "msp_medium_set_graph": (_i, [_vp, _i]),
+    "msp_medium_autotune": (_i, [_vp, _i, _u64, _d, _i, _i, _vp, C.POINTER(TuneReport)]),
     "msp_apply_operator": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, C.POINTER(_d), _vp]),
     "msp_basis_build_map": (_i, [_vp, _d, _i, _vp]),
     "msp_online_solve_map": (_i, [_vp, _vp, _i, _vp, _vp]),

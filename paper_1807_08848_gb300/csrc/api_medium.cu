@@ -179,7 +179,13 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
     return MSP_OK;
 }
 
-extern "C" void msp_medium_destroy(msp_medium m) { delete m; }
+extern "C" void msp_medium_destroy(msp_medium m) {
+    if (!m) return;
+    for (auto& g : m->M.graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (m->M.capture_stream) cudaStreamDestroy(m->M.capture_stream);
+    delete m;
+}
 
 extern "C" msp_status msp_medium_counts(msp_medium m, int* n_patches, int64_t* snapshot_elems, int* n_cells) {
     clear_error();
@@ -226,7 +232,7 @@ extern "C" msp_status msp_sample_patches(msp_medium m, uint64_t seed, int precis
     cfg.max_iter = max_iter;
     cfg.max_ref = 12;
     cfg.seed = seed;
-    MSP_TRY(launch_local_solves(m->M, cfg, s));
+    MSP_TRY(sample_launch(m->M, cfg, s));
     m->M.sampled = true;
     if (stats) {
         std::vector<int> st(3 * (size_t)m->M.n_items);

@@ -96,6 +96,17 @@ struct Medium {
     DevBuf<double> scratch_global;      // global-kernel workspace
     bool sampled = false;
     int device = 0;
+    // launch of the local solves: mode 0 split (tile kernel + global kernel), 1 fused
+    // (one persistent launch); rows instance of the tile kernel (0: the smallest that fits);
+    // set by msp_medium_set_launch or by the autotuner, per precision
+    int launch_mode[2] = {0, 0};
+    int launch_rows[2] = {0, 0};
+    bool tuned[2] = {false, false};
+    // CUDA graph of the local-solve launches, replayed while the configuration is unchanged
+    bool use_graph = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaStream_t capture_stream = nullptr;
+    double graph_key[2][6] = {};
 };
 
 // Ring node t of node box (X0,X1,Y0,Y1): counter-clockwise from (X0,Y0).
@@ -173,6 +184,10 @@ struct Basis {
 };
 
 // ------------------------------------------------------------------ launchers
+namespace gpath {
+struct SolveArgs;
+}
+
 struct LocalSolveCfg {
     int precision;       // MSP_FP64 / MSP_MIXED
     double tol;          // outer relative residual target
@@ -183,11 +198,23 @@ struct LocalSolveCfg {
 };
 
 msp_status launch_medium_coefficients(Medium& M, const msp_medium_desc& d, cudaStream_t s);
-msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);
+// Optional subset of the items for one launch of the local solves (the autotuner's
+// probe runs): the tile items, the rest, and the launch configuration to use.
+struct LaunchItems {
+    const int2* tile;
+    int n_tile;
+    const int2* rest;
+    int n_rest;
+    int mode, rows;
+};
+msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s, const LaunchItems* li = nullptr);
+// The local solves of msp_sample_patches: launched directly, or through the medium's
+// CUDA graph when graphs are on (captured on the first call of a configuration).
+msp_status sample_launch(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);
 int tile_launch_rows(const std::vector<PatchDev>& patches, int precision);
 bool tile_kernel_fits(const PatchDev& P, int precision, int R);
 msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const int2* items, int n_items, int* counter,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const gpath::SolveArgs* fused = nullptr, int R_launch = 0);
 msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst, cudaStream_t s);
 msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B);
 // boundary-to-coefficient map (serving)

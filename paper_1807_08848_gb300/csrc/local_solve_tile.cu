@@ -27,6 +27,7 @@
 // Items (patch, column) come from a global work counter, largest tiles first.
 #include "internal.h"
 #include "device_util.cuh"
+#include "global_path.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -58,6 +59,7 @@ struct TileArgs {
     long long slot_doubles;
     int* stats;
     int one_patch_index;      // random stream index of the patch (one-patch variant)
+    gpath::SolveArgs g;       // fused launch: the items that do not fit on chip (global-scratch path)
 };
 
 // Thread mapping of an nx x ny interior: strips of 32 columns, segments of rps rows.
@@ -100,7 +102,10 @@ __device__ __forceinline__ T block_sum1(T v, T* buf) {
 
 // ONE_PATCH: every item is column `item` of the single patch A.patches[0] whose
 // random stream index is A.one_patch_index (the variant without allocations).
-template <class T, int RPS, bool ONE_PATCH = false>
+// FUSED: one persistent launch for every item of the medium: the work counter
+// first hands out the A.g items (tiles beyond the on-chip limit, the largest and
+// slowest, solved in the CTA's slot of global scratch), then the tile items.
+template <class T, int RPS, bool ONE_PATCH = false, bool FUSED = false>
 __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) {
     constexpr bool kF32 = sizeof(T) == 4;
     constexpr int PI = kPitch;
@@ -111,10 +116,20 @@ __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* slot = A.scratch + (long long)blockIdx.x * A.slot_doubles;
     const int N = A.N;
+    __shared__ T redTg[FUSED ? 128 : 1];
+    __shared__ double red64g[FUSED ? 128 : 1];
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(A.counter, 1);
         __syncthreads();
-        const int item = s_item;
+        int item = s_item;
+        if constexpr (FUSED) {
+            if (item < A.g.n_items) {   // ends with a block barrier, so s_item may be rewritten next
+                gpath::global_item<T>(A.g, item, reinterpret_cast<char*>(A.g.scratch) + (long long)blockIdx.x * A.g.slot_bytes,
+                                      red64g, redTg);
+                continue;
+            }
+            item -= A.g.n_items;
+        }
         if (item >= A.n_items) break;
         int m, col;
         if constexpr (ONE_PATCH) {
@@ -439,10 +454,11 @@ int rows_instance(int rps) {
     return 0;
 }
 
-template <class T, int RPS>
+template <class T, int RPS, bool FUSED = false>
 msp_status launch_rps(const TileArgs& A, int grid, size_t smem, cudaStream_t s) {
-    MSP_CUDA(cudaFuncSetAttribute(local_solve_tile<T, RPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    local_solve_tile<T, RPS><<<grid, kTileThreads, smem, s>>>(A);
+    MSP_CUDA(cudaFuncSetAttribute(local_solve_tile<T, RPS, false, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    local_solve_tile<T, RPS, false, FUSED><<<grid, kTileThreads, smem, s>>>(A);
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
     return MSP_OK;
@@ -474,8 +490,8 @@ bool tile_kernel_fits(const PatchDev& P, int precision, int R) {
 }
 
 msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const int2* items, int n_items,
-                                    int* counter, cudaStream_t s) {
-    if (n_items == 0) return MSP_OK;
+                                    int* counter, cudaStream_t s, const gpath::SolveArgs* fused, int R_launch) {
+    if (n_items == 0 && !fused) return MSP_OK;
     TileArgs A{};
     A.N = M.N;
     A.aE = M.aE.p;
@@ -493,12 +509,15 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
     A.max_ref = cfg.max_ref;
     A.stats = M.item_stats.p;
     const bool mixed = cfg.precision == MSP_MIXED;
-    // one row-count instance for the launch (eligibility was decided with the same R)
-    const int R = tile_launch_rows(M.patches, cfg.precision);
+    // one row-count instance for the launch: eligibility was decided with the
+    // smallest instance every eligible tile needs; a larger one (R_launch) fits
+    // those tiles as long as their shared memory stays under the limit
+    const int R0 = std::max(4, tile_launch_rows(M.patches, cfg.precision));
+    const int R = std::max(R0, R_launch);
     int max_ny = 0;
     size_t smem = 0;
     for (const PatchDev& P : M.patches) {
-        if (!tile_kernel_fits(P, cfg.precision, R)) continue;
+        if (!tile_kernel_fits(P, cfg.precision, R0)) continue;
         const int ny = P.Y1 - P.Y0 - 1;
         Mapping mp;
         tile_mapping(P.X1 - P.X0 - 1, ny, mp);
@@ -506,12 +525,32 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
         max_ny = std::max(max_ny, ny);
     }
     smem = (smem + 15) / 16 * 16;
-    const int grid = std::max(1, std::min(n_items, num_sms()));
+    if (smem > 220 * 1024) {
+        set_error("local solves: this row instance does not fit the tiles in shared memory");
+        return MSP_ERR_INVALID_ARG;
+    }
+    const int grid = std::max(1, std::min(n_items + (fused ? fused->n_items : 0), num_sms()));
+    if (fused) {
+        A.g = *fused;
+        const size_t gneed = (size_t)(A.g.slot_bytes / (long long)sizeof(double)) * grid + 1;
+        if (M.scratch_global.n < gneed) MSP_TRY(M.scratch_global.alloc(gneed, s));
+        A.g.scratch = M.scratch_global.p;
+    }
     A.slot_doubles = (slot_rows(max_ny) * kPitch + 31) / 32 * 32;
     const size_t need = (size_t)A.slot_doubles * grid;
     if (M.scratch.n < need) MSP_TRY(M.scratch.alloc(need, s));
     A.scratch = M.scratch.p;
     MSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    if (fused) {
+        if (mixed) {
+            if (R == 4) return launch_rps<float, 4, true>(A, grid, smem, s);
+            if (R == 8) return launch_rps<float, 8, true>(A, grid, smem, s);
+            return launch_rps<float, 12, true>(A, grid, smem, s);
+        }
+        if (R == 4) return launch_rps<double, 4, true>(A, grid, smem, s);
+        if (R == 8) return launch_rps<double, 8, true>(A, grid, smem, s);
+        return launch_rps<double, 12, true>(A, grid, smem, s);
+    }
     if (mixed) {
         if (R == 4) return launch_rps<float, 4>(A, grid, smem, s);
         if (R == 8) return launch_rps<float, 8>(A, grid, smem, s);
