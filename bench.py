@@ -322,6 +322,83 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mapgemm(args):
+    """One serving medium (--medium 513/1025/2049) with its basis and map; two
+    batch-32 map solves with each GEMM engine, CUDA-event times: the small case for
+    profiler captures of the map GEMMs."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    md = synth.workload_serving()["media"][{513: 0, 1025: 1, 2049: 2}[args.medium]]
+    med = msp.Medium(md["medium"], md["patches"])
+    med.sample(1, "mixed", tol=1e-10, max_iter=20000, stats=False)
+    b = med.extract(1e-6, "mixed")
+    b.build_map(tol=1e-10, max_iter=5000)
+    n = b.n_cells
+    phi = torch.tensor(synth.phi_fourier(n, 16, 5, batch=32), device="cuda")
+    u = torch.empty((32, n + 1, n + 1), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for eng in ("cuda_cores", "tensor_cores"):
+        b.set_map_engine(eng)
+        ts = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.solve_map(phi, u=u)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[eng + "_ms"] = ts[-1]
+    print(json.dumps({"case": f"mapgemm-{args.medium}", "n_unknowns": b.n_unknowns, **res}), flush=True)
+
+
+def run_uneven(args):
+    """The uneven workload: 1025^2 nodes, eps = 2^-6, channel medium of contrast 1e3,
+    patches of 16-96 cells with 4-24-cell buffers and 64-256 samples; local solves per
+    second of the split launch, the fused persistent launch, and the autotuned choice
+    replayed from a CUDA graph (mixed precision, CUDA events)."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    w = synth.workload_uneven()
+    stream = torch.cuda.current_stream()
+    out = {"metric": "local sample-solves/s (uneven batch)", "unit": "local sample-solves/s",
+           "higher_is_better": True, "n_gpus": 1, "config": {"workload": w["name"]}}
+
+    def timed(med, reps=3):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            med.sample(w["seed"], "mixed", tol=1e-10, max_iter=40000, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.median(ts))
+
+    forms = {}
+    for name in ("split", "fused"):
+        med = msp.Medium(w["medium"], w["patches"])
+        med.set_launch("mixed", name)
+        st = med.sample(w["seed"], "mixed", tol=1e-10, max_iter=40000)
+        n = int(st.n_solves)
+        forms[name] = {"solves_per_s": n / timed(med), "launches": 1 if name == "fused" else 2}
+        del med
+    med = msp.Medium(w["medium"], w["patches"])
+    t0 = time.time()
+    rep = med.autotune(w["seed"], "mixed", tol=1e-10, max_iter=40000, max_probe_items=2048)
+    t_tune = time.time() - t0
+    med.set_graph(True)
+    med.sample(w["seed"], "mixed", tol=1e-10, max_iter=40000, stats=False)   # direct run + capture
+    forms["autotuned_graph"] = {"solves_per_s": n / timed(med), "choice": rep["best_mode"], "rows": rep["best_rows"],
+                                "tune_s": t_tune, "candidates": rep["candidates"]}
+    out["value"] = forms["autotuned_graph"]["solves_per_s"]
+    out["local_solves"] = n
+    out["forms"] = forms
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1807_08848_gb300 as msp
@@ -567,10 +644,12 @@ def main():
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving"],
+    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
     ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--medium", type=int, default=1025, choices=[513, 1025, 2049],
+                    help="serving medium of --case mapgemm")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-mem-gb", type=float, default=16.0)
@@ -580,6 +659,12 @@ def main():
         return
     if args.case == "serving":
         run_serving(args)
+        return
+    if args.case == "uneven":
+        run_uneven(args)
+        return
+    if args.case == "mapgemm":
+        run_mapgemm(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
