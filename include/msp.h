@@ -359,6 +359,26 @@ msp_status msp_basis_build_map(msp_basis b, double tol, int max_iter, void* stre
 msp_status msp_basis_set_map_engine(msp_basis b, int engine);
 msp_status msp_online_solve_map(msp_basis b, const double* phi_dev, int batch, double* u_dev, void* stream);
 
+/* Persistence: msp_save_basis writes the geometry, the bases Q_m, their singular
+ * values and the medium's face coefficients to a file (host I/O, synchronises);
+ * msp_load_basis reads such a file on the current device and rebuilds the online
+ * operators with the extraction's own code, so the loaded basis gives the same online
+ * results.  The map of msp_basis_build_map is not saved.  INVALID_ARG on an unreadable,
+ * foreign or truncated file (checked before any device work). */
+msp_status msp_save_basis(msp_basis b, const char* path);
+/* Geometry of a basis (also of a loaded one): the number of cells and patches, and
+ * patch `patch`'s boxes as msp_medium_patch gives them (out may be NULL). */
+msp_status msp_basis_patch(msp_basis b, int patch, int* n_cells, int* n_patches, msp_patch_info* out);
+msp_status msp_load_basis(const char* path, msp_basis* out);
+
+/* The online system of Eq. elliptic_cond_reduced for inspection of small cases:
+ * P~ (rows x N_p, see msp_online_counts) as COO triplets and d for the ring data
+ * phi_host ([4N], host).  *nnz receives the entry count; with rows = NULL only the
+ * count (and d if d_host is given) is returned; otherwise rows, cols, vals (host,
+ * capacity entries) receive the entries.  Synchronises. */
+msp_status msp_get_online_system(msp_basis b, const double* phi_host, int64_t capacity, int64_t* nnz, int* rows,
+                                 int* cols, double* vals, double* d_host);
+
 /* -------------------------------------------------------------------- serving */
 
 /* A request loop over several prebuilt media (bases with their maps built):

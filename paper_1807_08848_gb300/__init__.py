@@ -191,12 +191,18 @@ class Medium:
 class Basis:
     """Reduced bases Q_m and the online operators of one medium."""
 
-    def __init__(self, handle, medium: Medium):
+    def __init__(self, handle, medium: Medium | None = None):
         self._h = handle
-        self.n_cells = medium.n_cells
-        self.n_patches = medium.n_patches
-        self._cols = [medium.patch(m).cols for m in range(medium.n_patches)]
-        self._nk = [medium.patch(m).n_k for m in range(medium.n_patches)]
+        nc, npt = C.c_int(), C.c_int()
+        N.check(N.load().msp_basis_patch(handle, 0, C.byref(nc), C.byref(npt), None))
+        self.n_cells, self.n_patches = nc.value, npt.value
+        infos = []
+        for m in range(self.n_patches):
+            info = N.PatchInfo()
+            N.check(N.load().msp_basis_patch(handle, m, None, None, C.byref(info)))
+            infos.append(info)
+        self._cols = [i.cols for i in infos]
+        self._nk = [i.n_k for i in infos]
         nu, nr = C.c_int(), C.c_int()
         N.check(N.load().msp_online_counts(handle, C.byref(nu), C.byref(nr)))
         self.n_unknowns, self.n_rows = nu.value, nr.value
@@ -261,6 +267,33 @@ class Basis:
             c = c[0] if c is not None else None
         return (u, it, c) if want_c else (u, it)
 
+
+    def save(self, path: str):
+        """Write the bases, singular values, geometry and face coefficients to a file."""
+        N.check(N.load().msp_save_basis(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str) -> "Basis":
+        """Read a basis file on the current device (the online operators are rebuilt)."""
+        h = C.c_void_p()
+        N.check(N.load().msp_load_basis(str(path).encode(), C.byref(h)))
+        return cls(h)
+
+    def online_system(self, phi):
+        """(rows, cols, vals, d) of P~ (COO) and d for ring data phi (host arrays)."""
+        phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(-1))
+        nnz = C.c_int64()
+        d = np.empty(self.n_rows, dtype=np.float64)
+        pd = phi.ctypes.data_as(C.POINTER(C.c_double))
+        N.check(N.load().msp_get_online_system(self._h, pd, 0, C.byref(nnz), None, None, None,
+                                               d.ctypes.data_as(C.POINTER(C.c_double))))
+        r = np.empty(nnz.value, dtype=np.int32)
+        c = np.empty(nnz.value, dtype=np.int32)
+        v = np.empty(nnz.value, dtype=np.float64)
+        N.check(N.load().msp_get_online_system(self._h, pd, nnz.value, C.byref(nnz),
+                                               r.ctypes.data_as(C.POINTER(C.c_int)), c.ctypes.data_as(C.POINTER(C.c_int)),
+                                               v.ctypes.data_as(C.POINTER(C.c_double)), None))
+        return r, c, v, d
 
     def build_map(self, tol: float = 1e-10, max_iter: int = 5000, stream=None):
         """Boundary-to-coefficient map c = G phi (FP32 on the device) for serving."""

@@ -113,6 +113,11 @@ SIGNATURES = {
     "msp_medium_autotune": (_i, [_vp, _i, _u64, _d, _i, _i, _vp, C.POINTER(TuneReport)]),
     "msp_apply_operator": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, C.POINTER(_d), _vp]),
     "msp_basis_build_map": (_i, [_vp, _d, _i, _vp]),
+    "msp_save_basis": (_i, [_vp, C.c_char_p]),
+    "msp_basis_patch": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(PatchInfo)]),
+    "msp_load_basis": (_i, [C.c_char_p, C.POINTER(_vp)]),
+    "msp_get_online_system": (_i, [_vp, C.POINTER(_d), C.c_int64, C.POINTER(C.c_int64), C.POINTER(_i),
+                                   C.POINTER(_i), C.POINTER(_d), C.POINTER(_d)]),
     "msp_online_solve_map": (_i, [_vp, _vp, _i, _vp, _vp]),
     "msp_basis_set_map_engine": (_i, [_vp, _i]),
     "msp_server_create": (_i, [C.POINTER(_vp), _i, C.c_int64, _i, _i, _i, C.POINTER(_vp)]),

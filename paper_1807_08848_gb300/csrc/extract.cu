@@ -597,6 +597,22 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
         MSP_TRY(svd_bases(M.snaps.p, M.snap_elems, snap_off, n_rows, cols, tau, s, B.Q, B.k, B.sigma, B.sigma_off, B.q_off,
                           B.max_jacobi_sweeps, B.max_cholqr_tries, &B.mean_jacobi_sweeps));
     }
+    return finish_basis(B, M.aE.p, M.aN.p, s);
+}
+
+// Online operators of a basis whose geometry (N, patches, breaks), Q_m, k_m and
+// sigma are set: coefficient offsets, skeleton and row tables, edge operators (from
+// the FP64 face coefficients aE, aN on the device), patch-block preconditioner and
+// the block-row factor.  Shared by the extraction and by msp_load_basis.
+msp_status finish_basis(Basis& B, const double* aE_dev, const double* aN_dev, cudaStream_t s) {
+    const int np = (int)B.patches.size();
+    {
+        const size_t nf = (size_t)(B.N + 1) * B.N;
+        MSP_TRY(B.aE.alloc(nf, s));
+        MSP_TRY(B.aN.alloc(nf, s));
+        MSP_CUDA(cudaMemcpyAsync(B.aE.p, aE_dev, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+        MSP_CUDA(cudaMemcpyAsync(B.aN.p, aN_dev, sizeof(double) * nf, cudaMemcpyDeviceToDevice, s));
+    }
     B.c_off.resize(np + 1);
     int co = 0;
     for (int m = 0; m < np; ++m) {
@@ -607,7 +623,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     B.Np = co;
     // G as scratch for the precondtioner blocks below
     long long mo = 0;
-    for (int m = 0; m < np; ++m) mo += (long long)M.patches[m].cols * M.patches[m].cols;
+    for (int m = 0; m < np; ++m) mo += (long long)B.patches[m].cols * B.patches[m].cols;
     DevBuf<double> G, L, F, Fi, shift_scale;
     DevBuf<int> status;
     MSP_TRY(G.alloc(mo, s)); MSP_TRY(L.alloc(mo, s)); MSP_TRY(F.alloc(mo, s)); MSP_TRY(Fi.alloc(mo, s));
@@ -617,14 +633,14 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
 
 
     // ---- online tables (host): skeleton nodes, rows of P~, transpose lists
-    const int N = M.N;
+    const int N = B.N;
     B.n_e.resize(np);
     B.slot_off.resize(np + 1);
     B.e_off.resize(np);
     int slots = 0;
     long long eo = 0;
     for (int m = 0; m < np; ++m) {
-        const PatchDev& P = M.patches[m];
+        const PatchDev& P = B.patches[m];
         B.n_e[m] = 2 * (P.x1 - P.x0) + 2 * (P.y1 - P.y0);
         B.slot_off[m] = slots;
         slots += 2 * B.n_e[m];
@@ -635,7 +651,7 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     B.n_slots = slots;
     std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> skel;   // (j, i) -> (m, t)
     for (int m = 0; m < np; ++m) {
-        const PatchDev& P = M.patches[m];
+        const PatchDev& P = B.patches[m];
         for (int t = 0; t < B.n_e[m]; ++t) {
             int i, j;
             ring_node(P.x0, P.x1, P.y0, P.y1, t, i, j);
@@ -693,12 +709,12 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
     MSP_TRY(upload(B.d_ne, B.n_e, s)); MSP_TRY(upload(B.d_q_off, B.q_off, s)); MSP_TRY(upload(B.d_e_off, B.e_off, s));
     MSP_TRY(upload(B.d_patches, B.patches, s));
     std::vector<unsigned char> xbr(N + 1, 0), ybr(N + 1, 0);
-    for (size_t i = 1; i + 1 < M.xb.size(); ++i) xbr[M.xb[i]] = 1;
-    for (size_t i = 1; i + 1 < M.yb.size(); ++i) ybr[M.yb[i]] = 1;
+    for (size_t i = 1; i + 1 < B.xb.size(); ++i) xbr[B.xb[i]] = 1;
+    for (size_t i = 1; i + 1 < B.yb.size(); ++i) ybr[B.yb[i]] = 1;
     DevBuf<unsigned char> d_xbr, d_ybr;
     MSP_TRY(upload(d_xbr, xbr, s)); MSP_TRY(upload(d_ybr, ybr, s));
     MSP_TRY(B.E.alloc(std::max<long long>(eo, 1), s));
-    edge_ops_kernel<<<np, 256, 0, s>>>(N, M.aE.p, M.aN.p, B.d_patches.p, B.d_k.p, B.d_q_off.p, B.d_e_off.p, B.Q.p,
+    edge_ops_kernel<<<np, 256, 0, s>>>(N, aE_dev, aN_dev, B.d_patches.p, B.d_k.p, B.d_q_off.p, B.d_e_off.p, B.Q.p,
                                        B.E.p, d_xbr.p, d_ybr.p);
     count_launches(1);
     MSP_CUDA(cudaGetLastError());

@@ -171,6 +171,7 @@ struct Basis {
     DevBuf<unsigned int> d_bt_bar;      // grid barrier of the sweep kernel: arrivals, generation, error
     // boundary-to-coefficient map (serving): G (N_p x 4N, FP32) and FP32 bases
     DevBuf<float> G32, Q32, E32;
+    DevBuf<double> aE, aN;              // the medium's FP64 face coefficients (kept for msp_save_basis)
     DevBuf<float> Gt_hi, Gt_lo;         // G tiled for the tensor-core GEMM (TF32 high part, FP32 remainder)
     bool map_built = false;
     int map_engine = 0;                 // 0: tensor cores (tcgen05, split TF32), 1: CUDA cores (FP32 FMA)
@@ -217,6 +218,7 @@ msp_status launch_local_solves_tile(Medium& M, const LocalSolveCfg& cfg, const i
                                     cudaStream_t s, const gpath::SolveArgs* fused = nullptr, int R_launch = 0);
 msp_status launch_ring_samples(Medium& M, int patch, uint64_t seed, double* dst, cudaStream_t s);
 msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Basis& B);
+msp_status finish_basis(Basis& B, const double* aE_dev, const double* aN_dev, cudaStream_t s);
 // boundary-to-coefficient map (serving)
 struct MapWork {
     float* phi32 = nullptr;

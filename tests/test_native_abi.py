@@ -60,6 +60,17 @@ def test_null_arguments_are_rejected(lib):
     assert lib.msp_kinetic_sample(None, 0, 0, 1e-8, 10, None, None) == N.MSP_ERR_INVALID_ARG
 
 
+def test_basis_files_are_checked_before_any_device_work(lib, tmp_path):
+    from paper_1807_08848_gb300 import _native as N
+    out = C.c_void_p()
+    assert lib.msp_load_basis(str(tmp_path / "missing.mspb").encode(), C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    bad = tmp_path / "bad.mspb"
+    bad.write_bytes(b"MSPBASIS" + bytes(40))
+    assert lib.msp_load_basis(str(bad).encode(), C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    assert b"basis file" in lib.msp_last_error() or b"truncated" in lib.msp_last_error()
+    assert lib.msp_save_basis(None, b"x") == N.MSP_ERR_INVALID_ARG
+
+
 def test_server_arguments_are_checked_without_a_device(lib):
     from paper_1807_08848_gb300 import _native as N
     out = C.c_void_p()
