@@ -353,6 +353,29 @@ def run_mapgemm(args):
     print(json.dumps({"case": f"mapgemm-{args.medium}", "n_unknowns": b.n_unknowns, **res}), flush=True)
 
 
+def run_stencil(args):
+    """The streaming operator on every patch x 128 samples of one serving medium
+    (--medium), FP32 and FP64, CUDA-event times: the small case for profiler captures."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    md = synth.workload_serving()["media"][{513: 0, 1025: 1, 2049: 2}[args.medium]]
+    med = msp.Medium(md["medium"], md["patches"])
+    rows, cols = med.tile_shape()
+    pitch = (cols + 3) // 4 * 4
+    S = 128
+    out = {"case": f"stencil-{args.medium}", "tiles": med.n_patches * S}
+    nodes = sum((p.X1 - p.X0 + 1) * (p.Y1 - p.Y0 + 1) for p in (med.patch(m) for m in range(med.n_patches)))
+    for prec, dt, es in (("mixed", torch.float32, 4), ("fp64", torch.float64, 8)):
+        x = torch.randn((med.n_patches, S, rows, pitch), dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        med.apply_operator(x, prec, y=y)
+        ms = med.apply_operator(x, prec, y=y, timed=True)[1]
+        out[prec] = {"ms": ms, "achieved_gbs": (nodes * S * 2 * es + nodes * 2 * es) / ms / 1e6}
+        del x, y
+    print(json.dumps(out), flush=True)
+
+
 def run_uneven(args):
     """The uneven workload: 1025^2 nodes, eps = 2^-6, channel medium of contrast 1e3,
     patches of 16-96 cells with 4-24-cell buffers and 64-256 samples; local solves per
@@ -644,12 +667,12 @@ def main():
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm"],
+    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--medium", type=int, default=1025, choices=[513, 1025, 2049],
-                    help="serving medium of --case mapgemm")
+                    help="serving medium of --case mapgemm / --case stencil")
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-mem-gb", type=float, default=16.0)
@@ -665,6 +688,9 @@ def main():
         return
     if args.case == "mapgemm":
         run_mapgemm(args)
+        return
+    if args.case == "stencil":
+        run_stencil(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
