@@ -1,0 +1,97 @@
+"""Parity at the full sizes of the measured workloads, in the configuration
+bench.py times (mixed precision, local tolerance 1e-10, tau = 1e-6, online
+tolerance 1e-8), on outputs the oracle can compute one at a time:
+
+* 2049^2 log-normal workload: the snapshot blocks of sampled patches (corners, an
+  edge patch, interior patches) against the oracle's sparse direct solves
+  (relative L2 <= 1e-6, the mixed-path bound); their singular values against a
+  dense SVD of the oracle's block (|sigma_i - sigma_i^ref| <= 1e-6 sigma_1) and the
+  kept ranks; the online solution through properties that hold at any size: the
+  data on the domain boundary exactly, and least-squares optimality of the
+  coefficients, |P~^T (d - P~ c)| <= 1e-6 |P~^T d| (the iteration stops at 1e-8 on
+  its preconditioned residual; the plain gradient is held to a looser bound);
+* 1025^2 uneven channel workload: sampled patches, including the largest buffered
+  boxes (beyond the on-chip tile limit), in the autotuned launch.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+import synth
+from oracle import elliptic as E
+
+pytestmark = pytest.mark.gpu
+msp = pytest.importorskip("paper_1807_08848_gb300")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def batched():
+    w = synth.workload_batched()
+    med = msp.Medium(w["medium"], w["patches"])
+    st = med.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000)
+    basis = med.extract(w["tau"], "mixed")
+    aE, aN = E.face_coefficients(w["medium"])
+    return w, med, basis, st, aE, aN
+
+
+SAMPLED = (0, 31, 16, 528, 700, 1023)   # two corners, edge patches, interior patches, the last corner
+
+
+def test_2049_snapshots_of_sampled_patches(batched):
+    w, med, _, st, aE, aN = batched
+    assert st.n_not_converged == 0 and st.n_solves == 143356
+    patches = E.patch_boxes(2048, w["patches"])
+    for m in SAMPLED:
+        R = E.snapshots(aE, aN, patches[m], w["seed"], 2048)
+        assert rel(med.snapshots(m).cpu().numpy(), R) <= 1e-6, m
+
+
+def test_2049_singular_values_of_sampled_patches(batched):
+    w, _, basis, _, aE, aN = batched
+    patches = E.patch_boxes(2048, w["patches"])
+    for m in SAMPLED[:3]:
+        R = E.snapshots(aE, aN, patches[m], w["seed"], 2048)
+        _, s_ref = E.basis(R, w["tau"])
+        s = basis.sigma(m)
+        assert np.max(np.abs(s - s_ref)) <= 1e-6 * s_ref[0], m
+        near = np.abs(s_ref / s_ref[0] - w["tau"]) < 1e-2 * w["tau"]
+        if not near.any():
+            assert basis.k(m) == int(np.count_nonzero(s_ref > w["tau"] * s_ref[0])), m
+
+
+def test_2049_online_boundary_data_and_least_squares_optimality(batched):
+    w, _, basis, _, _, _ = batched
+    phi = w["phi"]
+    u, it, c = basis.solve(torch.tensor(phi, device="cuda"), tol=w["online_tol"], max_iter=1000, want_c=True)
+    u = u.cpu().numpy()
+    # the data on the domain boundary, node for node
+    x, y = synth.domain_ring_xy(2048)
+    I = np.rint(x * 2048).astype(int)
+    J = np.rint(y * 2048).astype(int)
+    assert np.array_equal(u[J, I], phi)
+    # least-squares optimality of the coefficients
+    r, cc, v, d = basis.online_system(phi)
+    P = sp.csr_matrix((v, (r, cc)), shape=(basis.n_rows, basis.n_unknowns))
+    cvec = c.cpu().numpy()
+    g = P.T @ (d - P @ cvec)
+    assert np.linalg.norm(g) <= 1e-6 * np.linalg.norm(P.T @ d)
+
+
+def test_1025_uneven_sampled_patches_in_the_autotuned_launch():
+    w = synth.workload_uneven()
+    med = msp.Medium(w["medium"], w["patches"])
+    med.autotune(w["seed"], "mixed", tol=1e-10, max_iter=40000, max_probe_items=1024)
+    st = med.sample(w["seed"], "mixed", tol=1e-10, max_iter=40000)
+    assert st.n_not_converged == 0
+    aE, aN = E.face_coefficients(w["medium"])
+    patches = E.patch_boxes(1024, w["patches"])
+    sizes = [(P.X1 - P.X0) * (P.Y1 - P.Y0) for P in patches]
+    order = np.argsort(sizes)
+    for m in (int(order[-1]), int(order[-2]), int(order[0]), len(patches) // 2):
+        R = E.snapshots(aE, aN, patches[m], w["seed"], 1024)
+        assert rel(med.snapshots(m).cpu().numpy(), R) <= 1e-6, m
