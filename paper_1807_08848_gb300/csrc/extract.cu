@@ -535,7 +535,12 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         MSP_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));
         // pairs of columns both below 1e-3 tau sigma_1 (|T|_F / sqrt(c) <= sigma_1) are not rotated
         const double small_rel = 1e-3 * tau / std::sqrt((double)std::max(maxc, 1));
-        jacobi_svd_kernel<<<np, 512, sm64, s>>>(d_mats.p, W.p, V.p, 40, maxc * 1.12e-16, small_rel, c64, sweeps.p);
+        // the largest blocks first (their sweeps cost the most), so the last wave is short
+        std::vector<SmallMat> by_size(mats);
+        std::stable_sort(by_size.begin(), by_size.end(), [](const SmallMat& a, const SmallMat& b) { return a.c > b.c; });
+        DevBuf<SmallMat> d_by_size;
+        MSP_TRY(upload(d_by_size, by_size, s));
+        jacobi_svd_kernel<<<np, 512, sm64, s>>>(d_by_size.p, W.p, V.p, 40, maxc * 1.12e-16, small_rel, c64, sweeps.p);
         count_launches(1);
         MSP_CUDA(cudaGetLastError());
     }

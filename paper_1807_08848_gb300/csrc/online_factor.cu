@@ -139,14 +139,19 @@ __global__ void potrf_tile_kernel(T* A, int lda, int nb, T* inv, int* fail) {
         const int i = e % nb, j = e / nb;
         A[i + (long long)j * lda] = (i >= j) ? L[i][j] : T(0);
     }
-    // inverse of the lower factor: thread j forward-substitutes column j
+    // inverse of the lower factor: thread j forward-substitutes column j in shared
+    // memory, keeping inv(L)[i][j] (i >= j) in the free upper part at L[j][i + 1]
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        for (int i = 0; i < kTile; ++i) inv[i + j * kTile] = T(0);
         for (int i = j; i < nb; ++i) {
             T s = (i == j) ? T(1) : T(0);
-            for (int q = j; q < i; ++q) s -= L[i][q] * inv[q + j * kTile];
-            inv[i + j * kTile] = s / L[i][i];
+            for (int q = j; q < i; ++q) s -= L[i][q] * L[j][q + 1];
+            L[j][i + 1] = s / L[i][i];
         }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+        const int i = e % kTile, j = e / kTile;
+        inv[i + j * kTile] = (i < nb && j < nb && i >= j) ? L[j][i + 1] : T(0);
     }
 }
 
