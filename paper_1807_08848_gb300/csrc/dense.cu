@@ -20,7 +20,8 @@ __device__ __forceinline__ void gemm_tile(const GemmDescT<T>& D) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads
     const int m0 = tm * TM, n0 = tn * TN;
     T acc[4][4] = {};
-    const int k_begin = D.b_lower ? (n0 / TK) * TK : 0;
+    int k_begin = D.b_lower ? (n0 / TK) * TK : 0;
+    if (D.a_k_lo && m0 < D.M) k_begin = max(k_begin, (D.a_k_lo[m0] / TK) * TK);
     const int k_end = D.a_lower ? min(D.K, m0 + TM) : D.K;
     for (int k0 = k_begin; k0 < k_end; k0 += TK) {
         // stage op(A)[m0 .. m0+63][k0 .. k0+15], reading along the contiguous index

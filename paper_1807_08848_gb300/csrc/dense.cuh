@@ -14,6 +14,8 @@ namespace msp {
 // K loop of an output tile starting at column j0 begins at j0.
 // a_lower != 0: op(A) is lower triangular (op(A)[i][k] = 0 for k > i), so the K
 // loop of an output tile ending at row i1 stops after i1.
+// a_k_lo (device, per row of op(A), nondecreasing): op(A)[i][k] = 0 for
+// k < a_k_lo[i], so the K loop of an output tile starting at row i0 begins there.
 template <class T>
 struct GemmDescT {
     const T* A;
@@ -25,6 +27,7 @@ struct GemmDescT {
     int lower = 0;
     int b_lower = 0;
     int a_lower = 0;
+    const int* a_k_lo = nullptr;
 };
 using GemmDesc = GemmDescT<double>;
 

@@ -167,6 +167,7 @@ struct Basis {
     int bt_apply_mode = 0;              // FP64 factor applied: 0 by batch size, 1 in FP64, 2 through bt32
     std::vector<int> bt_elo, bt_ehi;    // per patch: range of coupled patches in the row above
     DevBuf<int> d_bt_off;               // device copies of the block offsets (sweep kernel)
+    DevBuf<int> d_bt_rowlo;             // per unknown: first nonzero column of its row of C_{q-1}
     DevBuf<long long> d_bt_d_off, d_bt_e_off;
     DevBuf<unsigned int> d_bt_bar;      // grid barrier of the sweep kernel: arrivals, generation, error
     // boundary-to-coefficient map (serving): G (N_p x 4N, FP32) and FP32 bases

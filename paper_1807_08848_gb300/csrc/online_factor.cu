@@ -433,12 +433,12 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         int group_id = 0;
         auto add_gemm = [&](const T* A, int lda, const T* Bm, int ldb, T* C, int ldc, int M, int N, int K,
                             T alpha, T beta, bool tA, bool tB, int lower = 0, int b_lower = 0, int group = 0,
-                            int a_lower = 0) {
+                            int a_lower = 0, const int* a_k_lo = nullptr) {
             if (M <= 0 || N <= 0 || K <= 0) return;
             Step st{};
             st.kind = 0;
             st.group = group;
-            st.g = GemmDescT<T>{A, Bm, C, M, N, K, lda, ldb, ldc, alpha, beta, lower, b_lower, a_lower};
+            st.g = GemmDescT<T>{A, Bm, C, M, N, K, lda, ldb, ldc, alpha, beta, lower, b_lower, a_lower, a_k_lo};
             st.tA = tA;
             st.tB = tB;
             steps.push_back(st);
@@ -451,7 +451,8 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
             if (q > 0) {   // D_q -= C_{q-1} C_{q-1}^T
                 const int n0 = B.bt_off[q] - B.bt_off[q - 1];
                 const T* Cp = S.F.p + B.bt_e_off[q - 1];
-                add_gemm(Cp, n, Cp, n, Dq, n, n, n, n0, T(-1), T(1), false, true, 1);
+                add_gemm(Cp, n, Cp, n, Dq, n, n, n, n0, T(-1), T(1), false, true, 1, 0, 0, 0,
+                         B.d_bt_rowlo.p + B.bt_off[q]);
             }
             const int nt = (n + kTile - 1) / kTile;
             for (int kt = 0; kt < nt; ++kt) {
@@ -744,6 +745,22 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
         MSP_CUDA(cudaStreamSynchronize(s));   // descriptor buffers go out of scope
     }
     H64.free_now();
+    // first nonzero column of each row of C_{q-1} = E_{q-1} L_{q-1}^{-T} (in block q-1
+    // coordinates), as a suffix minimum so that it is nondecreasing along the rows
+    {
+        std::vector<int> rowlo(std::max(B.Np, 1), 0);
+        for (int q = 1; q < Qn; ++q) {
+            const int n0 = B.bt_off[q] - B.bt_off[q - 1];
+            for (int p = 0; p < mx; ++p) {
+                const int ma = q * mx + p;
+                if (ma >= np) continue;
+                const int lo = B.bt_elo[ma] < 0 ? n0 : B.c_off[B.bt_elo[ma]] - B.bt_off[q - 1];
+                for (int r = B.c_off[ma]; r < B.c_off[ma + 1]; ++r) rowlo[r] = lo;
+            }
+            for (int r = B.bt_off[q + 1] - 2; r >= B.bt_off[q]; --r) rowlo[r] = std::min(rowlo[r], rowlo[r + 1]);
+        }
+        MSP_TRY(upload(B.d_bt_rowlo, rowlo, s));
+    }
     // factorise in FP32; if a pivot fails, in FP64
     int fail = 0;
     MSP_TRY(factorize<float>(B, Hs64.p, total, 0.0, &fail, B.bt32, true, s));
