@@ -22,7 +22,8 @@ __device__ __forceinline__ void gemm_tile(const GemmDescT<T>& D) {
     T acc[4][4] = {};
     int k_begin = D.b_lower ? (n0 / TK) * TK : 0;
     if (D.a_k_lo && m0 < D.M) k_begin = max(k_begin, (D.a_k_lo[m0] / TK) * TK);
-    const int k_end = D.a_lower ? min(D.K, m0 + TM) : D.K;
+    int k_end = D.a_lower ? min(D.K, m0 + TM) : D.K;
+    if (D.b_upper) k_end = min(k_end, n0 + TN);
     for (int k0 = k_begin; k0 < k_end; k0 += TK) {
         // stage op(A)[m0 .. m0+63][k0 .. k0+15], reading along the contiguous index
         for (int e = threadIdx.x; e < TM * TK; e += 256) {

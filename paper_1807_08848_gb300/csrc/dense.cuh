@@ -28,6 +28,7 @@ struct GemmDescT {
     int b_lower = 0;
     int a_lower = 0;
     const int* a_k_lo = nullptr;
+    int b_upper = 0;   // op(B) upper triangular (op(B)[k][j] = 0 for k > j): K stops after the tile's last column
 };
 using GemmDesc = GemmDescT<double>;
 

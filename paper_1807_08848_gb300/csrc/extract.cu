@@ -482,6 +482,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
             const long long so_ = snap_off[m];
             gd[m] = GemmDesc{X + so_, X + so_, G.p + mats[m].off, mats[m].c, mats[m].c, mats[m].n,
                              mats[m].n, mats[m].n, mats[m].c, 1.0, 0.0};
+            gd[m].lower = 1;   // the Cholesky reads the lower triangle only
         }
         MSP_TRY(run_gemm(true, maxc, maxc));
         chol_factor_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p, L.p, F.p, Fi.p, shift_scale.p, pass == 0, status.p);
@@ -501,6 +502,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
             const long long so_ = snap_off[m];
             gd[m] = GemmDesc{X + so_, Fi.p + mats[m].off, Y + so_, mats[m].n, mats[m].c, mats[m].c,
                              mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
+            gd[m].b_upper = 1;   // Fi = L^{-T} is upper triangular
         }
         MSP_TRY(run_gemm(false, maxn, maxc));
         // T accumulation: Tacc <- F Tacc
