@@ -117,7 +117,7 @@ __global__ void jacobi_init_kernel(const SmallMat* mats, const double* T, double
     }
 }
 
-constexpr int kJacGroup = 4;       // threads per column pair
+constexpr int kJacGroup = 8;       // threads per column pair
 constexpr int kJacMaxPairs = 512;  // c <= 1024
 
 // One-sided (Hestenes) Jacobi in FP64 on the columns of W = T^T (c x c): rotate
