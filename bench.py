@@ -376,6 +376,27 @@ def run_stencil(args):
     print(json.dumps(out), flush=True)
 
 
+def run_kinetic(args):
+    """The kinetic slab workload alone (8192 cells, 64 GL velocities, 64 patches x 96
+    samples): one sample pass per precision, CUDA-event times, for profiler captures."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    kw = synth.workload_kinetic()
+    stream = torch.cuda.current_stream()
+    out = {"case": kw["name"]}
+    for kp in ("mixed", "fp64"):
+        km = msp.KineticMedium(kw["n_cells"], kw["eps"], kw["n_v"], kw["n_patches"], kw["buffer"], kw["samples"])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = km.sample(kw["seed"], tol=1e-13, max_iter=200000, precision=kp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[kp] = {"ms": e0.elapsed_time(e1), "solves": int(st.n_solves),
+                   "sweeps_per_solve": st.total_iters / max(1, int(st.n_solves))}
+    print(json.dumps(out), flush=True)
+
+
 def run_uneven(args):
     """The uneven workload: 1025^2 nodes, eps = 2^-6, channel medium of contrast 1e3,
     patches of 16-96 cells with 4-24-cell buffers and 64-256 samples; local solves per
@@ -667,7 +688,7 @@ def main():
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil"],
+    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
     ap.add_argument("--requests", type=int, default=10000)
@@ -691,6 +712,9 @@ def main():
         return
     if args.case == "stencil":
         run_stencil(args)
+        return
+    if args.case == "kinetic":
+        run_kinetic(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
