@@ -256,6 +256,8 @@ __global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
     extern __shared__ double ksm[];
     __shared__ double red[32];
     __shared__ float redf[32];
+    __shared__ double w64[256];   // quadrature weights, loaded once (n_v <= 256)
+    __shared__ float w32[256];
     const int m = blockIdx.x;
     const KPatchDev P = A.patches[m];
     const int nn = P.X1 - P.X0 + 1, nv = A.n_v, G = A.G;
@@ -264,6 +266,7 @@ __global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
     double* rho = ksm + (long long)G * nn * nv;        // G x nn
     double* res = rho + (long long)G * nn;             // G x nn
     float* del = reinterpret_cast<float*>(res + (long long)G * nn);   // G x nn
+    float* res32 = del + (long long)G * nn;                           // G x nn: res rounded once per step
     const int g = threadIdx.x / nv, l = threadIdx.x % nv;
     const int s = blockIdx.y * G + g;
     const bool live = g < G && s < A.S;
@@ -279,6 +282,10 @@ __global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
         inflow = (t & 1) ? z.y : z.x;
     }
     const float a2f = (float)a2, b2f = (float)b2;
+    for (int t = threadIdx.x; t < nv; t += blockDim.x) {
+        w64[t] = A.w[t];
+        w32[t] = (float)A.w[t];
+    }
     for (int t = threadIdx.x; t < G * nn; t += blockDim.x) rho[t] = 0.0;
     __syncthreads();
     double* fg = f + (long long)(live ? g : 0) * nn * nv;
@@ -315,7 +322,7 @@ __global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
             if (blockIdx.y * G + gg >= A.S) continue;
             const double* fi = f + ((long long)gg * nn + i) * nv;
             double r = 0.0;
-            for (int ll = 0; ll < nv; ++ll) r += A.w[ll] * fi[ll];
+            for (int ll = 0; ll < nv; ++ll) r += w64[ll] * fi[ll];
             r *= 0.5;
             res[t] = r - rho[t];
             rmax = fmax(rmax, fabs(r - rho[t]));
@@ -330,7 +337,7 @@ __global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
             break;
         }
         // (I - K) delta = res by FP32 source iteration
-        for (int t = threadIdx.x; t < G * nn; t += blockDim.x) del[t] = (float)res[t];
+        for (int t = threadIdx.x; t < G * nn; t += blockDim.x) del[t] = res32[t] = (float)res[t];
         __syncthreads();
         bool inner_done = false;
         for (int it = 0; it < A.max_iter && !inner_done; ++it) {
@@ -358,8 +365,8 @@ __global__ void kinetic_si_mixed_kernel(KSolveArgs A) {
                 if (blockIdx.y * G + gg >= A.S) continue;
                 const float* fi = f32 + ((long long)gg * nn + i) * nv;
                 float r = 0.f;
-                for (int ll = 0; ll < nv; ++ll) r = fmaf((float)A.w[ll], fi[ll], r);
-                r = 0.5f * r + (float)res[t];
+                for (int ll = 0; ll < nv; ++ll) r = fmaf(w32[ll], fi[ll], r);
+                r = 0.5f * r + res32[t];
                 dmax = fmaxf(dmax, fabsf(r - del[t]));
                 vmax = fmaxf(vmax, fabsf(r));
                 del[t] = r;
@@ -720,13 +727,14 @@ extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, int preci
     MSP_CHECK_ARG(k, "msp_kinetic_sample: NULL medium");
     MSP_CHECK_ARG(precision == MSP_FP64 || precision == MSP_MIXED, "msp_kinetic_sample: unknown precision");
     const bool mixed = precision == MSP_MIXED;
+    MSP_CHECK_ARG(!mixed || k->K.n_v <= 256, "msp_kinetic_sample: the mixed path takes at most 256 velocities");
     MSP_CHECK_ARG(tol > 0 && tol < 1 && max_iter >= 1, "msp_kinetic_sample: tol in (0,1), max_iter >= 1");
     KMedium& K = k->K;
     cudaStream_t s = (cudaStream_t)stream;
     int max_nn = 0;
     for (auto& P : K.patches) max_nn = std::max(max_nn, P.nn);
     const size_t per = sizeof(double) * ((size_t)max_nn * K.n_v + max_nn) +
-                       (mixed ? (sizeof(double) + sizeof(float)) * (size_t)max_nn : 0);
+                       (mixed ? (sizeof(double) + 2 * sizeof(float)) * (size_t)max_nn : 0);
     int G = (int)std::min<size_t>(std::max(1, 256 / K.n_v), (200 * 1024) / per);
     if (G < 1) {
         set_error("msp_kinetic_sample: buffered patch too long for on-chip sweeps");
