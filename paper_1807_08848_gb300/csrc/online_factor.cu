@@ -124,8 +124,8 @@ __global__ void potrf_tile_kernel(T* A, int lda, int nb, T* inv, int* fail) {
             else L[k][k] = sqrt(d);
         }
         __syncthreads();
-        const T piv = L[k][k];
-        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) L[i][k] /= piv;
+        const T rpiv = T(1) / L[k][k];   // one division per column, then products
+        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) L[i][k] *= rpiv;
         __syncthreads();
         const int R = nb - k - 1;
         for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
@@ -141,11 +141,14 @@ __global__ void potrf_tile_kernel(T* A, int lda, int nb, T* inv, int* fail) {
     }
     // inverse of the lower factor: thread j forward-substitutes column j in shared
     // memory, keeping inv(L)[i][j] (i >= j) in the free upper part at L[j][i + 1]
+    __shared__ T rdiag[kTile];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) rdiag[i] = T(1) / L[i][i];
+    __syncthreads();
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         for (int i = j; i < nb; ++i) {
             T s = (i == j) ? T(1) : T(0);
             for (int q = j; q < i; ++q) s -= L[i][q] * L[j][q + 1];
-            L[j][i + 1] = s / L[i][i];
+            L[j][i + 1] = s * rdiag[i];
         }
     }
     __syncthreads();
