@@ -33,13 +33,15 @@ struct GemmDescT {
 using GemmDesc = GemmDescT<double>;
 
 // Launch a batched GEMM over descriptors in device memory.  max_m, max_n bound
-// the batch's M and N (grid size).  C may alias A only when every CTA covers all
-// of N (N <= 64): each output tile then reads its rows of A before writing them.
+// the batch's M and N (grid size).  C may alias A only with N <= 64 and c_is_a
+// set: every CTA then covers all of N, so each output tile reads its rows of A
+// before writing them.
 template <class T>
 void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n, bool transA, bool transB,
-                  cudaStream_t s);
+                  cudaStream_t s, bool c_is_a = false);
 
-// One GEMM, descriptor passed by value (no device-side descriptor array).
+// One GEMM, descriptor passed by value (no device-side descriptor array); C == A
+// is detected from the descriptor (N <= 64, as above).
 template <class T>
 void gemm_one(const GemmDescT<T>& d, bool transA, bool transB, cudaStream_t s);
 

@@ -107,52 +107,82 @@ __global__ void patch_post_kernel(const double* F, const long long* f_off, const
 
 // Cholesky of one <= 64 x 64 diagonal tile in shared memory and the inverse of its
 // factor; writes L (lower, strict upper zeroed) in place and inv(L) to `inv` (ld 64).
+// One CTA of 256 threads, which sits on the factorisation's critical path, so
+// the work is spread over all threads and the FP64 square root and reciprocal
+// of each pivot are taken once, by the thread that finishes that pivot:
+//   factor, column k: scale column k by the pivot reciprocal; then thread (i, g)
+//     (row i = tid mod 64, g = tid / 64) updates L[i][j] for j = k+1+g, k+5+g, ...
+//     up to i, and the thread owning L[k+1][k+1] takes the next pivot;
+//   inverse: four lanes of a warp per column j of inv(L) run down its rows,
+//     each summing every fourth term of the forward substitution, combined by
+//     shuffles; column j is kept in the free strict upper part (inv(L)[i][j] at
+//     L[j][i + 1]).
 template <class T>
-__global__ void potrf_tile_kernel(T* A, int lda, int nb, T* inv, int* fail) {
+__device__ __forceinline__ void take_pivot(T (*L)[kTile + 1], int p, T* s_rp, int* s_ok) {
+    const T d = L[p][p];
+    if (!(d > T(0)) || !isfinite(d)) {
+        *s_ok = 0;
+        L[p][p] = T(1);
+        *s_rp = T(1);
+    } else {
+        const T r = sqrt(d);
+        L[p][p] = r;
+        *s_rp = T(1) / r;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) potrf_tile_kernel(T* A, int lda, int nb, T* inv, int* fail) {
+    static_assert(kTile == 64, "thread layout assumes 64-wide tiles and 256 threads");
     __shared__ T L[kTile][kTile + 1];
+    __shared__ T rdiag[kTile];
+    __shared__ T s_rp;
     __shared__ int s_ok;
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
         L[i][j] = (i >= j) ? A[i + (long long)j * lda] : T(0);
     }
-    if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
+    if (tid == 0) {
+        s_ok = 1;
+        if (nb > 0) take_pivot<T>(L, 0, &s_rp, &s_ok);
+    }
+    __syncthreads();
+    const int ri = tid & (kTile - 1), g = tid >> 6;
     for (int k = 0; k < nb; ++k) {
-        if (threadIdx.x == 0) {
-            const T d = L[k][k];
-            if (!(d > T(0)) || !isfinite(d)) { s_ok = 0; L[k][k] = T(1); }
-            else L[k][k] = sqrt(d);
-        }
+        const T rp = s_rp;
+        if (tid > k && tid < nb) L[tid][k] *= rp;
         __syncthreads();
-        const T rpiv = T(1) / L[k][k];   // one division per column, then products
-        for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x) L[i][k] *= rpiv;
-        __syncthreads();
-        const int R = nb - k - 1;
-        for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-            const int i = k + 1 + e % R, j = k + 1 + e / R;
-            if (i >= j) L[i][j] -= L[i][k] * L[j][k];
+        if (ri > k && ri < nb) {
+            const T lik = L[ri][k];
+            for (int j = k + 1 + g; j <= ri; j += 4) L[ri][j] = fma(-lik, L[j][k], L[ri][j]);
+            if (g == 0 && ri == k + 1) take_pivot<T>(L, k + 1, &s_rp, &s_ok);
         }
         __syncthreads();
     }
-    if (!s_ok && threadIdx.x == 0) atomicExch(fail, 1);
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    if (!s_ok && tid == 0) atomicExch(fail, 1);
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
         A[i + (long long)j * lda] = (i >= j) ? L[i][j] : T(0);
     }
-    // inverse of the lower factor: thread j forward-substitutes column j in shared
-    // memory, keeping inv(L)[i][j] (i >= j) in the free upper part at L[j][i + 1]
-    __shared__ T rdiag[kTile];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) rdiag[i] = T(1) / L[i][i];
+    for (int i = tid; i < nb; i += blockDim.x) rdiag[i] = T(1) / L[i][i];
     __syncthreads();
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        for (int i = j; i < nb; ++i) {
-            T s = (i == j) ? T(1) : T(0);
-            for (int q = j; q < i; ++q) s -= L[i][q] * L[j][q + 1];
-            L[j][i + 1] = s * rdiag[i];
+    {
+        const int j = tid >> 2, part = tid & 3;
+        const bool col = j < nb;
+        for (int i = (tid >> 5) * 8; i < nb; ++i) {   // warp-uniform rows: lanes with i < j add nothing
+            T acc = T(0);
+            if (col && i > j)
+                for (int q = j + part; q < i; q += 4) acc = fma(L[i][q], L[j][q + 1], acc);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (col && i >= j && part == 0) L[j][i + 1] = ((i == j ? T(1) : T(0)) - acc) * rdiag[i];
+            __syncwarp();
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    for (int e = tid; e < kTile * kTile; e += blockDim.x) {
         const int i = e % kTile, j = e / kTile;
         inv[i + j * kTile] = (i < nb && j < nb && i >= j) ? L[j][i + 1] : T(0);
     }
@@ -572,7 +602,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                     nn = std::max(nn, steps[sj].g.N);
                     ++sj;
                 }
-                gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s);
+                gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s, sj - si == 1 && st.g.C == st.g.A);
                 gi += sj - si;
                 si = sj - 1;
             } else if (st.kind == 1) {
