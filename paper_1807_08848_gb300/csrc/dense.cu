@@ -99,14 +99,16 @@ struct TileShape {
 
 // Output tile: 64 x 64 unless an FP64 launch would then give fewer than three
 // CTAs per SM, then the largest of 32 x 32 and 16 x 16 that does (16 x 16 if
-// neither does).  A product written in place over A (c_is_a, N <= 64) needs
-// every CTA to cover all of N, so it takes 16 x 64 instead.
+// neither does); structured FP64 launches take at most 32 x 32.  A product
+// written in place over A (N <= 64) needs every CTA to cover all of N, so it
+// takes 16 x 64 where a smaller tile is wanted.
 template <class T>
-TileShape pick_tile(int max_m, int max_n, long long batch, bool c_is_a) {
+TileShape pick_tile(int max_m, int max_n, long long batch, unsigned flags) {
     if (sizeof(T) != sizeof(double)) return {64, 64};
     const long long want = 3LL * num_sms();
-    if (tiles_of(max_m, max_n, 64, 64) * batch >= want) return {64, 64};
-    if (c_is_a) return {16, 64};
+    const bool big = tiles_of(max_m, max_n, 64, 64) * batch >= want;
+    if (flags & kGemmInPlace) return big ? TileShape{64, 64} : TileShape{16, 64};
+    if (big) return (flags & kGemmStructured) ? TileShape{32, 32} : TileShape{64, 64};
     if (tiles_of(max_m, max_n, 32, 32) * batch >= want) return {32, 32};
     return {16, 16};
 }
@@ -135,9 +137,9 @@ void launch_one(const GemmDescT<T>& d, TileShape t, dim3 grid, cudaStream_t s) {
 
 template <class T>
 void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n, bool transA, bool transB,
-                  cudaStream_t s, bool c_is_a) {
+                  cudaStream_t s, unsigned flags) {
     if (batch <= 0 || max_m <= 0 || max_n <= 0) return;
-    const TileShape tile = pick_tile<T>(max_m, max_n, batch, c_is_a);
+    const TileShape tile = pick_tile<T>(max_m, max_n, batch, flags);
     const int tiles = (int)tiles_of(max_m, max_n, tile.tm, tile.tn);
     for (int b0 = 0; b0 < batch; b0 += 65535) {
         const int nb = batch - b0 < 65535 ? batch - b0 : 65535;
@@ -153,7 +155,9 @@ void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n
 template <class T>
 void gemm_one(const GemmDescT<T>& d, bool transA, bool transB, cudaStream_t s) {
     if (d.M <= 0 || d.N <= 0) return;
-    const TileShape tile = pick_tile<T>(d.M, d.N, 1, d.C == d.A);
+    const bool structured = d.lower || d.b_lower || d.a_lower || d.b_upper || d.a_k_lo;
+    const TileShape tile =
+        pick_tile<T>(d.M, d.N, 1, (d.C == d.A ? kGemmInPlace : 0u) | (structured ? kGemmStructured : 0u));
     const dim3 grid((unsigned)tiles_of(d.M, d.N, tile.tm, tile.tn));
     if (transA && transB) launch_one<T, true, true>(d, tile, grid, s);
     else if (transA) launch_one<T, true, false>(d, tile, grid, s);
@@ -164,7 +168,7 @@ void gemm_one(const GemmDescT<T>& d, bool transA, bool transB, cudaStream_t s) {
 
 template void gemm_one<float>(const GemmDescT<float>&, bool, bool, cudaStream_t);
 template void gemm_one<double>(const GemmDescT<double>&, bool, bool, cudaStream_t);
-template void gemm_batched<double>(const GemmDescT<double>*, int, int, int, bool, bool, cudaStream_t, bool);
-template void gemm_batched<float>(const GemmDescT<float>*, int, int, int, bool, bool, cudaStream_t, bool);
+template void gemm_batched<double>(const GemmDescT<double>*, int, int, int, bool, bool, cudaStream_t, unsigned);
+template void gemm_batched<float>(const GemmDescT<float>*, int, int, int, bool, bool, cudaStream_t, unsigned);
 
 }  // namespace msp

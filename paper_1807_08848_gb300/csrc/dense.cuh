@@ -32,22 +32,29 @@ struct GemmDescT {
 };
 using GemmDesc = GemmDescT<double>;
 
+// Launch flags of gemm_batched.
+//   kGemmInPlace: C aliases A (allowed only with N <= 64): every CTA then covers
+//     all of N, so each output tile reads its rows of A before writing them.
+//   kGemmStructured: the descriptors use lower / b_lower / a_lower / b_upper /
+//     a_k_lo; FP64 launches then take tiles of at most 32 x 32, whose finer
+//     skipping of zero blocks saves more work than the smaller tile costs.
+enum : unsigned { kGemmInPlace = 1u, kGemmStructured = 2u };
+
 // Launch a batched GEMM over descriptors in device memory.  max_m, max_n bound
-// the batch's M and N (grid size).  C may alias A only with N <= 64 and c_is_a
-// set: every CTA then covers all of N, so each output tile reads its rows of A
-// before writing them.
+// the batch's M and N (grid size).
 template <class T>
 void gemm_batched(const GemmDescT<T>* descs_dev, int batch, int max_m, int max_n, bool transA, bool transB,
-                  cudaStream_t s, bool c_is_a = false);
+                  cudaStream_t s, unsigned flags = 0);
 
-// One GEMM, descriptor passed by value (no device-side descriptor array); C == A
-// is detected from the descriptor (N <= 64, as above).
+// One GEMM, descriptor passed by value (no device-side descriptor array); both
+// flags are read off the descriptor.
 template <class T>
 void gemm_one(const GemmDescT<T>& d, bool transA, bool transB, cudaStream_t s);
 
 // Backwards-compatible FP64 entry (op(B) = B).
-inline void gemm_batched(const GemmDesc* descs_dev, int batch, int max_m, int max_n, bool transA, cudaStream_t s) {
-    gemm_batched<double>(descs_dev, batch, max_m, max_n, transA, false, s);
+inline void gemm_batched(const GemmDesc* descs_dev, int batch, int max_m, int max_n, bool transA, cudaStream_t s,
+                         unsigned flags = 0) {
+    gemm_batched<double>(descs_dev, batch, max_m, max_n, transA, false, s, flags);
 }
 
 }  // namespace msp

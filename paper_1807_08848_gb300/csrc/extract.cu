@@ -126,13 +126,14 @@ constexpr int kJacMaxPairs = 512;  // c <= 1024
 // singular values are the column norms of W and V holds the left singular
 // vectors of T.  (On T^T the sweeps converge in about a third of the sweeps
 // needed on the columns of T.)  Pairs follow the round-robin tournament order,
-// c/2 disjoint pairs per round.  Each round has two phases: groups of
-// kJacGroup threads take one pair each (three inner products, the rotation
-// angle, the rotation of the two W columns), then the whole block applies the
-// round's rotations to V with coalesced row-wise accesses.  The FP64 pipe is
-// the bound, so the angle arithmetic is done once per pair, not once per lane
-// of a warp.  W lives in shared memory (leading dimension c + 1) when
-// c <= smem_c, else in global memory.
+// c/2 disjoint pairs per round.  Each round has three phases: groups of
+// kJacGroup threads take one pair each and form its three inner products; one
+// thread per pair decides whether to rotate and takes the angle (the FP64 pipe
+// is the bound, so the square roots and divisions are done once per pair, not
+// once per lane of a group); then the whole block applies the round's
+// rotations to the columns of W and V with row-wise accesses.  W lives in
+// shared memory (leading dimension c + 1) when c <= smem_c, else in global
+// memory.
 // Skips: columns below u |T|_F are numerically zero; a pair orthogonal to the
 // rounding floor of its inner product is left alone; and a pair whose columns
 // are both below small_rel |T|_F (far under the truncation level) is left alone,
@@ -140,7 +141,7 @@ constexpr int kJacMaxPairs = 512;  // c <= 1024
 __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, double* W, double* V, int max_sweeps,
                                                          double tol, double small_rel, int smem_c, int* sweeps_out) {
     extern __shared__ __align__(16) unsigned char jac_smem[];
-    __shared__ double s_cs[kJacMaxPairs], s_sn[kJacMaxPairs];
+    __shared__ double s_cs[kJacMaxPairs], s_sn[kJacMaxPairs], s_ga[kJacMaxPairs];
     __shared__ int s_p[kJacMaxPairs], s_q[kJacMaxPairs];
     __shared__ double s_red[32];
     __shared__ double s_fro;
@@ -194,8 +195,9 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
         if (threadIdx.x == 0) s_rot = 0;
         __syncthreads();
         for (int r = 0; r < np - 1; ++r) {
-            // phase 1: one group per pair; every thread runs the same number of
-            // iterations so that the group shuffles see full warps
+            // phase 1: one group per pair, its three inner products; every thread
+            // runs the same number of iterations so that the group shuffles see
+            // full warps
             for (int base = 0; base < npairs; base += groups) {
                 const int pr = base + threadIdx.x / kJacGroup;
                 const bool live = pr < npairs;
@@ -208,8 +210,8 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
                     q = max(a, b);
                 }
                 const bool real = live && q < c;
-                double* wp = w + (long long)p * ldw;
-                double* wq = w + (long long)q * ldw;
+                const double* wp = w + (long long)p * ldw;
+                const double* wq = w + (long long)q * ldw;
                 double al = 0.0, be = 0.0, ga = 0.0;
                 if (real) {
                     for (int i = g; i < c; i += kJacGroup) {
@@ -225,45 +227,51 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
                     be += __shfl_xor_sync(0xffffffffu, be, o);
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                double cs = 1.0, sn = 0.0;
-                bool rot = false;
-                if (real) {
-                    const double na = sqrt(al), nb = sqrt(be);
-                    rot = !(al <= negligible || be <= negligible || (al < small2 && be < small2) ||
-                            fabs(ga) <= tol * na * nb + floor_abs * (na + nb));
-                }
-                if (rot) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    cs = 1.0 / sqrt(1.0 + t * t);
-                    sn = cs * t;
-                    for (int i = g; i < c; i += kJacGroup) {
-                        const double x = wp[i], y = wq[i];
-                        wp[i] = cs * x - sn * y;
-                        wq[i] = sn * x + cs * y;
-                    }
-                }
                 if (live && g == 0) {
-                    s_p[pr] = rot ? p : -1;
+                    s_p[pr] = real ? p : -1;
                     s_q[pr] = q;
-                    s_cs[pr] = cs;
-                    s_sn[pr] = sn;
-                    if (rot) s_rot = 1;
+                    s_cs[pr] = al;   // the angle phase overwrites these with cos, sin
+                    s_sn[pr] = be;
+                    s_ga[pr] = ga;
                 }
             }
             __syncthreads();
-            // phase 2: the round's rotations applied to V, rows fastest
-            for (long long e = threadIdx.x; e < (long long)npairs * c; e += blockDim.x) {
-                const int pr = (int)(e / c), i = (int)(e % c);
+            // phase 2: one thread per pair, the decision and the rotation angle
+            for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
+                if (s_p[pr] < 0) continue;
+                const double al = s_cs[pr], be = s_sn[pr], ga = s_ga[pr];
+                const double na = sqrt(al), nb = sqrt(be);
+                if (al <= negligible || be <= negligible || (al < small2 && be < small2) ||
+                    fabs(ga) <= tol * na * nb + floor_abs * (na + nb)) {
+                    s_p[pr] = -1;
+                    continue;
+                }
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double cs = 1.0 / sqrt(1.0 + t * t);
+                s_cs[pr] = cs;
+                s_sn[pr] = cs * t;
+                s_rot = 1;
+            }
+            __syncthreads();
+            // phase 3: the round's rotations applied to the columns of W and V, rows
+            // fastest
+            for (int e = threadIdx.x; e < npairs * c; e += blockDim.x) {
+                const int pr = e / c, i = e - pr * c;
                 const int p = s_p[pr];
                 if (p < 0) continue;
                 const int q = s_q[pr];
                 const double cs = s_cs[pr], sn = s_sn[pr];
+                double* wp = w + (long long)p * ldw;
+                double* wq = w + (long long)q * ldw;
+                const double x = wp[i], y = wq[i];
+                wp[i] = cs * x - sn * y;
+                wq[i] = sn * x + cs * y;
                 double* vp = v + (long long)p * c;
                 double* vq = v + (long long)q * c;
-                const double x = vp[i], y = vq[i];
-                vp[i] = cs * x - sn * y;
-                vq[i] = sn * x + cs * y;
+                const double xv = vp[i], yv = vq[i];
+                vp[i] = cs * xv - sn * yv;
+                vq[i] = sn * xv + cs * yv;
             }
             __syncthreads();
         }
@@ -463,9 +471,9 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
     std::vector<GemmDesc> gd(np);
     DevBuf<GemmDesc> d_gd;
     MSP_TRY(d_gd.alloc(np, s));
-    auto run_gemm = [&](bool transA, int max_m, int max_n) -> msp_status {
+    auto run_gemm = [&](bool transA, int max_m, int max_n, unsigned flags = 0) -> msp_status {
         MSP_CUDA(cudaMemcpyAsync(d_gd.p, gd.data(), sizeof(GemmDesc) * np, cudaMemcpyHostToDevice, s));
-        gemm_batched(d_gd.p, np, max_m, max_n, transA, s);
+        gemm_batched(d_gd.p, np, max_m, max_n, transA, s, flags);
         MSP_CUDA(cudaGetLastError());
         MSP_CUDA(cudaStreamSynchronize(s));   // descriptors are reused
         return MSP_OK;
@@ -484,7 +492,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
                              mats[m].n, mats[m].n, mats[m].c, 1.0, 0.0};
             gd[m].lower = 1;   // the Cholesky reads the lower triangle only
         }
-        MSP_TRY(run_gemm(true, maxc, maxc));
+        MSP_TRY(run_gemm(true, maxc, maxc, kGemmStructured));
         chol_factor_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p, L.p, F.p, Fi.p, shift_scale.p, pass == 0, status.p);
         count_launches(1);
         MSP_CUDA(cudaGetLastError());
@@ -504,7 +512,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
                              mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
             gd[m].b_upper = 1;   // Fi = L^{-T} is upper triangular
         }
-        MSP_TRY(run_gemm(false, maxn, maxc));
+        MSP_TRY(run_gemm(false, maxn, maxc, kGemmStructured));
         // T accumulation: Tacc <- F Tacc
         if (pass == 0) {
             copy_kernel<<<1024, 256, 0, s>>>(F.p, Tacc, mo);
@@ -529,9 +537,16 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
     {
         jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
         count_launches(1);
-        const int smem_max = 226 * 1024;   // leaves room for the kernel's static shared memory
-        int c64 = 0;                       // largest order whose W is held in shared memory
-        while ((long long)(c64 + 1) * (c64 + 2) * (long long)sizeof(double) <= smem_max - 10 * 1024) ++c64;
+        // largest order whose W is held in shared memory: the opt-in limit per
+        // block less the kernel's static shared memory
+        cudaFuncAttributes fa{};
+        MSP_CUDA(cudaFuncGetAttributes(&fa, jacobi_svd_kernel));
+        int dev = 0, optin = 0;
+        MSP_CUDA(cudaGetDevice(&dev));
+        MSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const long long dyn_max = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
+        int c64 = 0;
+        while ((long long)(c64 + 1) * (c64 + 2) * (long long)sizeof(double) <= dyn_max) ++c64;
         c64 = std::min(c64, maxc);
         const size_t sm64 = (size_t)c64 * (c64 + 1) * sizeof(double);
         MSP_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));

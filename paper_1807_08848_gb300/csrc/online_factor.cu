@@ -602,7 +602,10 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                     nn = std::max(nn, steps[sj].g.N);
                     ++sj;
                 }
-                gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s, sj - si == 1 && st.g.C == st.g.A);
+                const GemmDescT<T>& g0 = st.g;
+                const bool structured = g0.lower || g0.b_lower || g0.a_lower || g0.b_upper || g0.a_k_lo;
+                gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s,
+                                (sj - si == 1 && g0.C == g0.A ? kGemmInPlace : 0u) | (structured ? kGemmStructured : 0u));
                 gi += sj - si;
                 si = sj - 1;
             } else if (st.kind == 1) {
