@@ -75,6 +75,29 @@ def test_face_coefficients(small, gpu_fp64):
     np.testing.assert_allclose(aN.cpu().numpy(), off.aN, rtol=1e-14, atol=0)
 
 
+@pytest.mark.parametrize("spec", [
+    synth.lognormal(96, 2.0 ** -4, 64, 1),
+    synth.lognormal(64, 2.0 ** -3, 16, 7, normalised=False),
+    synth.channels(96, 2.0 ** -4, 8, 2, contrast=1e3),
+    synth.hou_wu(100, 2.0 ** -4),
+], ids=["lognormal", "lognormal-unnormalised", "channels", "hou-wu"])
+def test_face_coefficients_every_medium(spec):
+    """Face coefficients of every analytic medium against the oracle's values
+    (Sec. 5, a(x, x/eps); the media of the workloads and the two-scale medium of
+    Sec. 5.3).  Channel faces are 1 or the contrast, so they must agree exactly,
+    except at faces within rounding of a strip edge."""
+    N = spec.n_cells
+    med = msp.Medium(spec, synth.uniform_patches(N, 2, 2, 2, 2))
+    aE, aN = med.coefficients()
+    oE, oN = E.face_coefficients(spec)
+    if spec.kind == synth.MEDIUM_CHANNELS:
+        for g, o in ((aE.cpu().numpy(), oE), (aN.cpu().numpy(), oN)):
+            assert np.mean(g != o) <= 1e-3
+    else:
+        np.testing.assert_allclose(aE.cpu().numpy(), oE, rtol=1e-13, atol=0)
+        np.testing.assert_allclose(aN.cpu().numpy(), oN, rtol=1e-13, atol=0)
+
+
 def test_samples_match_the_generator(small, gpu_fp64):
     w, off, _ = small
     med, _, _ = gpu_fp64

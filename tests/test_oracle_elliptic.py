@@ -46,6 +46,78 @@ def test_channels_medium_two_values():
     assert set(vals.tolist()) <= {1.0, 1e3} and len(vals) == 2
 
 
+def test_hou_wu_medium_hand_values():
+    """The two-scale medium of Sec. 5.3,
+    a = 2 + sin(2 pi x) cos(2 pi y) + (2 + 1.8 sin(2 pi x/eps)) / (2 + 1.8 cos(2 pi y/eps))
+          + (2 + sin(2 pi y/eps)) / (2 + 1.8 cos(2 pi x/eps)),
+    at points where the sines and cosines are 0, +-1, sqrt(2)/2 or sin(pi/8), worked by hand.
+    The points are chosen so that exchanging x and y, dropping eps from one
+    argument or exchanging sin and cos changes the value."""
+    r2 = math.sqrt(0.5)
+    cases = [
+        # (eps, x, y, value)
+        (1.0, 0.0, 0.0, 2.0 + 0.0 + 2.0 / 3.8 + 2.0 / 3.8),
+        (1.0, 0.25, 0.0, 2.0 + 1.0 + 3.8 / 3.8 + 2.0 / 2.0),        # sin(pi/2) cos 0; cos(pi/2) = 0 below
+        (0.5, 0.0, 0.125, 2.0 + 0.0 + 2.0 / 2.0 + 3.0 / 3.8),       # y/eps = 1/4: sin = 1, cos = 0
+        (0.5, 0.125, 0.0, 2.0 + r2 + 3.8 / 3.8 + 2.0 / 2.0),        # x/eps = 1/4; sin(2 pi x) = sqrt(2)/2
+        (0.25, 0.0625, 0.125, 2.0 + math.sin(math.pi / 8) * r2 + 3.8 / 0.2 + 2.0 / 2.0),   # x/eps = 1/4, y/eps = 1/2
+    ]
+    spec = synth.hou_wu(8, 1.0)
+    for eps, x, y, want in cases:
+        spec.eps = eps
+        got = float(E.medium_value(spec, np.array(x), np.array(y)))
+        assert abs(got - want) <= 1e-13 * abs(want), (eps, x, y, got, want)
+
+
+def test_lognormal_medium_hand_values():
+    """a = exp(amp * norm * sum_q [A_q cos(2 pi k_q.x) + B_q sin(2 pi k_q.x)])
+    with two hand-set modes, k = (1, 0) and k = (0, 2): at (1/4, 0) the first
+    phase is pi/2 (its sine term counts), at (0, 1/4) the second phase is pi
+    (its cosine term counts, negated), so a transposed k, a swapped cos/sin
+    or a dropped norm or amp all change the values."""
+    modes = np.array([[1.0, 0.0, 0.3, -0.7],
+                      [0.0, 2.0, 0.5, 0.9]])
+    spec = synth.MediumSpec(synth.MEDIUM_LOGNORMAL, 8, 0.5, modes=modes, amp=0.5, norm=1.0 / math.sqrt(2.0))
+    s = 0.5 / math.sqrt(2.0)
+    cases = [
+        (0.0, 0.0, s * (0.3 + 0.5)),                 # both phases 0: A_1 + A_2
+        (0.25, 0.0, s * (-0.7 + 0.5)),               # phase_1 = pi/2 -> B_1; phase_2 = 0 -> A_2
+        (0.0, 0.25, s * (0.3 - 0.5)),                # phase_1 = 0 -> A_1; phase_2 = pi -> -A_2
+        (0.5, 0.125, s * (-0.3 + 0.9)),              # phase_1 = pi -> -A_1; phase_2 = pi/2 -> B_2
+    ]
+    for x, y, g in cases:
+        got = float(E.medium_value(spec, np.array(x), np.array(y)))
+        assert abs(got - math.exp(g)) <= 1e-14 * math.exp(g), (x, y, got, math.exp(g))
+
+
+def test_channels_medium_hand_strips():
+    """Strips of width w through (px, py) at angle theta: a = contrast where the
+    distance |-(x - px) sin theta + (y - py) cos theta| <= w/2, else 1.  A
+    horizontal strip (theta = 0) measures the distance in y, a vertical one
+    (theta = pi/2) in x, an oblique one (theta = pi/4) |y - x| / sqrt 2; nodes
+    just inside and just outside w/2 = 0.05 decide each case."""
+    def value(px, py, th, x, y):
+        spec = synth.MediumSpec(synth.MEDIUM_CHANNELS, 8, 0.1, channels=np.array([[px, py, th]]),
+                                width=0.1, contrast=1e3)
+        return float(E.medium_value(spec, np.array(x), np.array(y)))
+
+    assert value(0.5, 0.5, 0.0, 0.9, 0.549) == 1e3
+    assert value(0.5, 0.5, 0.0, 0.1, 0.451) == 1e3
+    assert value(0.5, 0.5, 0.0, 0.5, 0.551) == 1.0
+    assert value(0.5, 0.5, 0.0, 0.549, 0.7) == 1.0           # x distance does not count
+    assert value(0.5, 0.5, math.pi / 2, 0.549, 0.9) == 1e3
+    assert value(0.5, 0.5, math.pi / 2, 0.551, 0.5) == 1.0
+    assert value(0.5, 0.5, math.pi / 2, 0.5, 0.9) == 1e3
+    assert value(0.3, 0.3, math.pi / 4, 0.6, 0.6 + 0.07) == 1e3      # distance 0.07 / sqrt 2 = 0.0495
+    assert value(0.3, 0.3, math.pi / 4, 0.6, 0.6 + 0.072) == 1.0     # 0.0509
+    assert value(0.3, 0.3, math.pi / 4, 0.6 + 0.072, 0.6) == 1.0
+    # the union of two strips
+    spec = synth.MediumSpec(synth.MEDIUM_CHANNELS, 8, 0.1,
+                            channels=np.array([[0.5, 0.2, 0.0], [0.2, 0.5, math.pi / 2]]), width=0.1, contrast=7.0)
+    got = E.medium_value(spec, np.array([0.9, 0.22, 0.9, 0.5]), np.array([0.21, 0.9, 0.9, 0.5]))
+    np.testing.assert_array_equal(got, [7.0, 7.0, 1.0, 1.0])
+
+
 # --------------------------------------------------------------- local solver
 
 @pytest.mark.parametrize("poly", [
