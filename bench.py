@@ -66,10 +66,26 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
+    @staticmethod
+    def smi_id(props, index: int) -> str:
+        """nvidia-smi's id of the GPU torch calls `index`: its UUID ("GPU-<uuid>"),
+        because nvidia-smi numbers GPUs in PCI order and ignores
+        CUDA_VISIBLE_DEVICES; the plain index only when the UUID is unknown."""
+        u = getattr(props, "uuid", None)
+        if u is None:
+            return str(index)
+        u = str(u)
+        return u if u.startswith("GPU-") else "GPU-" + u
+
     def start(self):
         try:
+            import torch
+            gid = self.smi_id(torch.cuda.get_device_properties(self.index), self.index)
+        except Exception:
+            gid = str(self.index)
+        try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", "-i", gid, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()

@@ -17,8 +17,10 @@
  *                       of Sec. 3.3), plus the value/flux edge operators and the
  *                       patch blocks of the least-squares system.
  *   msp_online_solve    online stage: c = argmin |P c - d| (Eq.
- *                       elliptic_cond_reduced) by a patch-block (additive
- *                       Schwarz) preconditioned CGLS iteration, then
+ *                       elliptic_cond_reduced) by CGLS preconditioned with a
+ *                       block-tridiagonal Cholesky factor of the normal matrix
+ *                       over rows of patches (or, on request, the patch blocks
+ *                       alone: one-level additive Schwarz), then
  *                       u = sum_m chi_m G_m c_m with a partition of unity.
  *   msp_kinetic_*       the slab radiative-transfer example of Sec. 4 with
  *                       discrete ordinates (Eq. RTE, Eq. rte_random, Eq.
@@ -145,6 +147,15 @@ const char* msp_version(void);
  * (all threads, all devices); for launch accounting in benchmarks. */
 int64_t msp_kernel_launches(void);
 
+/* Bound on the polls of a device-side grid barrier (the cooperative sweeps of the
+ * online factor): a CTA that has polled the barrier this many times without the
+ * rest of the grid arriving gives up, raises the barrier's error word and every
+ * CTA of the launch returns at its next barrier; the call that launched it then
+ * returns MSP_ERR_TIMEOUT and the context stays usable.  Process-wide, read at
+ * every launch.  polls = 0 restores the default (2^24 polls, tens of seconds);
+ * INVALID_ARG if polls < 0.  Small values are for tests of the timeout path. */
+msp_status msp_set_wait_limit(int64_t polls);
+
 /* --------------------------------------------------------------------- medium */
 
 /* Build the patch tables and evaluate the face coefficients on the device
@@ -200,7 +211,13 @@ msp_status msp_get_samples(msp_medium m, int patch, uint64_t seed, double* dst_d
  *   patch_index     the patch's index m in the Philox counter (same samples as
  *                   msp_sample_patches draws for patch m);
  *   samples         Gaussian columns, 1..4096 (no boundary-delta columns);
- *   snap_dev        output, n_k x samples doubles, column-major.
+ *   snap_dev        output, n_k x samples doubles, column-major;
+ *   n_not_converged_host  optional: if not NULL the call synchronises the
+ *                   stream, stores the number of columns whose solve stopped at
+ *                   max_iter and returns MSP_ERR_NOT_CONVERGED if it is not 0
+ *                   (read back from the static array's statistics through a
+ *                   stack buffer); if NULL that count is not reported and the
+ *                   call returns once the launch is enqueued.
  * Its scratch lives in one file-scope device array of 32 MiB that every GPU
  * loading the library holds until the process exits; a buffered patch whose
  * interior exceeds the on-chip tile (98 columns, 12 rows per thread segment)
@@ -212,7 +229,7 @@ msp_status msp_get_samples(msp_medium m, int patch, uint64_t seed, double* dst_d
  * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
 msp_status msp_sample_patch_static(const double* aE_dev, const double* aN_dev, int n_cells, const int* boxes_host,
                                    int patch_index, int samples, uint64_t seed, int precision, double tol,
-                                   int max_iter, double* snap_dev, void* stream);
+                                   int max_iter, double* snap_dev, void* stream, int* n_not_converged_host);
 
 /* Orthonormal basis of every patch's snapshot range (Sec. 3.2, Eq. svd):
  * shifted Cholesky-QR3 of the snapshot block, SVD of its triangular factor by
@@ -326,13 +343,20 @@ msp_status msp_medium_set_graph(msp_medium m, int enable);
  *   phi_dev: [batch][4N] values on the global boundary ring;
  *   u_dev:   [batch][N+1][N+1] reconstructed fields (output);
  *   c_dev:   optional [batch][N_p] coefficients (output) or NULL.
- * CGLS on the normal equations with the patch-block preconditioner
- * (P~^T P~)_mm^{-1}, stopped per data set at |P~^T r| <= tol |P~^T d| or
- * max_iter; every data set's iteration is independent of the others in the
- * batch (fixed-order reductions).  iters_host (optional, [batch]) receives the
- * iteration counts and makes the call synchronise; NOT_CONVERGED if any data
- * set hit max_iter.  u_dev may be NULL when c_dev is given (coefficients only,
- * no reconstruction). */
+ * CGLS on the normal equations, preconditioned as msp_basis_set_preconditioner
+ * selects (default: the block-tridiagonal Cholesky factor of the scaled normal
+ * matrix over rows of patches), stopped per data set at
+ * |P~^T r| <= tol |P~^T d| or max_iter; every data set's iteration is
+ * independent of the others in the batch (fixed-order reductions).
+ * The stop test is read on the host every 2 iterations (every 16 with the
+ * patch-block preconditioner), so the call synchronises the stream while it
+ * iterates; the reconstruction after the last test is enqueued without a
+ * further synchronisation unless iters_host is given.  iters_host (optional,
+ * [batch]) receives the iteration counts; NOT_CONVERGED if any data set hit
+ * max_iter or its residual became NaN or Inf (non-finite phi: that data set
+ * stops at once, the others finish); TIMEOUT if the factor sweeps' grid barrier gave up (see
+ * msp_set_wait_limit).  u_dev may be NULL when c_dev is given (coefficients
+ * only, no reconstruction). */
 msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
                             double* u_dev, double* c_dev, int* iters_host, void* stream);
 

@@ -21,11 +21,17 @@ from . import _native as N
 from ._native import MspError, MSP_FP64, MSP_MIXED
 
 __all__ = ["Medium", "Basis", "Server", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
-           "precision_code"]
+           "precision_code", "set_wait_limit"]
 
 
 def load_library():
     return N.load()
+
+
+def set_wait_limit(polls: int = 0):
+    """Poll bound of the device-side grid barriers (msp_set_wait_limit); 0 restores
+    the default."""
+    N.check(N.load().msp_set_wait_limit(int(polls)))
 
 
 def precision_code(p) -> int:

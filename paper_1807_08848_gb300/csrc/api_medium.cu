@@ -14,6 +14,11 @@ static std::atomic<long long> g_launches{0};
 
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Poll bound of the device-side grid barriers (process-wide, read at each launch).
+constexpr long long kDefaultWaitLimit = 1LL << 24;
+static std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
 
@@ -46,6 +51,13 @@ using namespace msp;
 extern "C" const char* msp_last_error(void) { return g_err.c_str(); }
 extern "C" const char* msp_version(void) { return "msp 0.1 (sm_103a)"; }
 extern "C" int64_t msp_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" msp_status msp_set_wait_limit(int64_t polls) {
+    clear_error();
+    MSP_CHECK_ARG(polls >= 0, "msp_set_wait_limit: polls must be >= 0 (0 restores the default)");
+    g_wait_limit.store(polls == 0 ? kDefaultWaitLimit : (long long)polls, std::memory_order_relaxed);
+    return MSP_OK;
+}
 
 extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch_desc* pd, void* stream,
                                        msp_medium* out) {

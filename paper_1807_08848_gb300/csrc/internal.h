@@ -243,6 +243,8 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
 msp_status apply_online_factor(Basis& B, const double* s_in, double* z_out, int Bsz, cudaStream_t s);
 
 int num_sms();
+// Poll bound of the device-side grid barriers (msp_set_wait_limit).
+long long wait_limit();
 
 // Count of kernel launches issued by the library (for launch accounting).
 void count_launches(long long n);

@@ -59,6 +59,7 @@ struct TileArgs {
     long long slot_doubles;
     int* stats;
     int one_patch_index;      // random stream index of the patch (one-patch variant)
+    PatchDev one_patch;       // the patch of the one-patch variant, passed by value
     gpath::SolveArgs g;       // fused launch: the items that do not fit on chip (global-scratch path)
 };
 
@@ -100,7 +101,7 @@ __device__ __forceinline__ T block_sum1(T v, T* buf) {
     return a[0];
 }
 
-// ONE_PATCH: every item is column `item` of the single patch A.patches[0] whose
+// ONE_PATCH: every item is column `item` of the single patch A.one_patch whose
 // random stream index is A.one_patch_index (the variant without allocations).
 // FUSED: one persistent launch for every item of the medium: the work counter
 // first hands out the A.g items (tiles beyond the on-chip limit, the largest and
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) local_solve_tile(TileArgs A) 
             m = itm.x;
             col = itm.y;
         }
-        const PatchDev P = A.patches[ONE_PATCH ? 0 : m];
+        const PatchDev P = ONE_PATCH ? A.one_patch : A.patches[m];
         const int W = P.X1 - P.X0 + 1, H = P.Y1 - P.Y0 + 1;
         const int nx = W - 2, ny = H - 2;
         Mapping mp;
@@ -607,7 +608,8 @@ msp_status static_scratch_address(void** out) {
 
 extern "C" msp_status msp_sample_patch_static(const double* aE_dev, const double* aN_dev, int n_cells,
                                               const int* boxes_host, int patch_index, int samples, uint64_t seed,
-                                              int precision, double tol, int max_iter, double* snap_dev, void* stream) {
+                                              int precision, double tol, int max_iter, double* snap_dev, void* stream,
+                                              int* n_not_converged_host) {
     using namespace msp;
     clear_error();
     MSP_CHECK_ARG(aE_dev && aN_dev && boxes_host && snap_dev, "msp_sample_patch_static: NULL argument");
@@ -653,19 +655,18 @@ extern "C" msp_status msp_sample_patch_static(const double* aE_dev, const double
     }
     unsigned char* base = nullptr;
     MSP_TRY(static_scratch_address(reinterpret_cast<void**>(&base)));
-    // header: [0, 256) work counter, [256, 512) patch description, [1024, ...) statistics
+    // header: [0, 256) work counter, [1024, ...) per-column statistics (3 ints each)
     int* counter = reinterpret_cast<int*>(base);
-    PatchDev* pdev = reinterpret_cast<PatchDev*>(base + 256);
     int* stats = reinterpret_cast<int*>(base + 1024);
     double* scratch = reinterpret_cast<double*>(base + kStaticHeaderBytes);
     cudaStream_t s = (cudaStream_t)stream;
     MSP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
-    MSP_CUDA(cudaMemcpyAsync(pdev, &P, sizeof(PatchDev), cudaMemcpyHostToDevice, s));
     TileArgs A{};
     A.N = n_cells;
     A.aE = aE_dev;
     A.aN = aN_dev;
-    A.patches = pdev;
+    A.patches = nullptr;
+    A.one_patch = P;
     A.bpos = nullptr;
     A.items = nullptr;
     A.n_items = samples;
@@ -699,5 +700,22 @@ extern "C" msp_status msp_sample_patch_static(const double* aE_dev, const double
 #undef MSP_STATIC_LAUNCH
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
+    if (n_not_converged_host) {
+        // read the not-converged flags back in chunks through a stack buffer: no
+        // allocation on either side
+        MSP_CUDA(cudaStreamSynchronize(s));
+        int bad = 0;
+        int buf[3 * 256];
+        for (int c0 = 0; c0 < samples; c0 += 256) {
+            const int nc = std::min(256, samples - c0);
+            MSP_CUDA(cudaMemcpy(buf, stats + 3 * c0, sizeof(int) * 3 * nc, cudaMemcpyDeviceToHost));
+            for (int c = 0; c < nc; ++c) bad += buf[3 * c + 2] != 0;
+        }
+        *n_not_converged_host = bad;
+        if (bad) {
+            set_error("msp_sample_patch_static: " + std::to_string(bad) + " columns stopped at max_iter");
+            return MSP_ERR_NOT_CONVERGED;
+        }
+    }
     return MSP_OK;
 }

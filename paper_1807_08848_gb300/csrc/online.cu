@@ -236,11 +236,12 @@ __global__ void finalize_beta_kernel(OnArgs A, const double* part, double* scal,
     if (lane == 0) {
         double* sc = scal + 8 * b;
         const double ns = sqrt(ss);
+        // sc[4]: 0 iterating, 1 converged, 2 stopped at max_iter, 3 non-finite residual
         if (mode == 0) {
             sc[0] = sz;
             sc[2] = ns;
             sc[3] = ns;
-            sc[4] = (ns == 0.0) ? 1.0 : 0.0;
+            sc[4] = (ns == 0.0) ? 1.0 : (isfinite(ns) && isfinite(sz)) ? 0.0 : 3.0;
             sc[5] = 0.0;
             sc[7] = 0.0;
         } else if (sc[4] != 0.0) {
@@ -248,7 +249,10 @@ __global__ void finalize_beta_kernel(OnArgs A, const double* part, double* scal,
         } else {
             sc[5] += 1.0;
             sc[3] = ns;
-            if (ns <= tol * sc[2] || sc[5] >= max_iter) {
+            if (!isfinite(ns) || !isfinite(sz)) {
+                sc[4] = 3.0;
+                sc[7] = 0.0;
+            } else if (ns <= tol * sc[2] || sc[5] >= max_iter) {
                 sc[4] = (ns <= tol * sc[2]) ? 1.0 : 2.0;
                 sc[7] = 0.0;
             } else {
@@ -451,7 +455,8 @@ static OnArgs make_args(const Basis& Bs, int B) {
 }
 
 static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, int max_iter, double* u,
-                               double* c_out, int* iters_host, cudaStream_t s, bool* not_conv) {
+                               double* c_out, int* iters_host, cudaStream_t s, bool* not_conv,
+                               bool* nonfinite = nullptr) {
     const int np = (int)Bs.patches.size();
     const int N = Bs.N, n4 = 4 * N;
     OnArgs A = make_args(Bs, B);
@@ -525,11 +530,24 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
         MSP_CUDA(cudaGetLastError());
         if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
             MSP_CUDA(cudaMemcpyAsync(scal.data(), Bs.w_scal.p, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, s));
+            unsigned int bar[4] = {0, 0, 0, 0};
+            if (Bs.d_bt_bar.p)   // the factor sweeps' grid barrier raises its error word on a timeout
+                MSP_CUDA(cudaMemcpyAsync(bar, Bs.d_bt_bar.p, sizeof(bar), cudaMemcpyDeviceToHost, s));
             MSP_CUDA(cudaStreamSynchronize(s));
+            if (bar[2] != 0) {
+                MSP_CUDA(cudaMemsetAsync(Bs.d_bt_bar.p, 0, sizeof(bar), s));
+                set_error("msp_online_solve: grid barrier of the factor sweeps timed out");
+                return MSP_ERR_TIMEOUT;
+            }
             bool all = true;
             for (int b = 0; b < B; ++b) all &= scal[8 * b + 4] != 0.0;
             if (all) break;
         }
+    }
+    // the last stop test read above holds every data set's final state
+    for (int b = 0; b < B; ++b) {
+        if (scal[8 * b + 4] != 1.0) *not_conv = true;
+        if (scal[8 * b + 4] == 3.0 && nonfinite) *nonfinite = true;
     }
     // reconstruction (skipped when only the coefficients are asked for)
     const long long nn = (long long)(N + 1) * (N + 1);
@@ -550,22 +568,8 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
     MSP_CUDA(cudaGetLastError());
     (void)nn;
     if (iters_host) {
-        MSP_CUDA(cudaMemcpyAsync(scal.data(), Bs.w_scal.p, sizeof(double) * 8 * B, cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
-        for (int b = 0; b < B; ++b) {
-            iters_host[b] = (int)scal[8 * b + 5];
-            if (scal[8 * b + 4] != 1.0) *not_conv = true;
-        }
-    }
-    if (Bs.d_bt_bar.p) {   // the sweep kernel's grid barrier reports a timeout here
-        unsigned int h[4] = {0, 0, 0, 0};
-        MSP_CUDA(cudaMemcpyAsync(h, Bs.d_bt_bar.p, sizeof(h), cudaMemcpyDeviceToHost, s));
-        MSP_CUDA(cudaStreamSynchronize(s));
-        if (h[2] != 0) {
-            MSP_CUDA(cudaMemsetAsync(Bs.d_bt_bar.p, 0, sizeof(h), s));
-            set_error("msp_online_solve: grid barrier of the factor sweeps timed out");
-            return MSP_ERR_TIMEOUT;
-        }
+        for (int b = 0; b < B; ++b) iters_host[b] = (int)scal[8 * b + 5];
     }
     return MSP_OK;
 }
@@ -585,13 +589,17 @@ msp_status online_solve(Basis& Bs, const double* phi, int batch, double tol, int
                         int* iters_host, cudaStream_t s) {
     const int N = Bs.N;
     const long long nn = (long long)(N + 1) * (N + 1);
-    bool not_conv = false;
+    bool not_conv = false, nonfinite = false;
     const int cap = online_batch_cap(Bs);
     for (int b0 = 0; b0 < batch; b0 += cap) {
         const int B = std::min(cap, batch - b0);
         MSP_TRY(online_batch(Bs, phi + (long long)b0 * 4 * N, B, tol, max_iter, u ? u + (long long)b0 * nn : nullptr,
                              c_out ? c_out + (long long)b0 * Bs.Np : nullptr, iters_host ? iters_host + b0 : nullptr, s,
-                             &not_conv));
+                             &not_conv, &nonfinite));
+    }
+    if (nonfinite) {
+        set_error("msp_online_solve: a data set's residual is not finite (NaN or Inf in phi); it stopped at once");
+        return MSP_ERR_NOT_CONVERGED;
     }
     if (not_conv) {
         set_error("msp_online_solve: some data sets stopped at max_iter");

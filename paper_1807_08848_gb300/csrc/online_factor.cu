@@ -15,6 +15,8 @@
 // the factorisation is repeated with a diagonal shift.
 #include "internal.h"
 
+#include <mutex>
+
 #include <array>
 #include "dense.cuh"
 #include "device_util.cuh"
@@ -259,9 +261,11 @@ struct SweepArgs {
     T* x;
     unsigned int* bar;         // [0] arrivals, [1] generation
     int* err;
+    long long spin_limit;      // polls of the generation word before a CTA gives up
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int& gen, int* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int& gen, int* err,
+                                             long long spin_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -275,7 +279,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nbl
             const volatile int* e = err;
             long long spins = 0;
             while (*g != target) {
-                if (++spins > (1LL << 24) || *e != 0) {
+                if (++spins > spin_limit || *e != 0) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -353,12 +357,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs<T> A) {
             if (n0 > 0) {
                 sweep_product<T, BT>(A.x + (long long)o0 * B, A.FT + A.e_off[q - 1], n0, A.y + (long long)o * B, n0, nq,
                                      B, T(-1), T(1), gw, nw, lane, xs);
-                if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+                if (!grid_barrier(A.bar, gridDim.x, gen, A.err, A.spin_limit)) return;
             }
         }
         sweep_product<T, BT>(A.y + (long long)o * B, A.LiT + A.d_off[q], nq, A.x + (long long)o * B, nq, nq, B, T(1),
                              T(0), gw, nw, lane, xs);
-        if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+        if (!grid_barrier(A.bar, gridDim.x, gen, A.err, A.spin_limit)) return;
     }
     // backward: x_q -= z_{q+1} C_q;  z_q = x_q Li_q   (z into y)
     for (int q = A.Qn - 1; q >= 0; --q) {
@@ -369,12 +373,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs<T> A) {
             if (n1 > 0) {
                 sweep_product<T, BT>(A.y + (long long)o1 * B, A.F + A.e_off[q], n1, A.x + (long long)o * B, n1, nq, B,
                                      T(-1), T(1), gw, nw, lane, xs);
-                if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+                if (!grid_barrier(A.bar, gridDim.x, gen, A.err, A.spin_limit)) return;
             }
         }
         sweep_product<T, BT>(A.x + (long long)o * B, A.Li + A.d_off[q], nq, A.y + (long long)o * B, nq, nq, B, T(1), T(0),
                              gw, nw, lane, xs);
-        if (!grid_barrier(A.bar, gridDim.x, gen, A.err)) return;
+        if (!grid_barrier(A.bar, gridDim.x, gen, A.err, A.spin_limit)) return;
     }
 }
 
@@ -836,20 +840,31 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
 // z = S (L L^T)^{-1} S s for a batch of Bsz vectors ([element][B] layout, FP64 in and out)
 // Cooperative launch of sweep_kernel: the grid is as many CTAs as are resident
 // at once (at most two per SM), so the grid barrier cannot wait on an unscheduled CTA.
+// The grid size and the shared-memory attribute are set up once per device and
+// instance, under a lock (several host threads may make their first call at once).
 template <class T, int BT>
 msp_status launch_sweeps_bt(SweepArgs<T> A, cudaStream_t s) {
-    static int grid = 0;
+    static std::mutex mu;
+    static std::vector<int> grids;   // per device; 0 = not set up yet
     const size_t smem = sizeof(T) * kSweepKC * BT;
-    if (grid == 0) {
-        MSP_CUDA(cudaFuncSetAttribute(sweep_kernel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int occ = 0;
-        MSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<T, BT>, 512, smem));
-        if (occ < 1) {
-            set_error("online sweeps: the sweep kernel does not fit on an SM");
-            return MSP_ERR_CUDA;
+    int dev = 0, grid = 0;
+    MSP_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if ((int)grids.size() <= dev) grids.resize(dev + 1, 0);
+        if (grids[dev] == 0) {
+            MSP_CUDA(cudaFuncSetAttribute(sweep_kernel<T, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int occ = 0;
+            MSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<T, BT>, 512, smem));
+            if (occ < 1) {
+                set_error("online sweeps: the sweep kernel does not fit on an SM");
+                return MSP_ERR_CUDA;
+            }
+            grids[dev] = num_sms() * std::min(occ, 2);
         }
-        grid = num_sms() * std::min(occ, 2);
+        grid = grids[dev];
     }
+    A.spin_limit = wait_limit();
     void* params[] = {&A};
     MSP_CUDA(cudaLaunchCooperativeKernel((const void*)sweep_kernel<T, BT>, dim3(grid), dim3(512), params, smem, s));
     count_launches(1);

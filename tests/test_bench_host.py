@@ -49,3 +49,22 @@ def test_thermal_and_hardware_slowdown_are_reported():
 def test_missing_nvidia_smi_is_stated():
     c = bench.ClockSampler(0).stop()
     assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_clock_sampler_queries_the_gpu_by_uuid():
+    """nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES, so the
+    sampler names the GPU by the UUID torch reports, not by torch's index."""
+    class Props:
+        uuid = "8c1f3a2e-0000-1111-2222-333344445555"
+
+    assert bench.ClockSampler.smi_id(Props(), 3) == "GPU-8c1f3a2e-0000-1111-2222-333344445555"
+
+    class PropsPrefixed:
+        uuid = "GPU-8c1f3a2e-0000-1111-2222-333344445555"
+
+    assert bench.ClockSampler.smi_id(PropsPrefixed(), 3) == "GPU-8c1f3a2e-0000-1111-2222-333344445555"
+
+    class NoUuid:
+        pass
+
+    assert bench.ClockSampler.smi_id(NoUuid(), 3) == "3"
