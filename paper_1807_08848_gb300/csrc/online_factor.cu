@@ -264,8 +264,12 @@ struct SweepArgs {
     long long spin_limit;      // polls of the generation word before a CTA gives up
 };
 
+// Every thread of a CTA returns the same verdict: thread 0 reads the error word
+// once and hands it to the others through shared memory (another CTA may raise
+// the word at any moment, so per-thread reads could split the CTA).
 __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int& gen, int* err,
                                              long long spin_limit) {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -287,10 +291,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nbl
             }
         }
         __threadfence();
+        s_ok = *((volatile int*)err) == 0;
     }
     ++gen;
     __syncthreads();
-    return *((volatile int*)err) == 0;
+    return s_ok != 0;
 }
 
 // Y[j][b] = alpha sum_k M[k][j] X[k][b] + beta Y[j][b] for b < B, spread over the
