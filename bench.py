@@ -171,6 +171,79 @@ def oracle_sample(budget_s: float = 15.0):
                       f"back-substitution; face coefficients {t_med:.1f} s not counted"}
 
 
+def cpu_model() -> str:
+    """CPU model name of the host (lscpu), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+_ORACLE_STATE = {}
+
+
+def _oracle_worker_init():
+    from oracle import elliptic as E
+    w = synth.workload_batched()
+    _ORACLE_STATE["E"] = E
+    _ORACLE_STATE["w"] = w
+    _ORACLE_STATE["faces"] = E.face_coefficients(w["medium"])
+    _ORACLE_STATE["patches"] = E.patch_boxes(2048, w["patches"])
+
+
+def _oracle_patch_solves(m):
+    E, w = _ORACLE_STATE["E"], _ORACLE_STATE["w"]
+    aE, aN = _ORACLE_STATE["faces"]
+    R = E.snapshots(aE, aN, _ORACLE_STATE["patches"][m], w["seed"], 2048)
+    return R.shape[1]
+
+
+def _noop(_):
+    return os.getpid()
+
+
+def oracle_sample_all_cores(budget_s: float = 15.0, cores: int | None = None):
+    """The CPU oracle on every host core: one process per core (spawned, so it
+    is safe after the CUDA context exists), each solving whole patches of the
+    2049^2 workload (sparse LU + back-substitution, as the oracle stands).  The
+    face coefficients are evaluated once per process before the clock starts.
+    Patches are handed out in a fixed seeded order until the time budget is
+    spent; returns solves/s over the wall time."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    order = np.random.default_rng(0).permutation(1024).tolist()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_worker_init) as pool:
+        pool.map(_noop, range(4 * cores), chunksize=1)          # every worker initialised
+        t0 = time.time()
+        solves, used = 0, 0
+        it = pool.imap_unordered(_oracle_patch_solves, order, chunksize=1)
+        for n in it:
+            solves += n
+            used += 1
+            if time.time() - t0 > budget_s:
+                break
+        dt = time.time() - t0
+        pool.terminate()
+    return {"value": solves / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{solves} local solves ({used} whole patches, seeded order) of the 2049^2 workload, "
+                      f"one spawned process per core, sparse LU + back-substitution per patch; "
+                      f"face coefficients evaluated before the clock"}
+
+
+def cpu_baselines(budget_s: float):
+    """Oracle baseline on one core and on all cores, with the host's core count
+    and CPU model."""
+    one = oracle_sample(budget_s=budget_s)
+    allc = oracle_sample_all_cores(budget_s=budget_s)
+    return {**allc, "one_core": one, "nproc": os.cpu_count(), "cpu_model": cpu_model()}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -215,6 +288,173 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     print(json.dumps({"case": "lognormal-513-8x8", "solves": int(st.n_solves), "cg_iters": int(st.total_iters),
                       "online_iters": oi}))
+
+
+def serve_poisson(srv, phis, arrivals, which, fetch_idx=()):
+    """Submit requests at the given arrival times (seconds from the start) with
+    boundary data phis[i][j] for request j on medium i = which[j]; a poller thread
+    records each request's latency (submit to result on the device) and fetches
+    the results of fetch_idx.  Returns (latencies ms, fetched {j: u}, wall s)."""
+    n_req = len(arrivals)
+    pending, fetched = {}, {}
+    lat = np.full(n_req, np.nan)
+    lock = threading.Lock()
+    finished = threading.Event()
+    fetch_idx = set(fetch_idx)
+
+    def poller():
+        while not finished.is_set() or pending:
+            with lock:
+                items = list(pending.items())
+            for rid, j in items:
+                d, l = srv.poll(rid)
+                if d == 0:
+                    continue
+                lat[j] = l
+                if j in fetch_idx:
+                    fetched[j] = srv.fetch(rid, int(which[j]))
+                else:
+                    srv.release(rid)
+                with lock:
+                    pending.pop(rid, None)
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t_start = time.perf_counter()
+    for j in range(n_req):
+        dt = arrivals[j] - (time.perf_counter() - t_start)
+        if dt > 0:
+            time.sleep(dt)
+        i = int(which[j])
+        rid = srv.submit(i, phis[i][j % len(phis[i])])
+        with lock:
+            pending[rid] = j
+    finished.set()
+    th.join(timeout=900)
+    return lat, fetched, time.perf_counter() - t_start
+
+
+def pct(x, q):
+    x = np.asarray(x)
+    x = x[~np.isnan(x)]
+    return float(np.percentile(x, q)) if x.size else None
+
+
+def online_latency_block(basis, n_req: int, rates, seed: int = 5, workers: int = 4):
+    """Online latency of one medium under Poisson load: the plain FP64 path
+    (the request loop's FP64 engine: FP64 CGLS, FP64 factor applied in FP64) and
+    the mixed path (the request loop's map engine: FP32 map GEMM on the tensor
+    cores), each fed the same arrival times and the same 64 boundary data sets.
+    Reports p50/p99 of submit-to-result latency, throughput, and the error of
+    sampled results against an FP64 online solve to 1e-12."""
+    import torch
+    n = basis.n_cells
+    phis = [synth.phi_fourier(n, 16, 3000 + seed, batch=64)]
+    which = np.zeros(n_req, dtype=np.int64)
+    check = list(range(0, n_req, max(1, n_req // 8)))[:8]
+    basis.set_preconditioner("block_rows_fp64")
+    refs = {}
+    for j in check:
+        r, _ = basis.solve(torch.tensor(phis[0][j % 64], device="cuda"), tol=1e-12, max_iter=5000, want_iters=False)
+        refs[j] = r.cpu().numpy()
+    basis.set_preconditioner("block_rows")
+    out = {"n_nodes": f"{n + 1}^2", "requests": n_req, "workers": workers,
+           "data": "64 distinct 16-mode Fourier boundary data sets, seeded", "loads": []}
+    for rate in rates:
+        arr = synth.poisson_arrivals(rate, n_req, 3)
+        rec = {"offered_rate_hz": rate}
+        for eng, tol in (("iterative_fp64", 1e-8), ("map", None)):
+            srv = msp_server(basis, workers)
+            try:
+                if eng == "map":
+                    srv.set_engine("map")
+                else:
+                    srv.set_engine("iterative_fp64", tol=tol, max_iter=1000)
+                lat, fetched, wall = serve_poisson(srv, phis, arr, which, check)
+                st = srv.stats()
+            finally:
+                srv.close()
+            errs = [float(np.linalg.norm(fetched[j] - refs[j]) / np.linalg.norm(refs[j])) for j in fetched]
+            rec["fp64_iterative" if eng != "map" else "mixed_map"] = {
+                "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput_hz": float(st["completed"] / wall),
+                "completed": int(st["completed"]), "failed": int(st["failed"]), "batches": int(st["batches"]),
+                "max_batch_seen": int(st["max_batch_seen"]),
+                "max_rel_err_vs_fp64_1e-12": max(errs) if errs else None,
+                "engine": ("FP64 CGLS to 1e-8, FP64 factor applied in FP64" if eng != "map"
+                           else "FP32 map on tensor cores (split TF32, FP32/FP64 accumulation)")}
+        out["loads"].append(rec)
+    return out
+
+
+def msp_server(basis, workers):
+    import paper_1807_08848_gb300 as msp
+    return msp.Server([basis], mem_budget_bytes=16 << 30, max_slots=4096, max_batch=32, n_workers=workers)
+
+
+def serving_summary(bench_basis, n_req: int, rate: float, workers: int = 4):
+    """Short serving run over three media (513^2, 1025^2 of the serving workload
+    and the bench's own 2049^2 medium, whose basis and map are already built):
+    Poisson arrivals on a uniformly chosen medium, map engine."""
+    import paper_1807_08848_gb300 as msp
+    wl = synth.workload_serving()
+    bases, meds = [], []
+    t0 = time.time()
+    for md in wl["media"][:2]:
+        med = msp.Medium(md["medium"], md["patches"])
+        med.sample(1, "mixed", tol=1e-10, max_iter=20000, stats=False)
+        b = med.extract(1e-6, "mixed")
+        b.build_map(tol=1e-10, max_iter=5000)
+        meds.append(med)
+        bases.append(b)
+    bases.append(bench_basis)
+    t_setup = time.time() - t0
+    rng = np.random.default_rng(wl["seed"])
+    arr = synth.poisson_arrivals(rate, n_req, wl["seed"])
+    which = rng.integers(0, 3, n_req)
+    phis = [synth.phi_fourier(b.n_cells, 16, 3000 + i, batch=64) for i, b in enumerate(bases)]
+    srv = msp.Server(bases, mem_budget_bytes=16 << 30, max_slots=4096, max_batch=32, n_workers=workers)
+    try:
+        lat, _, wall = serve_poisson(srv, phis, arr, which)
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"media": ["513^2 eps 2^-5 (serving workload)", "1025^2 eps 2^-6 (serving workload)",
+                      "2049^2 eps 2^-7 (the bench workload)"], "requests": n_req, "offered_rate_hz": rate,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "throughput_hz": float(st["completed"] / wall),
+            "completed": int(st["completed"]), "failed": int(st["failed"]), "batches": int(st["batches"]),
+            "max_batch_seen": int(st["max_batch_seen"]), "setup_s_two_media": t_setup}
+
+
+def measure_peaks():
+    """FP32 (CUDA cores), TF32 (tensor cores) and FP64 dense rates of this GPU at
+    its current clocks, from torch.matmul timed with CUDA events (best of 5):
+    the roofline denominators for kernels bound by those units."""
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, dt, n, tf32 in (("fp32_tflops", torch.float32, 8192, False), ("tf32_tflops", torch.float32, 8192, True),
+                              ("fp64_tflops", torch.float64, 4096, False)):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn((n, n), dtype=dt, device="cuda")
+            b = torch.randn((n, n), dtype=dt, device="cuda")
+            c = a @ b
+            best = 1e30
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                torch.matmul(a, b, out=c)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e12
+            del a, b, c
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = "torch.matmul n^3 (fp32/tf32 8192, fp64 4096), best of 5, CUDA events"
+    return out
 
 
 def run_serving(args):
@@ -544,20 +784,21 @@ def run_ours(args, rank, world):
     h2d = int(w["medium"].modes.nbytes + 4 * 4 * (33 + 33 + 1024 + 1024) + phi_host.numel() * 8)
     d2h = int(n * n * 8)
 
-    # ---- online latency on the prebuilt basis (single requests)
+    # ---- online latency on the prebuilt basis: the plain FP64 path and the mixed
+    # (map) path under the same Poisson load and data, then a short three-media
+    # serving run
     basis = state["basis"]
-    lat = []
-    ok = True
-    for i in range(args.online_reqs):
+    online = None
+    serving = None
+    if args.online_reqs > 0:
+        t0 = time.time()
+        basis.build_map(tol=1e-10, max_iter=5000)
         torch.cuda.synchronize()
-        a = time.perf_counter()
-        try:
-            basis.solve(phi_dev, tol=w["online_tol"], max_iter=args.online_iters, want_iters=False)
-        except _native.MspError:
-            ok = False
-        torch.cuda.synchronize()
-        lat.append((time.perf_counter() - a) * 1e3)
-    lat.sort()
+        t_map = time.time() - t0
+        online = online_latency_block(basis, args.online_reqs, rates=args.online_rates)
+        online["map_build_s"] = t_map
+        if args.serve_summary_reqs > 0:
+            serving = serving_summary(basis, args.serve_summary_reqs, args.rate)
 
     # ---- per-stage device times of one step (outside the timed region)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -634,6 +875,10 @@ def run_ours(args, rank, world):
                      "avg_cg_iters": st64.total_iters / max(1, int(st64.n_solves))}
         del med64
 
+    # ---- measured FP32 / TF32 / FP64 rates (roofline denominators)
+    mpk = measure_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+
     # ---- roofline of the dominant kernel: the CG arithmetic of the tile-resident
     # local solves.  Algorithmic flops per CG iteration and unknown of the
     # symmetrically scaled operator (unit diagonal): 9 for the 5-point apply
@@ -647,8 +892,8 @@ def run_ours(args, rank, world):
     achieved = flops / t_kernel / 1e12
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    peak = fp32_peak if prec == "mixed" else fp32_peak / 64.0
+    fp32_derived = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    peak = mpk["fp32_tflops"] if prec == "mixed" else mpk["fp64_tflops"]
     value = aggregate_rate(n_solves, world, t)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -662,9 +907,12 @@ def run_ours(args, rank, world):
         "e2e": {"value": aggregate_rate(n_solves, world, t_e2e), "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches)),
-        "online": {"p50_ms": lat[len(lat) // 2] if lat else None,
-                   "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)] if lat else None,
-                   "requests": len(lat), "converged": ok, "max_iter": args.online_iters},
+        "gaussian_only": {"value": aggregate_rate(n_gauss, world, t), "unit": "Gaussian sample-solves/s",
+                          "note": "the same step counted by its Gaussian columns only (the boundary-delta columns "
+                                  "of the patches on the domain boundary excluded)"},
+        "online": online,
+        "serving": serving,
+        "measured_peaks": {**mpk, "n_sm": n_sm, "fp32_derived_tflops": fp32_derived},
         "local_solve": {"seconds": t_kernel, "solves_per_s": n_solves / t_kernel,
                         "avg_cg_iters": stats.total_iters / max(1, n_solves),
                         "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged},
@@ -677,13 +925,15 @@ def run_ours(args, rank, world):
                      "traffic": traffic_per_solve * n_solves if prec == "mixed" else None,
                      "traffic_source": "ncu capture of the 513^2 case scaled by solves" if prec == "mixed" else None,
                      "kernel": "local_solve_tile<float, 12>" if prec == "mixed" else "local_solve_tile<double, 12>",
-                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"
-                                    + ("" if prec == "mixed" else " / 64 (FP64 rate)")},
+                     "peak_source": ("measured: cuBLAS SGEMM (torch.matmul fp32, TF32 off) in this run" if prec == "mixed"
+                                     else "measured: cuBLAS DGEMM (torch.matmul fp64) in this run")
+                                    + f"; derived FP32 unit peak {fp32_derived:.1f} TFLOP/s "
+                                      f"({n_sm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz)"},
         "clocks": clk,
     }
     if rank == 0:
         if args.cpu_baseline and world >= 1:
-            line["cpu_baseline"] = oracle_sample(budget_s=args.cpu_budget)
+            line["cpu_baseline"] = cpu_baselines(budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
 
 
@@ -695,7 +945,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--online-iters", type=int, default=1000)
-    ap.add_argument("--online-reqs", type=int, default=5)
+    ap.add_argument("--online-reqs", type=int, default=200,
+                    help="requests per load and engine of the online latency block (0: skip it)")
+    ap.add_argument("--online-rates", type=float, nargs="+", default=[2000.0, 50.0],
+                    help="Poisson rates (req/s) of the online latency block")
+    ap.add_argument("--serve-summary-reqs", type=int, default=2000,
+                    help="requests of the three-media serving summary (0: skip it)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-kinetic", dest="kinetic", action="store_false",

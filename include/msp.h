@@ -417,7 +417,9 @@ msp_status msp_get_online_system(msp_basis b, const double* phi_host, int64_t ca
  * the device until it is fetched or released.  Latency = submit to the host
  * seeing the batch complete.  n_workers = 0: no threads; msp_server_step runs
  * one admit + solve + retire cycle on the caller's stream.
- * The server borrows the bases: they must outlive it. */
+ * The server borrows the bases: they must outlive it.  With the map engine
+ * (the default, msp_server_set_engine) every medium needs its map
+ * (msp_basis_build_map); a batch of a medium without one fails with STATE. */
 typedef struct msp_server_s* msp_server;
 typedef struct {
     long long submitted, completed, released, failed, batches;
@@ -440,6 +442,24 @@ msp_status msp_server_release(msp_server s, uint64_t req_id);
  * receives the number of requests it completed. */
 msp_status msp_server_step(msp_server s, void* stream, int* n_done);
 msp_status msp_server_get_stats(msp_server s, msp_server_stats* out);
+/* Engine of the batch solves, read when a batch is admitted (so it may change
+ * between requests):
+ *   MSP_SERVE_MAP (default): one msp_online_solve_map per batch (the FP32 map
+ *     on the tensor cores, FP64 skeleton); INVALID_ARG unless every medium has
+ *     its map;
+ *   MSP_SERVE_ITERATIVE_FP64: the plain FP64 path, the CGLS iteration of
+ *     msp_online_solve to |P~^T r| <= tol |P~^T d| (at most max_iter
+ *     iterations) with an FP64 block-row factor applied in FP64 (the
+ *     preconditioner only sets the pace: residuals and iterates are FP64 with
+ *     either factor precision).  That iteration
+ *     works in the basis's own buffers, so the batches of one medium run one at
+ *     a time (a lock per medium) and the caller must not run msp_online_solve on
+ *     a served basis meanwhile; a batch whose data sets stop at max_iter fails
+ *     with NOT_CONVERGED.
+ * tol and max_iter are ignored by the map engine. */
+#define MSP_SERVE_MAP            0
+#define MSP_SERVE_ITERATIVE_FP64 1
+msp_status msp_server_set_engine(msp_server s, int engine, double tol, int max_iter);
 void msp_server_destroy(msp_server s);
 
 /* --------------------------------------------------------------------- kinetic */

@@ -365,6 +365,12 @@ class Server:
         N.check(N.load().msp_server_step(self._h, _stream_ptr(stream), C.byref(n)))
         return n.value
 
+    def set_engine(self, engine: str = "map", tol: float = 1e-8, max_iter: int = 1000):
+        """Batch solves by the map ("map") or by the plain FP64 iteration
+        ("iterative_fp64", to tol / max_iter)."""
+        code = {"map": 0, "iterative_fp64": 1}[engine]
+        N.check(N.load().msp_server_set_engine(self._h, code, tol, max_iter))
+
     def stats(self) -> dict:
         st = N.ServerStats()
         N.check(N.load().msp_server_get_stats(self._h, C.byref(st)))

@@ -128,6 +128,7 @@ SIGNATURES = {
     "msp_server_release": (_i, [_vp, _u64]),
     "msp_server_step": (_i, [_vp, _vp, C.POINTER(_i)]),
     "msp_server_get_stats": (_i, [_vp, C.POINTER(ServerStats)]),
+    "msp_server_set_engine": (_i, [_vp, _i, _d, _i]),
     "msp_server_destroy": (None, [_vp]),
 }
 

@@ -35,15 +35,29 @@ template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
+    // A request beyond the device's free memory is refused before the call; a
+    // stream-ordered allocation may also report its failure through the last-error
+    // state instead of its return value, so that is read (and cleared) right after.
     msp_status alloc(size_t count, cudaStream_t s) {
         free_now();
         if (count == 0) return MSP_OK;
-        cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), s);
+        const size_t bytes = count * sizeof(T);
+        size_t free_b = 0, total_b = 0;
+        cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+        if (e == cudaSuccess && bytes > free_b) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&p, bytes, s);
+        if (e == cudaSuccess) {
+            const cudaError_t late = cudaGetLastError();
+            if (late != cudaSuccess) {
+                if (p) cudaFreeAsync(p, s);
+                e = late;
+            }
+        }
         if (e != cudaSuccess) {
             p = nullptr;
-            set_error(std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
-                      " bytes failed: " + cudaGetErrorString(e));
-            return MSP_ERR_OOM;
+            set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+                      cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? MSP_ERR_OOM : MSP_ERR_CUDA;
         }
         n = count;
         return MSP_OK;

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -71,6 +72,12 @@ struct Server {
     std::vector<Worker*> workers;
     Worker manual;   // n_workers == 0
     cudaStream_t free_stream = nullptr;   // stream-ordered frees of released results (no device-wide sync)
+    // engine of the batch solves (read under the lock when a batch is admitted):
+    // the map GEMM, or the plain FP64 iteration of msp_online_solve
+    int engine = MSP_SERVE_MAP;
+    double it_tol = 1e-8;
+    int it_max_iter = 1000;
+    std::vector<std::unique_ptr<std::mutex>> medium_mu;   // the iteration uses the basis's own workspace
 
     long long request_bytes(int m) const {
         const long long N = media[m]->N;
@@ -130,15 +137,30 @@ msp_status ensure_worker_buffers(Server& S, Worker& W, int medium, int B) {
         W.phi_n = n4 * S.max_batch;
     }
     if (W.work.size() < S.media.size()) W.work.resize(S.media.size());
-    if (W.work[medium].cap < B) {
+    if (Bs.map_built && W.work[medium].cap < B) {
         map_work_free(W.work[medium]);
         MSP_TRY(map_work_alloc(Bs, S.max_batch, W.work[medium]));
     }
     return MSP_OK;
 }
 
+// The plain FP64 path for one batch: the CGLS iteration of msp_online_solve with
+// the FP64 factor applied in FP64.  The iteration works in the basis's own
+// buffers, so the batches of one medium take its lock.
+msp_status iterative_batch(Server& S, int medium, const double* phi, int B, double* u, double tol, int max_iter,
+                           cudaStream_t stream) {
+    Basis& Bs = *S.media[medium];
+    std::lock_guard<std::mutex> lk(*S.medium_mu[medium]);
+    const int mode = Bs.bt_apply_mode;
+    Bs.bt_apply_mode = 1;
+    const msp_status st = online_solve(Bs, phi, B, tol, max_iter, u, nullptr, nullptr, stream);
+    Bs.bt_apply_mode = mode;
+    return st;
+}
+
 // Runs one admitted batch on the worker's stream and retires it.  Called without the lock.
-msp_status run_batch(Server& S, Worker& W, cudaStream_t stream, int medium, const std::vector<uint64_t>& ids) {
+msp_status run_batch(Server& S, Worker& W, cudaStream_t stream, int medium, const std::vector<uint64_t>& ids, int engine,
+                     double it_tol, int it_max_iter) {
     const Basis& Bs = *S.media[medium];
     const int B = (int)ids.size();
     const size_t n4 = 4 * (size_t)Bs.N;
@@ -167,7 +189,16 @@ msp_status run_batch(Server& S, Worker& W, cudaStream_t stream, int medium, cons
             st = MSP_ERR_CUDA;
         }
     }
-    if (st == MSP_OK) st = online_solve_map(Bs, W.phi_dev, B, mem->u, stream, &W.work[medium]);
+    if (st == MSP_OK) {
+        if (engine == MSP_SERVE_ITERATIVE_FP64) {
+            st = iterative_batch(S, medium, W.phi_dev, B, mem->u, it_tol, it_max_iter, stream);
+        } else if (!Bs.map_built) {
+            set_error("server: the map engine needs msp_basis_build_map on every medium");
+            st = MSP_ERR_STATE;
+        } else {
+            st = online_solve_map(Bs, W.phi_dev, B, mem->u, stream, &W.work[medium]);
+        }
+    }
     if (st == MSP_OK) {
         cudaError_t e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) {
@@ -175,7 +206,7 @@ msp_status run_batch(Server& S, Worker& W, cudaStream_t stream, int medium, cons
             st = MSP_ERR_CUDA;
         }
     }
-    if (st == MSP_OK) st = map_work_check(W.work[medium], stream);
+    if (st == MSP_OK && engine == MSP_SERVE_MAP) st = map_work_check(W.work[medium], stream);
     const double t = now_ms();
     std::lock_guard<std::mutex> lk(S.mu);
     S.st.batches += 1;
@@ -219,10 +250,14 @@ void worker_loop(Server* S, Worker* W) {
     cudaSetDevice(S->device);
     std::vector<uint64_t> ids;
     for (;;) {
-        int medium = -1;
+        int medium = -1, engine = MSP_SERVE_MAP, it_max = 0;
+        double it_tol = 0.0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             while (!S->stop && !admit(*S, medium, ids)) S->cv.wait_for(lk, std::chrono::milliseconds(2));
+            engine = S->engine;
+            it_tol = S->it_tol;
+            it_max = S->it_max_iter;
             if (S->stop) {
                 // give back anything admitted in the same pass
                 for (uint64_t id : ids) {
@@ -235,7 +270,7 @@ void worker_loop(Server* S, Worker* W) {
                 return;
             }
         }
-        run_batch(*S, *W, W->stream, medium, ids);
+        run_batch(*S, *W, W->stream, medium, ids, engine, it_tol, it_max);
     }
 }
 
@@ -283,13 +318,13 @@ extern "C" msp_status msp_server_create(const msp_basis* media, int n_media, lon
     MSP_CHECK_ARG(mem_budget_bytes > 0 && max_slots >= 1, "msp_server_create: budget and slots must be positive");
     MSP_CHECK_ARG(max_batch >= 1 && max_batch <= 64, "msp_server_create: max_batch must lie in [1, 64]");
     MSP_CHECK_ARG(n_workers >= 0 && n_workers <= 16, "msp_server_create: n_workers must lie in [0, 16]");
-    for (int m = 0; m < n_media; ++m) {
-        MSP_CHECK_ARG(media[m], "msp_server_create: NULL basis");
-        MSP_CHECK_ARG(media[m]->B.map_built, "msp_server_create: every medium needs msp_basis_build_map first");
-    }
+    for (int m = 0; m < n_media; ++m) MSP_CHECK_ARG(media[m], "msp_server_create: NULL basis");
     auto* h = new msp_server_s();
     Server& S = h->S;
-    for (int m = 0; m < n_media; ++m) S.media.push_back(&media[m]->B);
+    for (int m = 0; m < n_media; ++m) {
+        S.media.push_back(&media[m]->B);
+        S.medium_mu.emplace_back(new std::mutex());
+    }
     S.budget = mem_budget_bytes;
     S.max_slots = max_slots;
     S.max_batch = max_batch;
@@ -390,17 +425,41 @@ extern "C" msp_status msp_server_step(msp_server h, void* stream, int* n_done) {
     MSP_CHECK_ARG(h, "msp_server_step: NULL server");
     Server& S = h->S;
     MSP_CHECK_ARG(S.workers.empty(), "msp_server_step: the server runs worker threads");
-    int medium = -1;
+    int medium = -1, engine = MSP_SERVE_MAP, it_max = 0;
+    double it_tol = 0.0;
     std::vector<uint64_t> ids;
     {
         std::lock_guard<std::mutex> lk(S.mu);
         admit(S, medium, ids);
+        engine = S.engine;
+        it_tol = S.it_tol;
+        it_max = S.it_max_iter;
     }
     if (n_done) *n_done = 0;
     if (ids.empty()) return MSP_OK;
-    msp_status st = run_batch(S, S.manual, (cudaStream_t)stream, medium, ids);
+    msp_status st = run_batch(S, S.manual, (cudaStream_t)stream, medium, ids, engine, it_tol, it_max);
     if (st == MSP_OK && n_done) *n_done = (int)ids.size();
     return st;
+}
+
+extern "C" msp_status msp_server_set_engine(msp_server h, int engine, double tol, int max_iter) {
+    clear_error();
+    MSP_CHECK_ARG(h, "msp_server_set_engine: NULL server");
+    MSP_CHECK_ARG(engine == MSP_SERVE_MAP || engine == MSP_SERVE_ITERATIVE_FP64, "msp_server_set_engine: unknown engine");
+    Server& S = h->S;
+    if (engine == MSP_SERVE_MAP) {
+        for (Basis* b : S.media)
+            MSP_CHECK_ARG(b->map_built, "msp_server_set_engine: the map engine needs msp_basis_build_map on every medium");
+    } else {
+        MSP_CHECK_ARG(tol > 0 && tol < 1 && max_iter >= 1, "msp_server_set_engine: tol in (0, 1), max_iter >= 1");
+    }
+    std::lock_guard<std::mutex> lk(S.mu);
+    S.engine = engine;
+    if (engine == MSP_SERVE_ITERATIVE_FP64) {
+        S.it_tol = tol;
+        S.it_max_iter = max_iter;
+    }
+    return MSP_OK;
 }
 
 extern "C" msp_status msp_server_get_stats(msp_server h, msp_server_stats* out) {

@@ -195,3 +195,53 @@ def test_server_manual_steps(media):
             assert np.array_equal(u, ref)
     finally:
         srv.close()
+
+
+def test_server_iterative_fp64_engine(media):
+    """The plain FP64 engine of the request loop: every batch is the FP64 CGLS
+    iteration of msp_online_solve (factor applied in FP64), so each result
+    matches the direct FP64 online solve of its own data to the iteration's
+    tolerance and the oracle's least-squares solution to the FP64 bound; the map
+    engine gives the same fields within the mixed bound.  Switching to the map
+    engine needs every medium's map."""
+    w, _, b = media[0]
+    srv = msp.Server([b], mem_budget_bytes=1 << 30, max_slots=16, max_batch=4, n_workers=0)
+    try:
+        srv.set_engine("iterative_fp64", tol=1e-12, max_iter=2000)
+        phis = synth.phi_fourier(b.n_cells, 16, 41, batch=6)
+        ids = [srv.submit(0, p) for p in phis]
+        done = 0
+        for _ in range(10):
+            done += srv.step()
+            if done == 6:
+                break
+        assert done == 6
+        off = E.offline(w["medium"], w["patches"], w["seed"], w["tau"])
+        b.set_preconditioner("block_rows_fp64")
+        try:
+            for rid, p in zip(ids, phis):
+                u = srv.fetch(rid, 0)
+                ref, _ = b.solve(torch.tensor(p, device="cuda"), tol=1e-12, max_iter=2000)
+                assert rel(u, ref.cpu().numpy()) <= 1e-10
+                u_or, *_ = E.online(off, w["patches"], b.n_cells, p)
+                assert rel(u, u_or) <= 1e-8
+                assert rel(b.solve_map(torch.tensor(p, device="cuda")).cpu().numpy(), u) <= MIXED_TOL
+        finally:
+            b.set_preconditioner("block_rows")
+        srv.set_engine("map")
+    finally:
+        srv.close()
+    ms = synth.periodic_sin(32, 1 / 4)
+    med = msp.Medium(ms, synth.uniform_patches(32, 2, 2, 4, 12))
+    med.sample(3, "fp64", tol=1e-12, max_iter=5000)
+    nomap = med.extract(1e-8, "fp64")
+    srv = msp.Server([nomap], mem_budget_bytes=1 << 30, max_slots=8, max_batch=4, n_workers=0)
+    try:
+        with pytest.raises(msp.MspError):
+            srv.set_engine("map")
+        srv.set_engine("iterative_fp64", tol=1e-10, max_iter=500)
+        rid = srv.submit(0, synth.phi_sin_cos(32))
+        assert srv.step() == 1
+        assert np.all(np.isfinite(srv.fetch(rid, 0)))
+    finally:
+        srv.close()
