@@ -153,8 +153,12 @@ msp_status iterative_batch(Server& S, int medium, const double* phi, int B, doub
     std::lock_guard<std::mutex> lk(*S.medium_mu[medium]);
     const int mode = Bs.bt_apply_mode;
     Bs.bt_apply_mode = 1;
-    const msp_status st = online_solve(Bs, phi, B, tol, max_iter, u, nullptr, nullptr, stream);
+    msp_status st = online_solve(Bs, phi, B, tol, max_iter, u, nullptr, nullptr, stream);
     Bs.bt_apply_mode = mode;
+    // the reconstruction is still queued on this stream and reads the basis's
+    // buffers: it must finish before another worker's batch may use them
+    const cudaError_t e = cudaStreamSynchronize(stream);
+    if (st == MSP_OK && e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
     return st;
 }
 

@@ -155,6 +155,24 @@ def test_basis_principal_angles(small, gpu_fp64):
             assert max_principal_angle(Qg[:, :j], Qo[:, :j]) <= 1e-5, (m, j)
 
 
+def test_basis_principal_angles_mixed(small, gpu_mixed):
+    """Mixed-path bases (FP32 CG inside FP64 refinement): the same Wedin rule as
+    the FP64 test, with the snapshot error measured (Frobenius norm, an upper
+    bound of the spectral norm Wedin's bound needs)."""
+    w, off, _ = small
+    med, basis, _ = gpu_mixed
+    for m in range(16):
+        Qg = basis.Q(m).cpu().numpy()
+        Qo = off.Q[m]
+        np.testing.assert_allclose(Qg.T @ Qg, np.eye(Qg.shape[1]), atol=1e-12)
+        so = off.sigma[m]
+        err = float(np.linalg.norm(med.snapshots(m).cpu().numpy() - off.R[m]))
+        dims = [j for j in wedin_dims(so, err) if j <= min(Qg.shape[1], Qo.shape[1])]
+        assert dims, m
+        for j in dims:
+            assert max_principal_angle(Qg[:, :j], Qo[:, :j]) <= 1e-5, (m, j)
+
+
 def test_online_fp64(small, gpu_fp64):
     w, off, u_ref = small
     _, basis, _ = gpu_fp64

@@ -245,3 +245,29 @@ def test_server_iterative_fp64_engine(media):
         assert np.all(np.isfinite(srv.fetch(rid, 0)))
     finally:
         srv.close()
+
+
+def test_server_iterative_fp64_engine_several_workers(media):
+    """Three workers, each with its own stream, serve batches of the same medium
+    with the FP64 engine: the batches share the basis's buffers and run one after
+    another; every result still equals the direct FP64 solve of its own data."""
+    _, _, b = media[1]
+    srv = msp.Server([b], mem_budget_bytes=1 << 30, max_slots=64, max_batch=2, n_workers=3)
+    try:
+        srv.set_engine("iterative_fp64", tol=1e-12, max_iter=2000)
+        phis = synth.phi_fourier(64, 16, 51, batch=9)
+        ids = [srv.submit(0, p) for p in phis]
+        got = []
+        for rid in ids:
+            wait_done(srv, rid)
+            got.append(srv.fetch(rid, 0))
+        assert srv.stats()["batches"] >= 5
+    finally:
+        srv.close()
+    b.set_preconditioner("block_rows_fp64")
+    try:
+        for u, p in zip(got, phis):
+            ref, _ = b.solve(torch.tensor(p, device="cuda"), tol=1e-12, max_iter=2000)
+            assert rel(u, ref.cpu().numpy()) <= 1e-10
+    finally:
+        b.set_preconditioner("block_rows")
