@@ -666,6 +666,56 @@ def run_kinetic(args):
     print(json.dumps(out), flush=True)
 
 
+def run_direct(args):
+    """The 2049^2 workload's local solves by the direct solver (block LDL^T over
+    the grid rows, FP32 inverse Schur complements, FP64 refinement) beside the CG
+    tile kernel, same medium and seed, CUDA events; the factorisation is timed on
+    its own (first call) and inside steady-state calls it is reused."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    w = synth.workload_batched()
+    stream = torch.cuda.current_stream()
+    out = {"case": "direct-2049"}
+
+    def timed(med, reps=3):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            med.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts
+
+    cg = msp.Medium(w["medium"], w["patches"])
+    st = cg.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000)
+    out["cg_ms"] = timed(cg)
+    d = msp.Medium(w["medium"], w["patches"])
+    d.set_launch("mixed", "direct")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    std = d.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["direct_first_call_ms"] = e0.elapsed_time(e1)
+    out["direct_ms"] = timed(d)
+    out["solves"] = int(std.n_solves)
+    out["direct_max_passes"] = int(std.max_iters)
+    out["direct_not_converged"] = int(std.n_not_converged)
+    out["cg_avg_iters"] = st.total_iters / max(1, int(st.n_solves))
+    diffs = []
+    for m in (0, 17, 528, 1023):
+        a = cg.snapshots(m).cpu().numpy()
+        b = d.snapshots(m).cpu().numpy()
+        diffs.append(float(np.linalg.norm(a - b) / np.linalg.norm(a)))
+    out["rel_diff_direct_vs_cg"] = diffs
+    out["direct_solves_per_s"] = out["solves"] / (min(out["direct_ms"]) / 1e3)
+    out["cg_solves_per_s"] = out["solves"] / (min(out["cg_ms"]) / 1e3)
+    print(json.dumps(out), flush=True)
+
+
 def run_uneven(args):
     """The uneven workload: 1025^2 nodes, eps = 2^-6, channel medium of contrast 1e3,
     patches of 16-96 cells with 4-24-cell buffers and 64-256 samples; local solves per
@@ -972,7 +1022,8 @@ def main():
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic"],
+    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic",
+                                                      "direct"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
     ap.add_argument("--requests", type=int, default=10000)
@@ -999,6 +1050,9 @@ def main():
         return
     if args.case == "kinetic":
         run_kinetic(args)
+        return
+    if args.case == "direct":
+        run_direct(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

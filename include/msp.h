@@ -305,11 +305,25 @@ msp_status msp_apply_operator(msp_medium m, int samples, int precision, const vo
  *     whose tile fits on chip, then the global-scratch kernel for the rest;
  *   MSP_LAUNCH_FUSED: one persistent launch for every (patch, column): the CTAs
  *     take the large tiles first (global-scratch path), then the on-chip tiles.
+ *   MSP_LAUNCH_DIRECT (precision MSP_MIXED only; buffered patches of at most 160
+ *     interior nodes per row): the direct local solver -- per patch, a block LDL^T
+ *     factorisation of the Jacobi-scaled operator over the grid rows with FP32
+ *     inverses W_j of the Schur complements (computed once per medium, on the
+ *     first call), applied to chunks of 32 columns by a forward and a backward
+ *     sweep of dense W_j products, inside FP64 iterative refinement (FP64
+ *     residual, FP32 correction) until |r| <= tol |b| per column, at most 8
+ *     passes; the statistics count passes as iterations.  Device memory: the
+ *     inverses (ny ld^2 floats per patch, ld = interior row length rounded up to
+ *     4) and the FP64 iterate, the residual and the forward sweep's blocks of
+ *     every column (about 25 GB at 2049^2 with 32 x 32 patches).
  *   rows: rows per thread segment of the tile kernel, 4, 8 or 12 (0: the smallest
  *     that every eligible tile fits); INVALID_ARG if below that.
- * Results do not depend on the launch: each column's arithmetic is the same. */
+ * Results do not depend on the launch beyond the solver tolerance: the split and
+ * fused launches run each column's arithmetic identically; the direct solver
+ * reaches the same tolerance by another route. */
 #define MSP_LAUNCH_SPLIT 0
 #define MSP_LAUNCH_FUSED 1
+#define MSP_LAUNCH_DIRECT 2
 msp_status msp_medium_set_launch(msp_medium m, int precision, int mode, int rows);
 
 /* Autotuner of that launch: every candidate (split or fused, each rows instance

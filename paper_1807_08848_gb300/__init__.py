@@ -121,7 +121,7 @@ class Medium:
     def set_launch(self, precision="mixed", mode="split", rows: int = 0):
         """Launch of the local solves: 'split' (tile kernel + global kernel) or 'fused'
         (one persistent launch); rows per thread segment 4/8/12 (0: smallest that fits)."""
-        N.check(N.load().msp_medium_set_launch(self._h, precision_code(precision), {"split": 0, "fused": 1}[mode],
+        N.check(N.load().msp_medium_set_launch(self._h, precision_code(precision), {"split": 0, "fused": 1, "direct": 2}[mode],
                                                rows))
 
     def set_graph(self, enable: bool = True):

@@ -35,16 +35,18 @@ template <class T>
 struct DevBuf {
     T* p = nullptr;
     size_t n = 0;
-    // A request beyond the device's free memory is refused before the call; a
-    // stream-ordered allocation may also report its failure through the last-error
-    // state instead of its return value, so that is read (and cleared) right after.
+    // A request beyond the device's whole memory is refused before the call (free
+    // memory is no test: the stream-ordered pool may serve a request from memory it
+    // holds); a stream-ordered allocation may also report its failure through the
+    // last-error state instead of its return value, so that is read (and cleared)
+    // right after.
     msp_status alloc(size_t count, cudaStream_t s) {
         free_now();
         if (count == 0) return MSP_OK;
         const size_t bytes = count * sizeof(T);
         size_t free_b = 0, total_b = 0;
         cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
-        if (e == cudaSuccess && bytes > free_b) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess && bytes > total_b) e = cudaErrorMemoryAllocation;
         if (e == cudaSuccess) e = cudaMallocAsync((void**)&p, bytes, s);
         if (e == cudaSuccess) {
             const cudaError_t late = cudaGetLastError();
@@ -116,6 +118,22 @@ struct Medium {
     int launch_mode[2] = {0, 0};
     int launch_rows[2] = {0, 0};
     bool tuned[2] = {false, false};
+    // direct local solver (launch mode MSP_LAUNCH_DIRECT): per-patch FP32 inverse
+    // Schur complements of the row-block LDL^T factorisation, FP64 refinement state
+    struct Direct {
+        bool planned = false, factored = false;
+        int n_cols = 0, n_chunks = 0, max_nxp = 0;
+        long long w_elems = 0, s_elems = 0, x_elems = 0, r_elems = 0, k_elems = 0;
+        DevBuf<long long> w_off, s_off, x_off, r_off, k_off;   // per patch
+        DevBuf<int> col_base;                                   // per patch: first global column
+        DevBuf<int2> cols;                                      // global column -> (patch, column)
+        DevBuf<int4> chunks;                                    // (patch, first column, columns, -)
+        DevBuf<int> stat_idx;                                   // global column -> statistics slot
+        DevBuf<float> W, D, R, K;
+        DevBuf<double> s, X, b2, r2;
+        DevBuf<int> active, passes;
+        int chunk_smem_max = 0, factor_smem_max = 0;
+    } dir;
     // CUDA graph of the local-solve launches, replayed while the configuration is unchanged
     bool use_graph = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -224,6 +242,9 @@ struct LaunchItems {
     int mode, rows;
 };
 msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s, const LaunchItems* li = nullptr);
+// The direct local solver (launch mode MSP_LAUNCH_DIRECT): eligibility and launch.
+bool direct_fits(const Medium& M);
+msp_status launch_local_solves_direct(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);
 // The local solves of msp_sample_patches: launched directly, or through the medium's
 // CUDA graph when graphs are on (captured on the first call of a configuration).
 msp_status sample_launch(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s);

@@ -83,7 +83,16 @@ extern "C" msp_status msp_medium_set_launch(msp_medium m, int precision, int mod
     clear_error();
     MSP_CHECK_ARG(m, "msp_medium_set_launch: NULL medium");
     MSP_CHECK_ARG(precision == MSP_FP64 || precision == MSP_MIXED, "msp_medium_set_launch: unknown precision");
-    MSP_CHECK_ARG(mode == MSP_LAUNCH_SPLIT || mode == MSP_LAUNCH_FUSED, "msp_medium_set_launch: unknown mode");
+    MSP_CHECK_ARG(mode == MSP_LAUNCH_SPLIT || mode == MSP_LAUNCH_FUSED || mode == MSP_LAUNCH_DIRECT,
+                  "msp_medium_set_launch: unknown mode");
+    if (mode == MSP_LAUNCH_DIRECT) {
+        MSP_CHECK_ARG(precision == MSP_MIXED, "msp_medium_set_launch: the direct solver is a mixed-precision launch");
+        MSP_CHECK_ARG(direct_fits(m->M), "msp_medium_set_launch: the direct solver takes buffered patches of at most "
+                                         "160 interior nodes per row");
+        m->M.launch_mode[1] = MSP_LAUNCH_DIRECT;
+        m->M.launch_rows[1] = 0;
+        return MSP_OK;
+    }
     MSP_CHECK_ARG(rows == 0 || rows == 4 || rows == 8 || rows == 12, "msp_medium_set_launch: rows must be 0, 4, 8 or 12");
     Medium& M = m->M;
     const int pi = precision == MSP_MIXED ? 1 : 0;

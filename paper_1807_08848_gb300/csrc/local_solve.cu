@@ -69,6 +69,7 @@ SolveArgs base_args(Medium& M) {
 msp_status launch_local_solves(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s, const LaunchItems* li) {
     const bool mixed = cfg.precision == MSP_MIXED;
     const int pi = mixed ? 1 : 0;
+    if (!li && M.launch_mode[pi] == MSP_LAUNCH_DIRECT) return launch_local_solves_direct(M, cfg, s);
     const int n_tile = li ? li->n_tile : M.n_tile_items[pi];
     const int2* items = li ? li->tile : M.items_prec[pi].p;
     const int n_rest = li ? li->n_rest : M.n_items - n_tile;
