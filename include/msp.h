@@ -164,6 +164,15 @@ msp_status msp_set_wait_limit(int64_t polls);
  * descriptions (breaks not covering [0,N], non-positive sizes, NULL tables). */
 msp_status msp_build_medium(const msp_medium_desc* medium, const msp_patch_desc* patches,
                             void* stream, msp_medium* out);
+/* The full-basis medium of DetLocalSolu (Algorithm alg:summary, Sec. 3.3): as
+ * msp_build_medium, but every patch m has one delta column per ring node of its
+ * buffered patch and no Gaussian columns (samples_host is ignored and may be
+ * NULL): samples = 0, n_b = cols = n_ring, column t the unit datum at ring
+ * position t.  msp_sample_patches then computes the restricted Green's matrix
+ * G~_m (n_k x n_ring) of the buffered patch -- of K_m itself with buffer 0 --
+ * and msp_extract_basis its singular values and basis as for sampled media. */
+msp_status msp_build_medium_full(const msp_medium_desc* medium, const msp_patch_desc* patches,
+                                 void* stream, msp_medium* out);
 void msp_medium_destroy(msp_medium m);
 
 /* Counts: patches, total snapshot elements, N. */
@@ -194,6 +203,21 @@ msp_status msp_sample_patches(msp_medium m, uint64_t seed, int precision, double
 
 /* Copy patch `patch`'s snapshot block (n_k x cols, column-major) to dst_dev. */
 msp_status msp_get_snapshots(msp_medium m, int patch, double* dst_dev, void* stream);
+
+/* The local solves of the listed patches only (the offline loop of Algorithm
+ * alg:summary restricted to a set of patches: a share of the patches when the
+ * offline stage is split across GPUs).  Every column of each listed patch is
+ * solved as msp_sample_patches solves it (same random data, same launch: the
+ * split or fused CG launch of the medium's setting; a medium set to the direct
+ * solver uses the split launch here); the other patches' snapshot blocks are
+ * left as they are.  Synchronises; stats_host (optional) covers the listed
+ * patches; NOT_CONVERGED as for msp_sample_patches; INVALID_ARG on an index
+ * outside the medium. */
+msp_status msp_sample_patch_list(msp_medium m, const int* patches_host, int n_patches, uint64_t seed, int precision,
+                                 double tol, int max_iter, void* stream, msp_solve_stats* stats_host);
+/* Write patch `patch`'s snapshot block (n_k x cols, column-major) from src_dev,
+ * e.g. a block another GPU computed; the medium then counts as sampled. */
+msp_status msp_set_snapshots(msp_medium m, int patch, const double* src_dev, void* stream);
 
 /* Ring data of patch `patch` as the sampler draws it, (n_ring x cols)
  * column-major, to dst_dev (for checking the generator). */

@@ -63,9 +63,11 @@ class Medium:
     medium: object with kind, n_cells, eps, modes, amp, norm, channels, width,
             contrast, user_aE, user_aN (e.g. synth.MediumSpec).
     patches: object with x_breaks, y_breaks, buffers, samples (e.g. synth.PatchSpec).
+    full_basis: DetLocalSolu -- one delta column per ring node of every buffered
+            patch and no Gaussian columns (msp_build_medium_full; samples ignored).
     """
 
-    def __init__(self, medium, patches, stream=None):
+    def __init__(self, medium, patches, stream=None, full_basis: bool = False):
         lib = N.load()
         self._keep = []
         d = N.MediumDesc()
@@ -96,7 +98,8 @@ class Medium:
         self._keep += [xb, yb, bu, sa]
         p = N.PatchDesc(len(xb) - 1, len(yb) - 1, _i32p(xb), _i32p(yb), _i32p(bu), _i32p(sa))
         h = C.c_void_p()
-        N.check(lib.msp_build_medium(C.byref(d), C.byref(p), _stream_ptr(stream), C.byref(h)))
+        build = lib.msp_build_medium_full if full_basis else lib.msp_build_medium
+        N.check(build(C.byref(d), C.byref(p), _stream_ptr(stream), C.byref(h)))
         self._h = h
         self._keep = []
         npch, ne, nc = C.c_int(), C.c_int64(), C.c_int()
@@ -173,6 +176,25 @@ class Medium:
                                            _stream_ptr(stream), C.byref(st) if stats else None)
         N.check(code)
         return st if stats else None
+
+    def sample_patches(self, patches, seed: int, precision="fp64", tol: float = 1e-12, max_iter: int = 20000,
+                       stream=None):
+        """Local solves of the listed patches only (msp_sample_patch_list)."""
+        lst = np.ascontiguousarray(np.asarray(patches, dtype=np.int32).ravel())
+        st = N.SolveStats()
+        N.check(N.load().msp_sample_patch_list(self._h, _i32p(lst), int(lst.size), C.c_uint64(seed),
+                                               precision_code(precision), tol, max_iter, _stream_ptr(stream),
+                                               C.byref(st)))
+        return st
+
+    def set_snapshots(self, m: int, block: torch.Tensor, stream=None):
+        """Write patch m's snapshot block, an (n_k, cols) tensor as snapshots()
+        returns it (stored column-major)."""
+        info = self.patch(m)
+        assert tuple(block.shape) == (info.n_k, info.cols)
+        t = block.to(dtype=torch.float64, device="cuda").T.contiguous()     # (cols, n_k) row-major
+        N.check(N.load().msp_set_snapshots(self._h, m, _dptr(t), _stream_ptr(stream)))
+        (stream or torch.cuda.current_stream()).synchronize()
 
     def snapshots(self, m: int, stream=None) -> torch.Tensor:
         """Snapshot block of patch m as an (n_k, cols) tensor (column-major storage)."""
@@ -417,6 +439,25 @@ class KineticMedium:
         N.check(N.load().msp_kinetic_sample(self._h, C.c_uint64(seed), precision_code(precision), tol, max_iter,
                                             _stream_ptr(stream), C.byref(st) if stats else None))
         return st if stats else None
+
+    def sample_patches(self, patches, seed: int, precision="fp64", tol: float = 1e-12, max_iter: int = 20000,
+                       stream=None):
+        """Local solves of the listed patches only (msp_sample_patch_list)."""
+        lst = np.ascontiguousarray(np.asarray(patches, dtype=np.int32).ravel())
+        st = N.SolveStats()
+        N.check(N.load().msp_sample_patch_list(self._h, _i32p(lst), int(lst.size), C.c_uint64(seed),
+                                               precision_code(precision), tol, max_iter, _stream_ptr(stream),
+                                               C.byref(st)))
+        return st
+
+    def set_snapshots(self, m: int, block: torch.Tensor, stream=None):
+        """Write patch m's snapshot block, an (n_k, cols) tensor as snapshots()
+        returns it (stored column-major)."""
+        info = self.patch(m)
+        assert tuple(block.shape) == (info.n_k, info.cols)
+        t = block.to(dtype=torch.float64, device="cuda").T.contiguous()     # (cols, n_k) row-major
+        N.check(N.load().msp_set_snapshots(self._h, m, _dptr(t), _stream_ptr(stream)))
+        (stream or torch.cuda.current_stream()).synchronize()
 
     def snapshots(self, m: int, stream=None) -> torch.Tensor:
         t = torch.empty((self.samples, self.n_k), dtype=torch.float64, device="cuda")

@@ -82,12 +82,15 @@ SIGNATURES = {
     "msp_version": (C.c_char_p, []),
     "msp_kernel_launches": (C.c_int64, []),
     "msp_build_medium": (_i, [C.POINTER(MediumDesc), C.POINTER(PatchDesc), _vp, C.POINTER(_vp)]),
+    "msp_build_medium_full": (_i, [C.POINTER(MediumDesc), C.POINTER(PatchDesc), _vp, C.POINTER(_vp)]),
     "msp_medium_destroy": (None, [_vp]),
     "msp_medium_counts": (_i, [_vp, C.POINTER(_i), C.POINTER(C.c_int64), C.POINTER(_i)]),
     "msp_medium_patch": (_i, [_vp, _i, C.POINTER(PatchInfo)]),
     "msp_get_coefficients": (_i, [_vp, _vp, _vp, _vp]),
     "msp_sample_patches": (_i, [_vp, _u64, _i, _d, _i, _vp, C.POINTER(SolveStats)]),
     "msp_get_snapshots": (_i, [_vp, _i, _vp, _vp]),
+    "msp_sample_patch_list": (_i, [_vp, C.POINTER(_i), _i, _u64, _i, _d, _i, _vp, C.POINTER(SolveStats)]),
+    "msp_set_snapshots": (_i, [_vp, _i, _vp, _vp]),
     "msp_get_samples": (_i, [_vp, _i, _u64, _vp, _vp]),
     "msp_sample_patch_static": (_i, [_vp, _vp, _i, C.POINTER(_i), _i, _i, _u64, _i, _d, _i, _vp, _vp, C.POINTER(_i)]),
     "msp_set_wait_limit": (_i, [C.c_int64]),

@@ -59,8 +59,10 @@ extern "C" msp_status msp_set_wait_limit(int64_t polls) {
     return MSP_OK;
 }
 
-extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch_desc* pd, void* stream,
-                                       msp_medium* out) {
+// det: DetLocalSolu (Algorithm alg:summary) -- every patch solves one delta
+// datum per ring node of its buffered patch and no Gaussian data.
+static msp_status build_medium(const msp_medium_desc* d, const msp_patch_desc* pd, void* stream, msp_medium* out,
+                               bool det) {
     clear_error();
     MSP_CHECK_ARG(d && pd && out, "msp_build_medium: NULL argument");
     *out = nullptr;
@@ -76,7 +78,8 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
     if (d->kind == MSP_MEDIUM_PERIODIC_SIN || d->kind == MSP_MEDIUM_HOU_WU)
         MSP_CHECK_ARG(d->eps > 0, "msp_build_medium: eps must be positive");
     const int mx = pd->nx_patches, my = pd->ny_patches;
-    MSP_CHECK_ARG(mx >= 1 && my >= 1 && pd->x_breaks_host && pd->y_breaks_host && pd->buffers_host && pd->samples_host,
+    MSP_CHECK_ARG(mx >= 1 && my >= 1 && pd->x_breaks_host && pd->y_breaks_host && pd->buffers_host &&
+                      (det || pd->samples_host),
                   "msp_build_medium: bad patch description");
     MSP_TRY(need_device());
 
@@ -103,8 +106,8 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
     for (int q = 0; q < my; ++q) {
         for (int p = 0; p < mx; ++p) {
             const int m = p + q * mx;
-            const int b = pd->buffers_host[m], S = pd->samples_host[m];
-            if (b < 0 || S < 1) {
+            const int b = pd->buffers_host[m], S = det ? 0 : pd->samples_host[m];
+            if (b < 0 || (!det && S < 1)) {
                 delete h;
                 set_error("msp_build_medium: buffers must be >= 0 and samples >= 1");
                 return MSP_ERR_INVALID_ARG;
@@ -120,7 +123,7 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
             for (int t = 0; t < P.n_ring; ++t) {
                 int i, j;
                 ring_node(P.X0, P.X1, P.Y0, P.Y1, t, i, j);
-                if (i == 0 || i == N || j == 0 || j == N) M.bpos.push_back(t);
+                if (det || i == 0 || i == N || j == 0 || j == N) M.bpos.push_back(t);
             }
             P.n_b = (int)M.bpos.size() - P.bpos_offset;
             P.cols = S + P.n_b;
@@ -189,6 +192,16 @@ extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch
 #undef BAILC
     *out = h;
     return MSP_OK;
+}
+
+extern "C" msp_status msp_build_medium(const msp_medium_desc* d, const msp_patch_desc* pd, void* stream,
+                                       msp_medium* out) {
+    return build_medium(d, pd, stream, out, false);
+}
+
+extern "C" msp_status msp_build_medium_full(const msp_medium_desc* d, const msp_patch_desc* pd, void* stream,
+                                            msp_medium* out) {
+    return build_medium(d, pd, stream, out, true);
 }
 
 extern "C" void msp_medium_destroy(msp_medium m) {
@@ -267,6 +280,85 @@ extern "C" msp_status msp_sample_patches(msp_medium m, uint64_t seed, int precis
             return MSP_ERR_NOT_CONVERGED;
         }
     }
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_sample_patch_list(msp_medium m, const int* patches_host, int n_list, uint64_t seed,
+                                            int precision, double tol, int max_iter, void* stream,
+                                            msp_solve_stats* stats) {
+    clear_error();
+    MSP_CHECK_ARG(m && (patches_host || n_list == 0), "msp_sample_patch_list: NULL argument");
+    MSP_CHECK_ARG(n_list >= 0, "msp_sample_patch_list: negative patch count");
+    MSP_CHECK_ARG(precision == MSP_FP64 || precision == MSP_MIXED, "msp_sample_patch_list: unknown precision");
+    MSP_CHECK_ARG(tol > 0 && tol < 1, "msp_sample_patch_list: tol must lie in (0, 1)");
+    MSP_CHECK_ARG(max_iter >= 1, "msp_sample_patch_list: max_iter must be >= 1");
+    Medium& M = m->M;
+    const int np = (int)M.patches.size();
+    std::vector<char> want(np, 0);
+    for (int i = 0; i < n_list; ++i) {
+        MSP_CHECK_ARG(patches_host[i] >= 0 && patches_host[i] < np, "msp_sample_patch_list: patch out of range");
+        want[patches_host[i]] = 1;
+    }
+    const int pi = precision == MSP_MIXED ? 1 : 0;
+    // the listed patches' items, in the medium's order: tile-eligible ones first
+    const std::vector<int2>& all = M.items_prec_host[pi];
+    std::vector<int2> sub;
+    int n_tile = 0;
+    for (int i = 0; i < M.n_items; ++i) {
+        if (!want[all[i].x]) continue;
+        sub.push_back(all[i]);
+        if (i < M.n_tile_items[pi]) ++n_tile;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    M.sampled = true;
+    if (sub.empty()) {
+        if (stats) *stats = msp_solve_stats{};
+        return MSP_OK;
+    }
+    DevBuf<int2> d_sub;
+    MSP_TRY(d_sub.alloc(sub.size(), s));
+    MSP_CUDA(cudaMemcpyAsync(d_sub.p, sub.data(), sizeof(int2) * sub.size(), cudaMemcpyHostToDevice, s));
+    LocalSolveCfg cfg{};
+    cfg.precision = precision;
+    cfg.tol = tol;
+    cfg.inner_tol = 1e-4;
+    cfg.max_iter = max_iter;
+    cfg.max_ref = 12;
+    cfg.seed = seed;
+    // the CG launches (a direct-solver setting of the medium applies to whole media only)
+    const int mode = M.launch_mode[pi] == MSP_LAUNCH_FUSED ? MSP_LAUNCH_FUSED : MSP_LAUNCH_SPLIT;
+    LaunchItems li{d_sub.p, n_tile, d_sub.p + n_tile, (int)sub.size() - n_tile, mode, M.launch_rows[pi]};
+    MSP_TRY(launch_local_solves(M, cfg, s, &li));
+    // statistics sit at the subset's positions; read them before d_sub goes
+    std::vector<int> st(3 * sub.size());
+    MSP_CUDA(cudaMemcpyAsync(st.data(), M.item_stats.p, st.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    msp_solve_stats r{};
+    r.n_solves = (long long)sub.size();
+    for (size_t i = 0; i < sub.size(); ++i) {
+        const PatchDev& P = M.patches[sub[i].x];
+        r.unknown_iters += (long long)st[3 * i] * (P.X1 - P.X0 - 1) * (P.Y1 - P.Y0 - 1);
+        r.total_iters += st[3 * i];
+        r.max_iters = std::max(r.max_iters, st[3 * i]);
+        r.max_refinements = std::max(r.max_refinements, st[3 * i + 1]);
+        r.n_not_converged += st[3 * i + 2];
+    }
+    if (stats) *stats = r;
+    if (r.n_not_converged) {
+        set_error("msp_sample_patch_list: " + std::to_string(r.n_not_converged) + " local solves did not converge");
+        return MSP_ERR_NOT_CONVERGED;
+    }
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_set_snapshots(msp_medium m, int patch, const double* src, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(m && src, "msp_set_snapshots: NULL argument");
+    MSP_CHECK_ARG(patch >= 0 && patch < (int)m->M.patches.size(), "msp_set_snapshots: patch out of range");
+    const PatchDev& P = m->M.patches[patch];
+    MSP_CUDA(cudaMemcpyAsync(m->M.snaps.p + P.snap_offset, src, sizeof(double) * (size_t)P.n_k * P.cols,
+                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    m->M.sampled = true;
     return MSP_OK;
 }
 
