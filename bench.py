@@ -716,6 +716,43 @@ def run_direct(args):
     print(json.dumps(out), flush=True)
 
 
+def run_extract(args):
+    """Extraction of the 2049^2 workload's bases (Cholesky-QR3, Jacobi SVD,
+    projection, online operators and factor) with the FP64 products on the tensor
+    cores and on the CUDA cores, same snapshots, CUDA events; the singular values,
+    ranks and an online field of the two are compared."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    torch.cuda.set_device(0)
+    w = synth.workload_batched()
+    stream = torch.cuda.current_stream()
+    med = msp.Medium(w["medium"], w["patches"])
+    med.set_launch("mixed", "direct")
+    med.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000)
+    out = {"case": "extract-2049"}
+    bases = {}
+    for eng in ("tensor_cores", "cuda_cores", "tensor_cores"):
+        msp.set_gemm_engine(eng)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b = med.extract(w["tau"], "mixed")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[eng + "_ms"] = e0.elapsed_time(e1)
+        bases[eng] = b
+    msp.set_gemm_engine("tensor_cores")
+    bt, bc = bases["tensor_cores"], bases["cuda_cores"]
+    out["max_sigma_diff_rel_sigma1"] = max(float(np.max(np.abs(bt.sigma(m) - bc.sigma(m))) / bc.sigma(m)[0])
+                                           for m in range(0, med.n_patches, 37))
+    out["k_equal"] = all(bt.k(m) == bc.k(m) for m in range(med.n_patches))
+    phi = torch.tensor(w["phi"], device="cuda")
+    ut, _ = bt.solve(phi, tol=1e-10, max_iter=1000)
+    uc, _ = bc.solve(phi, tol=1e-10, max_iter=1000)
+    out["online_rel_diff"] = float(torch.linalg.norm(ut - uc) / torch.linalg.norm(uc))
+    out["stats_tc"] = bt.stats()
+    print(json.dumps(out), flush=True)
+
+
 def run_uneven(args):
     """The uneven workload: 1025^2 nodes, eps = 2^-6, channel medium of contrast 1e3,
     patches of 16-96 cells with 4-24-cell buffers and 64-256 samples; local solves per
@@ -1023,7 +1060,7 @@ def main():
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
     ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic",
-                                                      "direct"],
+                                                      "direct", "extract"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
     ap.add_argument("--requests", type=int, default=10000)
@@ -1053,6 +1090,9 @@ def main():
         return
     if args.case == "direct":
         run_direct(args)
+        return
+    if args.case == "extract":
+        run_extract(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -156,6 +156,23 @@ int64_t msp_kernel_launches(void);
  * INVALID_ARG if polls < 0.  Small values are for tests of the timeout path. */
 msp_status msp_set_wait_limit(int64_t polls);
 
+/* Engine of the FP64 matrix products inside msp_extract_basis (the Gram and
+ * triangular products of Cholesky-QR, the projection onto the singular vectors)
+ * and of the large products of the online factorisation:
+ *   MSP_GEMM_TENSOR_CORES (default): FP64-accurate products on the tensor cores --
+ *     each FP64 row / column cut by truncation into 8 BF16 slices of 7 bits under
+ *     a power-of-two scale (error-free splitting, Ozaki et al. 2012), the slice
+ *     products with t + u <= 9 accumulated exactly by tcgen05 kind::f16 MMAs in
+ *     K chunks of 128 and in int32 registers across the chunks, the sum formed in
+ *     FP64; the error of a product is of the order of 2^-56 |a_i|_inf |b_j|_inf per
+ *     term, below the rounding of an FP64 product;
+ *   MSP_GEMM_CUDA_CORES: the FP64 FMA kernels.
+ * Process-wide, read by every extraction; products with K > 16256 use the CUDA
+ * cores.  INVALID_ARG on an unknown engine. */
+#define MSP_GEMM_TENSOR_CORES 0
+#define MSP_GEMM_CUDA_CORES   1
+msp_status msp_set_gemm_engine(int engine);
+
 /* --------------------------------------------------------------------- medium */
 
 /* Build the patch tables and evaluate the face coefficients on the device

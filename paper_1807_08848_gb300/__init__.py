@@ -21,7 +21,7 @@ from . import _native as N
 from ._native import MspError, MSP_FP64, MSP_MIXED
 
 __all__ = ["Medium", "Basis", "Server", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
-           "precision_code", "set_wait_limit"]
+           "precision_code", "set_wait_limit", "set_gemm_engine"]
 
 
 def load_library():
@@ -32,6 +32,12 @@ def set_wait_limit(polls: int = 0):
     """Poll bound of the device-side grid barriers (msp_set_wait_limit); 0 restores
     the default."""
     N.check(N.load().msp_set_wait_limit(int(polls)))
+
+
+def set_gemm_engine(engine: str = "tensor_cores"):
+    """FP64 products of the extraction and the online factorisation on the tensor
+    cores (error-free BF16 slicing, the default) or on the CUDA cores."""
+    N.check(N.load().msp_set_gemm_engine({"tensor_cores": 0, "cuda_cores": 1}[engine]))
 
 
 def precision_code(p) -> int:

@@ -19,6 +19,10 @@ constexpr long long kDefaultWaitLimit = 1LL << 24;
 static std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
 long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
+// Engine of the FP64 products of the extraction and the online factorisation.
+static std::atomic<int> g_gemm_engine{0};
+int fp64_gemm_engine() { return g_gemm_engine.load(std::memory_order_relaxed); }
+
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
 
@@ -51,6 +55,13 @@ using namespace msp;
 extern "C" const char* msp_last_error(void) { return g_err.c_str(); }
 extern "C" const char* msp_version(void) { return "msp 0.1 (sm_103a)"; }
 extern "C" int64_t msp_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" msp_status msp_set_gemm_engine(int engine) {
+    clear_error();
+    MSP_CHECK_ARG(engine == MSP_GEMM_TENSOR_CORES || engine == MSP_GEMM_CUDA_CORES, "msp_set_gemm_engine: unknown engine");
+    g_gemm_engine.store(engine, std::memory_order_relaxed);
+    return MSP_OK;
+}
 
 extern "C" msp_status msp_set_wait_limit(int64_t polls) {
     clear_error();

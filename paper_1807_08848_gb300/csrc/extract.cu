@@ -471,9 +471,16 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
     std::vector<GemmDesc> gd(np);
     DevBuf<GemmDesc> d_gd;
     MSP_TRY(d_gd.alloc(np, s));
+    OzakiWork ozw;
+    const bool tc = fp64_gemm_engine() == MSP_GEMM_TENSOR_CORES;
     auto run_gemm = [&](bool transA, int max_m, int max_n, unsigned flags = 0) -> msp_status {
         MSP_CUDA(cudaMemcpyAsync(d_gd.p, gd.data(), sizeof(GemmDesc) * np, cudaMemcpyHostToDevice, s));
-        gemm_batched(d_gd.p, np, max_m, max_n, transA, s, flags);
+        if (tc && ozaki_gemm_supported(gd)) {
+            MSP_TRY(ozaki_gemm_batched(gd, d_gd.p, transA, false, s, ozw));
+            MSP_TRY(ozaki_check(ozw, s));   // synchronises
+        } else {
+            gemm_batched(d_gd.p, np, max_m, max_n, transA, s, flags);
+        }
         MSP_CUDA(cudaGetLastError());
         MSP_CUDA(cudaStreamSynchronize(s));   // descriptors are reused
         return MSP_OK;

@@ -75,6 +75,25 @@ struct DevBuf {
     DevBuf& operator=(const DevBuf&) = delete;
 };
 
+// Work buffers of the tensor-core FP64 GEMM (ozaki_gemm.cu), grown on demand.
+struct OzakiWork {
+    DevBuf<unsigned short> slices;   // BF16 slices of both operands of every product
+    DevBuf<double> scales;           // power-of-two row / column scales
+    DevBuf<long long> ents;          // per-product tables
+    DevBuf<int> err;                 // set by a timed-out wait
+};
+// FP64 products on the tensor cores (error-free BF16 slicing): every descriptor
+// of h (host copy of d_dev), C = alpha op(A) op(B) + beta C; the structure flags
+// mark zero ranges, tiles strictly above the diagonal are skipped with `lower`.
+bool ozaki_gemm_supported(const std::vector<GemmDesc>& h);
+msp_status ozaki_gemm_batched(const std::vector<GemmDesc>& h, const GemmDesc* d_dev, bool transA, bool transB,
+                              cudaStream_t s, OzakiWork& w);
+// TIMEOUT if a product on this workspace gave up a bounded wait (synchronises).
+msp_status ozaki_check(OzakiWork& w, cudaStream_t s);
+// Engine of the FP64 products of the extraction and the online factorisation:
+// 0 tensor cores (default), 1 CUDA cores.
+int fp64_gemm_engine();
+
 // ------------------------------------------------------------------ geometry
 
 // Per-patch geometry as the kernels see it.

@@ -438,6 +438,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         max_e = std::max<long long>(max_e, (long long)(B.bt_off[q + 2] - B.bt_off[q + 1]) * (B.bt_off[q + 1] - B.bt_off[q]));
     DevBuf<T> ctmp;
     MSP_TRY(ctmp.alloc((size_t)max_e, s));
+    OzakiWork ozw;   // the large FP64 products on the tensor cores
     int hfail = 1;
     {
         MSP_CUDA(cudaMemsetAsync(fail.p, 0, sizeof(int), s));
@@ -613,8 +614,24 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                 }
                 const GemmDescT<T>& g0 = st.g;
                 const bool structured = g0.lower || g0.b_lower || g0.a_lower || g0.b_upper || g0.a_k_lo;
-                gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s,
-                                (sj - si == 1 && g0.C == g0.A ? kGemmInPlace : 0u) | (structured ? kGemmStructured : 0u));
+                bool on_tc = false;
+                if constexpr (sizeof(T) == sizeof(double)) {
+                    // a group worth at least ~2^27 multiply-adds goes to the tensor cores
+                    double work = 0.0;
+                    for (size_t k = si; k < sj; ++k) work += (double)steps[k].g.M * steps[k].g.N * steps[k].g.K;
+                    if (fp64_gemm_engine() == MSP_GEMM_TENSOR_CORES && work >= 134217728.0) {
+                        std::vector<GemmDesc> hg;
+                        for (size_t k = si; k < sj; ++k) hg.push_back(steps[k].g);
+                        if (ozaki_gemm_supported(hg)) {
+                            MSP_TRY(ozaki_gemm_batched(hg, reinterpret_cast<const GemmDesc*>(d_all.p + gi), st.tA, st.tB,
+                                                       s, ozw));
+                            on_tc = true;
+                        }
+                    }
+                }
+                if (!on_tc)
+                    gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s,
+                                    (sj - si == 1 && g0.C == g0.A ? kGemmInPlace : 0u) | (structured ? kGemmStructured : 0u));
                 gi += sj - si;
                 si = sj - 1;
             } else if (st.kind == 1) {
@@ -639,6 +656,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         MSP_CUDA(cudaGetLastError());
         MSP_CUDA(cudaMemcpyAsync(&hfail, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
+        MSP_TRY(ozaki_check(ozw, s));
         B.bt_shift = shift;
     }
     *fail_out = hfail;

@@ -1,0 +1,525 @@
+// FP64-accurate batched GEMM on the fifth-generation tensor cores: the snapshot
+// Gram and basis-projection products of the extraction (Sec. 3.2, Eq. svd; the
+// QR remark of Sec. 3.3) and the large products of the online factorisation.
+//
+// Error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump (2012):
+// every row i of op(A) is scaled by a power of two sigma_i > max_k |a_ik| and cut
+// by truncation into kSlices slices of kBeta bits,
+//     a_ik = sigma_i sum_t d_ik^(t) 2^(-kBeta t),  d^(t) integers with |d| <= 127,
+// and likewise every column j of op(B) with tau_j and slices e^(u).  Each slice
+// is exact in BF16, each product d^(t) e^(u) exact in FP32 (|.| < 2^14), and the
+// products of one diagonal t + u = g are summed by the tensor core (kind::f16,
+// FP32 accumulation in tensor memory) over K chunks of 128, in which at most 8
+// pairs x 128 terms x 2^14 < 2^24 keep every partial sum an exact integer.
+// After each chunk the accumulators are read out of tensor memory and added into
+// int32 registers (exact for K up to 16256), so
+//     C_ij = alpha sigma_i tau_j sum_g 2^(-kBeta g) V_g(i, j) + beta C_ij
+// is formed in FP64 once per element at the end.  Pairs with t + u > kSlices + 1
+// are dropped: with 8 slices of 7 bits each dropped or truncated term is below
+// about 2^-56 sigma_i tau_j, under the rounding of an FP64 product.
+//
+// Structure flags of the descriptors (zero ranges of op(A) or op(B)) are applied
+// while slicing: those entries become zero slices whatever the memory holds.
+// Layout of a sliced operand: [slice][row tile][K slab of 32][row group of 8]
+// [k core of 8][row][k], BF16 -- the no-swizzle K-major layout of the MMA, 16-byte
+// core matrices, K-adjacent cores 128 B apart, 8-row groups 512 B apart; one
+// (slice, row tile, slab) block is contiguous and moves with one bulk copy.
+//
+// MMA kernel: one CTA of 256 threads per 128 x 32 output tile of one product.
+// Thread 0 issues the bulk copies (two stages of 80 KB: 8 A slices of 128 x 32
+// and 8 B slices of 32 x 32) and the MMAs; the 8 diagonal accumulators of a chunk
+// (8 x 32 columns) alternate between two halves of tensor memory, so the read-out
+// of one chunk overlaps the MMAs of the next.  Every wait is bounded: on timeout
+// the CTA records the failure, stops issuing work, waits (bounded) for its issued
+// MMAs, frees its tensor memory and leaves without writing C.
+#include "internal.h"
+#include "dense.cuh"
+
+#include <algorithm>
+#include <cuda_bf16.h>
+#include <vector>
+
+namespace msp {
+
+namespace {
+
+constexpr int kSlices = 8;
+constexpr int kBeta = 7;
+constexpr int kDiag = kSlices;            // diagonals g = t + u = 2 .. kSlices + 1
+constexpr int kTM = 128;                  // output rows per CTA (MMA M)
+constexpr int kTN = 32;                   // output columns per CTA (MMA N)
+constexpr int kSlabK = 32;                // K per staged slab
+constexpr int kChunkSlabs = 4;            // slabs per exactness chunk (K = 128)
+constexpr int kOzThreads = 256;
+constexpr unsigned kAElems = kTM * kSlabK;                    // one A slice block
+constexpr unsigned kBElems = kTN * kSlabK;
+constexpr unsigned kStageBytes = (unsigned)(kSlices * (kAElems + kBElems) * 2);
+constexpr int kOzMaxK = 16256;            // int32 accumulation stays exact up to here
+
+struct OzEntry {
+    long long a_sl, b_sl;                 // element offsets of the sliced operands
+    long long a_sc, b_sc;                 // offsets of the row / column scales
+    int rta, rtb, slabs;                  // row tiles of op(A), of op(B)^T, K slabs
+    int pad;
+};
+static_assert(sizeof(OzEntry) % sizeof(long long) == 0, "entries travel as long long words");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait that also gives up as soon as another thread of the CTA has failed
+__device__ __forceinline__ bool mbar_wait_or_fail(unsigned long long* bar, unsigned parity, volatile int* fail) {
+    for (long long spin = 0; spin < (1LL << 26); ++spin) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((spin & 255) == 255 && fail && *fail) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets (16-byte
+// units), descriptor version 1, no swizzle
+__device__ __forceinline__ unsigned long long smem_desc(const void* p, unsigned lbo, unsigned sbo) {
+    const unsigned long long a = (smem_u32(p) >> 4) & 0x3FFFu;
+    return a | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) | ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) |
+           (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16 (the same type), both
+// K-major, N = 32, M = 128
+constexpr unsigned kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTN >> 3) << 17) |
+                            ((unsigned)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(unsigned d_tmem, unsigned long long a, unsigned long long b, unsigned acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ slicing
+// Operand view: R rows x K, element (r, k) at base[r * sr + k * sk]; zero where
+// the structure of the product says so.
+struct OpView {
+    const double* base;
+    long long sr, sk;
+    int R, K;
+    int lower_k_gt_r;    // entries with k > r are zero (op(A) lower triangular)
+    int zero_k_lt_r;     // entries with k < r are zero (op(B) lower triangular, seen by column)
+    int zero_k_gt_r;     // entries with k > r are zero (op(B) upper triangular, seen by column)
+    const int* k_lo;     // entries with k < k_lo[r] are zero
+};
+
+__device__ __forceinline__ OpView view_a(const GemmDesc& D, bool tA) {
+    OpView v;
+    v.base = D.A;
+    v.sr = tA ? D.lda : 1;
+    v.sk = tA ? 1 : D.lda;
+    v.R = D.M;
+    v.K = D.K;
+    v.lower_k_gt_r = D.a_lower;
+    v.zero_k_lt_r = 0;
+    v.zero_k_gt_r = 0;
+    v.k_lo = D.a_k_lo;
+    return v;
+}
+
+__device__ __forceinline__ OpView view_b(const GemmDesc& D, bool tB) {
+    OpView v;   // rows = columns j of op(B); op(B)[k][j] = tB ? B[k * ldb + j] : B[j * ldb + k]
+    v.base = D.B;
+    v.sr = tB ? 1 : D.ldb;
+    v.sk = tB ? D.ldb : 1;
+    v.R = D.N;
+    v.K = D.K;
+    v.lower_k_gt_r = 0;
+    v.zero_k_lt_r = D.b_lower;
+    v.zero_k_gt_r = D.b_upper;
+    v.k_lo = nullptr;
+    return v;
+}
+
+__device__ __forceinline__ double op_elem(const OpView& v, int r, int k) {
+    if (r >= v.R || k >= v.K) return 0.0;
+    if (v.lower_k_gt_r && k > r) return 0.0;
+    if (v.zero_k_lt_r && k < r) return 0.0;
+    if (v.zero_k_gt_r && k > r) return 0.0;
+    if (v.k_lo && k < v.k_lo[r]) return 0.0;
+    return v.base[(long long)r * v.sr + (long long)k * v.sk];
+}
+
+// Per row: the scale 2^e with 2^(e-1) <= max|x| < 2^e (1 for an all-zero row).
+// One warp per row.
+template <bool IS_B>
+__global__ void __launch_bounds__(256) oz_scale_kernel(const GemmDesc* descs, const OzEntry* ents, bool tA, bool tB,
+                                                       double* scales, int max_rows) {
+    const int z = blockIdx.y;
+    const GemmDesc D = descs[z];
+    const OpView v = IS_B ? view_b(D, tB) : view_a(D, tA);
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= v.R || r >= max_rows) return;
+    double mx = 0.0;
+    for (int k = lane; k < v.K; k += 32) mx = fmax(mx, fabs(op_elem(v, r, k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        int e = 0;
+        if (mx > 0.0) {
+            frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): 2^(e-1) <= mx < 2^e
+        }
+        scales[(IS_B ? ents[z].b_sc : ents[z].a_sc) + r] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+    }
+}
+
+// Slices of every element of the tiled layout (one thread per element, all
+// slices): x = a / scale in (-1, 1); d_t = trunc(2^7 x), x = 2^7 x - d_t.
+template <bool IS_B>
+__global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, const OzEntry* ents, bool tA, bool tB,
+                                                       const double* scales, __nv_bfloat16* out) {
+    const int z = blockIdx.y;
+    const GemmDesc D = descs[z];
+    const OzEntry E = ents[z];
+    const OpView v = IS_B ? view_b(D, tB) : view_a(D, tA);
+    const int RT = IS_B ? kTN : kTM;
+    const int tiles = IS_B ? E.rtb : E.rta;
+    const long long per_slice = (long long)tiles * E.slabs * RT * kSlabK;
+    const long long base = IS_B ? E.b_sl : E.a_sl;
+    const double* sc = scales + (IS_B ? E.b_sc : E.a_sc);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per_slice;
+         e += (long long)gridDim.x * blockDim.x) {
+        // e = [tile][slab][row group][k core][row][k]
+        const int kk = (int)(e & 7);
+        const int rr = (int)((e >> 3) & 7);
+        const int kc = (int)((e >> 6) & 3);
+        long long q = e >> 8;
+        const int rg = (int)(q % (RT / 8));
+        q /= (RT / 8);
+        const int slab = (int)(q % E.slabs);
+        const int tile = (int)(q / E.slabs);
+        const int r = tile * RT + rg * 8 + rr, k = slab * kSlabK + kc * 8 + kk;
+        double x = 0.0;
+        if (r < v.R && k < v.K) x = op_elem(v, r, k) / sc[r];
+#pragma unroll
+        for (int t = 0; t < kSlices; ++t) {
+            const double y = x * (double)(1 << kBeta);
+            const double d = trunc(y);
+            x = y - d;
+            out[base + (long long)t * per_slice + e] = __float2bfloat16_rn((float)d);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ MMA
+struct OzArgs {
+    const GemmDesc* descs;
+    const OzEntry* ents;
+    const __nv_bfloat16* slices;
+    const double* scales;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
+    extern __shared__ __align__(1024) unsigned char oz_smem[];
+    __shared__ __align__(8) unsigned long long full[2], empty[2], accb[2], accfree[2];
+    __shared__ unsigned s_tmem;
+    __shared__ int s_fail;
+    const int z = blockIdx.z;
+    const GemmDesc D = A.descs[z];
+    const OzEntry E = A.ents[z];
+    const int tm = blockIdx.x % E.rta, tn = blockIdx.x / E.rta;
+    if (blockIdx.x >= E.rta * E.rtb) return;                       // whole CTA: uniform
+    if (D.lower && tn * kTN > tm * kTM + kTM - 1) return;          // tile above the diagonal
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&accb[s], 1);
+            mbar_init(&accfree[s], kOzThreads);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = s_tmem;
+    volatile int* fail = &s_fail;
+    const int slabs = E.slabs;
+    const int chunks = (slabs + kChunkSlabs - 1) / kChunkSlabs;
+    const long long a_ps = (long long)E.rta * slabs * kAElems;     // elements per A slice
+    const long long b_ps = (long long)E.rtb * slabs * kBElems;
+    const __nv_bfloat16* a0 = A.slices + E.a_sl + (long long)tm * slabs * kAElems;
+    const __nv_bfloat16* b0 = A.slices + E.b_sl + (long long)tn * slabs * kBElems;
+    unsigned char* stage0 = oz_smem;
+    auto a_stage = [&](int st, int t) { return stage0 + (size_t)st * kStageBytes + (size_t)t * kAElems * 2; };
+    auto b_stage = [&](int st, int u) {
+        return stage0 + (size_t)st * kStageBytes + (size_t)kSlices * kAElems * 2 + (size_t)u * kBElems * 2;
+    };
+    int last_copy[2] = {-1, -1};   // thread 0: last slab copied into each stage
+    auto issue_copy = [&](int slab) {
+        const int st = slab & 1;
+        last_copy[st] = slab;
+        mbar_expect_tx(&full[st], kStageBytes);
+        for (int t = 0; t < kSlices; ++t)
+            bulk_g2s(a_stage(st, t), a0 + t * a_ps + (long long)slab * kAElems, kAElems * 2, &full[st]);
+        for (int u = 0; u < kSlices; ++u)
+            bulk_g2s(b_stage(st, u), b0 + u * b_ps + (long long)slab * kBElems, kBElems * 2, &full[st]);
+    };
+    const unsigned lbo = 128, sbo = 512;
+    int last_commit[2] = {-1, -1};   // thread 0: last chunk committed to each accumulator half
+    // thread 0: the MMAs of one slab; false on a timed-out wait
+    auto mma_slab = [&](int sl) -> bool {
+        const int chunk = sl / kChunkSlabs, first = (sl % kChunkSlabs) == 0;
+        const int half = chunk & 1;
+        if (sl + 1 < slabs) {   // refill the other stage once its MMAs are done
+            if (sl >= 1 && !mbar_wait_or_fail(&empty[(sl - 1) & 1], (unsigned)(((sl - 1) >> 1) & 1), fail))
+                return false;
+            issue_copy(sl + 1);
+        }
+        const int st = sl & 1;
+        if (!mbar_wait_or_fail(&full[st], (unsigned)((sl >> 1) & 1), fail)) return false;
+        if (first && chunk >= 2 && !mbar_wait_or_fail(&accfree[half], (unsigned)(((chunk - 2) >> 1) & 1), fail))
+            return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int t = 0; t < kSlices; ++t) {
+            for (int u = 0; t + u <= kSlices - 1; ++u) {   // t + u (0-based) <= kSlices - 1
+                const int g = t + u;
+                const unsigned d = tmem + (unsigned)(half * (kDiag * kTN) + g * kTN);
+#pragma unroll
+                for (int ks = 0; ks < kSlabK / 16; ++ks) {   // K = 16 per MMA: two core matrices
+                    const unsigned off = ks * 256;
+                    const unsigned long long da = smem_desc(a_stage(st, t) + off, lbo, sbo);
+                    const unsigned long long db = smem_desc(b_stage(st, u) + off, lbo, sbo);
+                    // the first product of diagonal g in a chunk (t = 0, the slab's first K
+                    // step) overwrites the accumulator; every later one adds to it
+                    const unsigned acc = (first && ks == 0 && t == 0) ? 0u : 1u;
+                    mma_bf16(d, da, db, acc);
+                }
+            }
+        }
+        mma_commit(&empty[st]);
+        if ((sl % kChunkSlabs) == kChunkSlabs - 1 || sl == slabs - 1) {
+            mma_commit(&accb[half]);
+            last_commit[half] = chunk;
+        }
+        return true;
+    };
+    // every thread: row (warp & 3) * 32 + lane of the tile, columns (warp >> 2) * 16 + 0..15
+    int vacc[kDiag][16];
+#pragma unroll
+    for (int g = 0; g < kDiag; ++g)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) vacc[g][c] = 0;
+    auto readout = [&](int chunk) -> bool {
+        const int half = chunk & 1;
+        const bool got = mbar_wait_or_fail(&accb[half], (unsigned)((chunk >> 1) & 1), fail);
+        if (!__all_sync(0xffffffffu, got)) {
+            *fail = 1;
+            return false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int g = 0; g < kDiag; ++g) {
+            unsigned r[16];
+            const unsigned taddr = tmem + ((unsigned)((warp & 3) * 32) << 16) +
+                                   (unsigned)(half * (kDiag * kTN) + g * kTN + (warp >> 2) * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 16; ++c) vacc[g][c] += __float2int_rn(__uint_as_float(r[c]));
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accfree[half])) : "memory");
+        return true;
+    };
+    if (tid == 0 && slabs >= 1) issue_copy(0);
+    bool ok = true;   // warp-uniform
+    int done_chunks = 0;
+    for (int sl = 0; sl < slabs; ++sl) {
+        bool f = false;
+        if (tid == 0) f = !mma_slab(sl);
+        if (f) *fail = 1;
+        if (__any_sync(0xffffffffu, f || *fail != 0)) {
+            ok = false;
+            break;
+        }
+        // once the MMAs of a chunk are issued, read out the chunk before it
+        if ((sl % kChunkSlabs) == kChunkSlabs - 1 || sl == slabs - 1) {
+            const int chunk = sl / kChunkSlabs;
+            if (chunk >= 1) {
+                if (!readout(chunk - 1)) {
+                    ok = false;
+                    break;
+                }
+                done_chunks = chunk;
+            }
+        }
+    }
+    if (ok && chunks >= 1 && done_chunks < chunks && !readout(chunks - 1)) ok = false;
+    if (!ok) *fail = 1;
+    __syncthreads();
+    const bool failed = *fail != 0;
+    if (failed && tid == 0) atomicExch(A.err, 1);
+    if (!failed) {
+        const int i = tm * kTM + (warp & 3) * 32 + lane;
+        if (i < D.M) {
+            const double si = A.scales[E.a_sc + i];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int j = tn * kTN + (warp >> 2) * 16 + c;
+                if (j < D.N) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int g = kDiag - 1; g >= 0; --g) v += ldexp((double)vacc[g][c], -kBeta * (g + 2));
+                    v *= si * A.scales[E.b_sc + j];
+                    double* cp = D.C + (long long)j * D.ldc + i;
+                    *cp = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*cp);
+                }
+            }
+        }
+    }
+    if (failed && tid == 0) {
+        // bounded waits for the copies and MMAs already issued, before the shared
+        // and tensor memory they use is given up
+        for (int st = 0; st < 2; ++st)
+            if (last_copy[st] >= 0) mbar_wait_or_fail(&full[st], (unsigned)((last_copy[st] >> 1) & 1), nullptr);
+        for (int h = 0; h < 2; ++h)
+            if (last_commit[h] >= 0) mbar_wait_or_fail(&accb[h], (unsigned)((last_commit[h] >> 1) & 1), nullptr);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
+}  // namespace
+
+bool ozaki_gemm_supported(const std::vector<GemmDesc>& h) {
+    for (const GemmDesc& d : h)
+        if (d.K > kOzMaxK) return false;
+    return true;
+}
+
+msp_status ozaki_gemm_batched(const std::vector<GemmDesc>& h, const GemmDesc* d_dev, bool transA, bool transB,
+                              cudaStream_t s, OzakiWork& w) {
+    const int batch = (int)h.size();
+    if (batch == 0) return MSP_OK;
+    std::vector<OzEntry> ents(batch);
+    long long sl = 0, sc = 0;
+    int max_rows_a = 0, max_rows_b = 0, max_tiles = 0;
+    long long max_a_elems = 0, max_b_elems = 0;
+    for (int z = 0; z < batch; ++z) {
+        const GemmDesc& d = h[z];
+        OzEntry& e = ents[z];
+        e = OzEntry{};
+        e.rta = std::max(1, (d.M + kTM - 1) / kTM);
+        e.rtb = std::max(1, (d.N + kTN - 1) / kTN);
+        e.slabs = std::max(1, (d.K + kSlabK - 1) / kSlabK);
+        const long long a_el = (long long)kSlices * e.rta * e.slabs * kAElems;
+        const long long b_el = (long long)kSlices * e.rtb * e.slabs * kBElems;
+        e.a_sl = sl;
+        sl += a_el;
+        e.b_sl = sl;
+        sl += b_el;
+        e.a_sc = sc;
+        sc += e.rta * kTM;
+        e.b_sc = sc;
+        sc += e.rtb * kTN;
+        max_rows_a = std::max(max_rows_a, d.M);
+        max_rows_b = std::max(max_rows_b, d.N);
+        max_tiles = std::max(max_tiles, e.rta * e.rtb);
+        max_a_elems = std::max(max_a_elems, a_el / kSlices);
+        max_b_elems = std::max(max_b_elems, b_el / kSlices);
+    }
+    if ((long long)w.slices.n < sl) MSP_TRY(w.slices.alloc((size_t)sl, s));
+    if ((long long)w.scales.n < sc) MSP_TRY(w.scales.alloc((size_t)sc, s));
+    const size_t ent_words = sizeof(OzEntry) / sizeof(long long) * (size_t)batch;
+    if (w.ents.n < ent_words) MSP_TRY(w.ents.alloc(ent_words, s));
+    if (!w.err.p) {
+        MSP_TRY(w.err.alloc(1, s));
+        MSP_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int), s));
+    }
+    MSP_CUDA(cudaMemcpyAsync(w.ents.p, ents.data(), sizeof(OzEntry) * batch, cudaMemcpyHostToDevice, s));
+    const OzEntry* d_ents = reinterpret_cast<const OzEntry*>(w.ents.p);
+    __nv_bfloat16* slices = reinterpret_cast<__nv_bfloat16*>(w.slices.p);
+    for (int z0 = 0; z0 < batch; z0 += 65535) {
+        const int nb = std::min(65535, batch - z0);
+        oz_scale_kernel<false><<<dim3((max_rows_a + 7) / 8, nb), 256, 0, s>>>(d_dev + z0, d_ents + z0, transA, transB,
+                                                                              w.scales.p, max_rows_a);
+        oz_scale_kernel<true><<<dim3((max_rows_b + 7) / 8, nb), 256, 0, s>>>(d_dev + z0, d_ents + z0, transA, transB,
+                                                                             w.scales.p, max_rows_b);
+        const int ga = (int)std::min<long long>((max_a_elems + 255) / 256, 4096);
+        const int gb = (int)std::min<long long>((max_b_elems + 255) / 256, 4096);
+        oz_slice_kernel<false><<<dim3(std::max(ga, 1), nb), 256, 0, s>>>(d_dev + z0, d_ents + z0, transA, transB,
+                                                                         w.scales.p, slices);
+        oz_slice_kernel<true><<<dim3(std::max(gb, 1), nb), 256, 0, s>>>(d_dev + z0, d_ents + z0, transA, transB,
+                                                                        w.scales.p, slices);
+        count_launches(4);
+        OzArgs a{};
+        a.descs = d_dev + z0;
+        a.ents = d_ents + z0;
+        a.slices = slices;
+        a.scales = w.scales.p;
+        a.err = w.err.p;
+        const int smem = 2 * (int)kStageBytes;
+        MSP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        oz_mma_kernel<<<dim3(max_tiles, 1, nb), kOzThreads, smem, s>>>(a);
+        count_launches(1);
+        MSP_CUDA(cudaGetLastError());
+    }
+    return MSP_OK;
+}
+
+msp_status ozaki_check(OzakiWork& w, cudaStream_t s) {
+    if (!w.err.p) return MSP_OK;
+    int h = 0;
+    MSP_CUDA(cudaMemcpyAsync(&h, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        MSP_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int), s));
+        set_error("tensor-core FP64 GEMM: a bounded wait timed out");
+        return MSP_ERR_TIMEOUT;
+    }
+    return MSP_OK;
+}
+
+}  // namespace msp

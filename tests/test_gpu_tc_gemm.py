@@ -1,0 +1,83 @@
+"""The FP64 products of the extraction on the tensor cores (error-free BF16
+slicing, tcgen05 kind::f16) against the same extraction on the CUDA cores' FP64
+FMA kernels, and both against the oracle.
+
+The Gram and triangular products of Cholesky-QR and the projection onto the
+singular vectors (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) are FP64-accurate
+either way, so the bases agree far inside the parity bounds: singular values to
+1e-12 sigma_1, bases orthonormal to 1e-12, principal angles of the leading
+subspaces to 1e-8, online fields (Eq. elliptic_cond_reduced) to 1e-10; against
+the oracle the usual bounds hold (sigma 1e-6 sigma_1, online field 1e-8 for the
+plain FP64 path)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import elliptic as E
+
+pytestmark = pytest.mark.gpu
+msp = pytest.importorskip("paper_1807_08848_gb300")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def max_angle(Qa, Qb):
+    s = np.linalg.svd(Qa.T @ Qb, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0))) if s.size else 0.0
+
+
+def extract_both(med, tau, precision):
+    try:
+        msp.set_gemm_engine("cuda_cores")
+        b_cc = med.extract(tau, precision)
+        msp.set_gemm_engine("tensor_cores")
+        b_tc = med.extract(tau, precision)
+    finally:
+        msp.set_gemm_engine("tensor_cores")
+    return b_cc, b_tc
+
+
+@pytest.mark.parametrize("case", ["small", "lognormal-256", "ragged"])
+def test_engines_agree_and_match_the_oracle(case):
+    if case == "small":
+        w = synth.workload_small()
+        ms, ps, seed, tau, N = w["medium"], w["patches"], w["seed"], w["tau"], 128
+    elif case == "lognormal-256":
+        ms, ps, seed, tau, N = synth.lognormal(256, 1 / 16, 32, 3), synth.uniform_patches(256, 4, 4, 16, 64), 5, 1e-6, 256
+    else:
+        N = 60
+        ps = synth.PatchSpec(np.array([0, 13, 37, 60]), np.array([0, 22, 41, 60]),
+                             np.array([3, 0, 5, 2, 4, 1, 6, 3, 2]), np.array([9, 17, 5, 12, 30, 7, 11, 8, 20]))
+        ms, seed, tau = synth.hou_wu(N, 1 / 6), 21, 1e-6
+    med = msp.Medium(ms, ps)
+    med.sample(seed, "fp64", tol=1e-13, max_iter=20000)
+    b_cc, b_tc = extract_both(med, tau, "fp64")
+    off = E.offline(ms, ps, seed, tau)
+    for m in range(ps.n_patches):
+        s_cc, s_tc = b_cc.sigma(m), b_tc.sigma(m)
+        assert np.max(np.abs(s_tc - s_cc)) <= 1e-12 * s_cc[0], m
+        assert np.max(np.abs(s_tc - off.sigma[m])) <= 1e-6 * off.sigma[m][0], m
+        assert b_tc.k(m) == b_cc.k(m) == off.Q[m].shape[1], m
+        Qt, Qc = b_tc.Q(m).cpu().numpy(), b_cc.Q(m).cpu().numpy()
+        np.testing.assert_allclose(Qt.T @ Qt, np.eye(Qt.shape[1]), atol=1e-12)
+        # leading subspaces separated from the rest by a relative gap of 1e-3
+        s = off.sigma[m]
+        for j in range(1, Qt.shape[1]):
+            if (s[j - 1] - s[j]) > 1e-3 * s[0]:
+                assert max_angle(Qt[:, :j], Qc[:, :j]) <= 1e-8, (m, j)
+    phi = torch.tensor(synth.phi_sin_cos(N), device="cuda")
+    u_cc, _ = b_cc.solve(phi, tol=1e-12, max_iter=20000)
+    u_tc, _ = b_tc.solve(phi, tol=1e-12, max_iter=20000)
+    assert rel(u_tc.cpu().numpy(), u_cc.cpu().numpy()) <= 1e-10
+    u_ref, *_ = E.online(off, ps, N, synth.phi_sin_cos(N))
+    assert rel(u_tc.cpu().numpy(), u_ref) <= 1e-8
+
+
+def test_engine_argument():
+    with pytest.raises(KeyError):
+        msp.set_gemm_engine("other")
+    from paper_1807_08848_gb300 import _native as N
+    assert N.load().msp_set_gemm_engine(7) == N.MSP_ERR_INVALID_ARG
