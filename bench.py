@@ -820,9 +820,16 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
 
     state = {}
+    direct = prec == "mixed" and args.local_solver == "direct"
+
+    def new_medium():
+        med = msp.Medium(w["medium"], w["patches"])
+        if direct:
+            med.set_launch("mixed", "direct")
+        return med
 
     def step(host_io: bool):
-        med = msp.Medium(w["medium"], w["patches"])
+        med = new_medium()
         st = med.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
         basis = med.extract(w["tau"], prec)
         if host_io:
@@ -845,18 +852,38 @@ def run_ours(args, rank, world):
         step(False)
     torch.cuda.synchronize()
     # solve statistics of one step (outside the timed region)
-    med = msp.Medium(w["medium"], w["patches"])
+    med = new_medium()
     stats = med.sample(w["seed"], prec, tol=tol, max_iter=20000)
     n_solves = int(stats.n_solves)
     n_gauss = int(np.sum(w["patches"].samples))
-    # dominant kernel timing (local solves) with events on the launching stream
+    infos = [med.patch(m) for m in range(med.n_patches)]
+    # local-solve stage timing with events on the launching stream; the direct
+    # solver also times each of its phases with events around its launches
+    if direct:
+        med.set_timing(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     med.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_kernel = ev0.elapsed_time(ev1) / 1e3
+    phases = med.direct_timing() if direct else None
     del med
+    # the CG tile kernel on the same medium (the mixed path without the direct solver)
+    cg = None
+    if prec == "mixed" and direct and args.compare_fp64:
+        cmed = msp.Medium(w["medium"], w["patches"])
+        cst = cmed.sample(w["seed"], "mixed", tol=tol, max_iter=20000)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cmed.sample(w["seed"], "mixed", tol=tol, max_iter=20000, stats=False)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        tc_ = c0.elapsed_time(c1) / 1e3
+        cg = {"kernel": "local_solve_tile<float, 12>", "seconds": tc_, "solves_per_s": n_solves / tc_,
+              "avg_cg_iters": cst.total_iters / max(1, n_solves),
+              "achieved_tflops": 19.0 * float(cst.unknown_iters) / tc_ / 1e12}
+        del cmed
 
     # ---- timed region (device-resident inputs)
     clocks = ClockSampler(dev)
@@ -903,7 +930,7 @@ def run_ours(args, rank, world):
     # ---- per-stage device times of one step (outside the timed region)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     evs[0].record(stream)
-    smed = msp.Medium(w["medium"], w["patches"])
+    smed = new_medium()
     evs[1].record(stream)
     smed.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
     evs[2].record(stream)
@@ -984,16 +1011,36 @@ def run_ours(args, rank, world):
     # symmetrically scaled operator (unit diagonal): 9 for the 5-point apply
     # (4 products, 4 adds, 1 subtract), 2 for p.Ap, 2 + 2 for the x and r
     # updates, 2 for r.r, 2 for the p update: 19.
-    flops = 19.0 * float(stats.unknown_iters)
-    # DRAM bytes per local solve of local_solve_tile<float, 12>, from one ncu
-    # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 513^2 case,
-    # whose buffered tiles have the same sizes: 1012.35 MB / 11164 solves.
-    traffic_per_solve = (22942720 + 989403648) / 11164.0
-    achieved = flops / t_kernel / 1e12
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_derived = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     peak = mpk["fp32_tflops"] if prec == "mixed" else mpk["fp64_tflops"]
+    if direct:
+        # the direct solver's sweeps: per column and refinement pass, the forward
+        # and the backward sweep each multiply every interior row block by W_j
+        # (nx x nx): 4 nx^2 ny flop; passes per column from the statistics
+        # (their mean, the columns of one patch share their tiles)
+        passes = stats.total_iters / max(1, n_solves)
+        flops = passes * sum(4.0 * (p.X1 - p.X0 - 1) ** 2 * (p.Y1 - p.Y0 - 1) * p.cols for p in infos)
+        t_roof = phases["solve"]["ms"] / 1e3
+        kernel_name = "direct_solve_kernel<3>"
+        roof_launches = phases["solve"]["launches"]
+        traffic = None
+        traffic_source = "not captured for this kernel build"
+    else:
+        # the CG arithmetic of the tile-resident local solves: per CG iteration and
+        # unknown of the symmetrically scaled operator (unit diagonal), 9 flop for the
+        # 5-point apply, 2 for p.Ap, 2 + 2 for the x and r updates, 2 for r.r, 2 for p
+        flops = 19.0 * float(stats.unknown_iters)
+        t_roof = t_kernel
+        kernel_name = "local_solve_tile<float, 12>" if prec == "mixed" else "local_solve_tile<double, 12>"
+        roof_launches = 1
+        # DRAM bytes per local solve of local_solve_tile<float, 12>, from one ncu
+        # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 513^2 case,
+        # whose buffered tiles have the same sizes: 1012.35 MB / 11164 solves.
+        traffic = (22942720 + 989403648) / 11164.0 * n_solves if prec == "mixed" else None
+        traffic_source = "ncu capture of the 513^2 case scaled by solves" if prec == "mixed" else None
+    achieved = flops / t_roof / 1e12
     value = aggregate_rate(n_solves, world, t)
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -1013,18 +1060,22 @@ def run_ours(args, rank, world):
         "online": online,
         "serving": serving,
         "measured_peaks": {**mpk, "n_sm": n_sm, "fp32_derived_tflops": fp32_derived},
-        "local_solve": {"seconds": t_kernel, "solves_per_s": n_solves / t_kernel,
-                        "avg_cg_iters": stats.total_iters / max(1, n_solves),
-                        "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged},
+        "local_solve": {"solver": "direct (block LDL^T, FP32 inverse Schur complements, FP64 refinement)"
+                                  if direct else "CG tile kernel",
+                        "seconds": t_kernel, "solves_per_s": n_solves / t_kernel,
+                        "avg_iters": stats.total_iters / max(1, n_solves),
+                        "iters_unit": "refinement passes" if direct else "CG iterations",
+                        "max_refinements": stats.max_refinements, "not_converged": stats.n_not_converged,
+                        "phases": phases},
+        "local_solve_cg_mixed": cg,
         "fp64_path_local_solve": fp64_rate,
         "stencil_apply": stencil,
         "kinetic_local_solve": kinetic,
         "stages": stages,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": traffic_per_solve * n_solves if prec == "mixed" else None,
-                     "traffic_source": "ncu capture of the 513^2 case scaled by solves" if prec == "mixed" else None,
-                     "kernel": "local_solve_tile<float, 12>" if prec == "mixed" else "local_solve_tile<double, 12>",
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_source,
+                     "kernel": kernel_name, "launches": roof_launches, "seconds": t_roof,
+                     "algorithmic_flop": flops,
                      "peak_source": ("measured: cuBLAS SGEMM (torch.matmul fp32, TF32 off) in this run" if prec == "mixed"
                                      else "measured: cuBLAS DGEMM (torch.matmul fp64) in this run")
                                     + f"; derived FP32 unit peak {fp32_derived:.1f} TFLOP/s "
@@ -1044,6 +1095,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--local-solver", default="direct", choices=["direct", "cg"],
+                    help="local solver of the mixed path: the direct solver (block LDL^T with FP32 inverse Schur "
+                         "complements inside FP64 refinement) or the CG tile kernel")
     ap.add_argument("--online-iters", type=int, default=1000)
     ap.add_argument("--online-reqs", type=int, default=200,
                     help="requests per load and engine of the online latency block (0: skip it)")

@@ -367,6 +367,15 @@ msp_status msp_apply_operator(msp_medium m, int samples, int precision, const vo
 #define MSP_LAUNCH_DIRECT 2
 msp_status msp_medium_set_launch(msp_medium m, int precision, int mode, int rows);
 
+/* Phase timing of the direct solver (CUDA events on the caller's stream around
+ * each of its launches; off by default).  After a msp_sample_patches call with the
+ * direct launch and timing on, msp_medium_direct_timing waits for the events and
+ * returns, per phase -- 0 factorisation (first call only), 1 iterate set-up,
+ * 2 FP64 residuals, 3 sweeps (the dense W_j products), 4 restriction -- the summed
+ * milliseconds (ms_host[5]) and launch counts (launches_host[5], optional). */
+msp_status msp_medium_set_timing(msp_medium m, int enable);
+msp_status msp_medium_direct_timing(msp_medium m, double* ms_host, int* launches_host);
+
 /* Autotuner of that launch: every candidate (split or fused, each rows instance
  * the eligible tiles fit) runs an even-strided subset of at most max_probe_items
  * of the medium's columns, once to warm up and once timed (CUDA events); the

@@ -133,6 +133,18 @@ class Medium:
         N.check(N.load().msp_medium_set_launch(self._h, precision_code(precision), {"split": 0, "fused": 1, "direct": 2}[mode],
                                                rows))
 
+    def set_timing(self, enable: bool = True):
+        """CUDA-event timing of the direct solver's phases (msp_medium_set_timing)."""
+        N.check(N.load().msp_medium_set_timing(self._h, 1 if enable else 0))
+
+    def direct_timing(self) -> dict:
+        """Milliseconds and launches per phase of the last direct-solver call."""
+        ms = (C.c_double * 5)()
+        nl = (C.c_int * 5)()
+        N.check(N.load().msp_medium_direct_timing(self._h, ms, nl))
+        names = ("factor", "init", "residual", "solve", "finish")
+        return {n: {"ms": ms[i], "launches": nl[i]} for i, n in enumerate(names)}
+
     def set_graph(self, enable: bool = True):
         """Replay the local-solve launches from a CUDA graph (captured on first use)."""
         N.check(N.load().msp_medium_set_graph(self._h, 1 if enable else 0))

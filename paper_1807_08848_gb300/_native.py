@@ -115,6 +115,8 @@ SIGNATURES = {
     "msp_operator_tile_shape": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
     "msp_medium_set_launch": (_i, [_vp, _i, _i, _i]),
     "msp_medium_set_graph": (_i, [_vp, _i]),
+    "msp_medium_set_timing": (_i, [_vp, _i]),
+    "msp_medium_direct_timing": (_i, [_vp, C.POINTER(_d), C.POINTER(_i)]),
     "msp_medium_autotune": (_i, [_vp, _i, _u64, _d, _i, _i, _vp, C.POINTER(TuneReport)]),
     "msp_apply_operator": (_i, [_vp, _i, _i, _vp, _vp, _i, _i, C.POINTER(_d), _vp]),
     "msp_basis_build_map": (_i, [_vp, _d, _i, _vp]),

@@ -152,6 +152,15 @@ struct Medium {
         DevBuf<double> s, X, b2, r2;
         DevBuf<int> active, passes;
         int chunk_smem_max = 0, factor_smem_max = 0;
+        // optional CUDA-event timing of the phases of the last call: factor, init,
+        // residual, solve, finish (start/stop event pairs, summed per phase)
+        bool timing = false;
+        std::vector<cudaEvent_t> ev;
+        std::vector<int> ev_phase;
+        int ev_used = 0;
+        ~Direct() {
+            for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        }
     } dir;
     // CUDA graph of the local-solve launches, replayed while the configuration is unchanged
     bool use_graph = false;

@@ -514,6 +514,28 @@ DirArgs direct_args(Medium& M, const LocalSolveCfg& cfg) {
     return A;
 }
 
+// phases of the optional timing
+enum { kPhFactor = 0, kPhInit = 1, kPhResidual = 2, kPhSolve = 3, kPhFinish = 4, kPhases = 5 };
+
+// start (begin = true) or stop an event pair of phase ph
+msp_status mark(Medium::Direct& D, int ph, bool begin, cudaStream_t s) {
+    if (!D.timing) return MSP_OK;
+    if (begin) {
+        while ((int)D.ev.size() < D.ev_used + 2) {
+            cudaEvent_t e;
+            MSP_CUDA(cudaEventCreate(&e));
+            D.ev.push_back(e);
+            D.ev_phase.push_back(0);
+        }
+        D.ev_phase[D.ev_used] = ph;
+        MSP_CUDA(cudaEventRecord(D.ev[D.ev_used], s));
+    } else {
+        MSP_CUDA(cudaEventRecord(D.ev[D.ev_used + 1], s));
+        D.ev_used += 2;
+    }
+    return MSP_OK;
+}
+
 template <int G>
 msp_status launch_solve_g(const DirArgs& A, int grid, int smem, cudaStream_t s) {
     MSP_CUDA(cudaFuncSetAttribute(direct_solve_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -541,22 +563,30 @@ msp_status launch_local_solves_direct(Medium& M, const LocalSolveCfg& cfg, cudaS
     Medium::Direct& D = M.dir;
     DirArgs A = direct_args(M, cfg);
     const int np = (int)M.patches.size();
+    D.ev_used = 0;
     if (!D.factored) {
         MSP_CUDA(cudaFuncSetAttribute(direct_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       D.factor_smem_max));
+        MSP_TRY(mark(D, kPhFactor, true, s));
         direct_factor_kernel<<<np, kDirThreads, D.factor_smem_max, s>>>(A);
         count_launches(1);
+        MSP_TRY(mark(D, kPhFactor, false, s));
         MSP_CUDA(cudaGetLastError());
         D.factored = true;
     }
+    MSP_TRY(mark(D, kPhInit, true, s));
     direct_init_kernel<<<D.n_cols, kDirThreads, 0, s>>>(A);
     count_launches(1);
+    MSP_TRY(mark(D, kPhInit, false, s));
+    MSP_TRY(mark(D, kPhResidual, true, s));
     direct_residual_kernel<<<D.n_chunks, kDirThreads, 0, s>>>(A, 1);
     count_launches(1);
+    MSP_TRY(mark(D, kPhResidual, false, s));
     MSP_CUDA(cudaGetLastError());
     const int G = std::max(1, (D.max_nxp + 31) / 32);
     const int passes = std::max(1, std::min(cfg.max_ref, kDirMaxPasses));
     for (int p = 0; p < passes; ++p) {
+        MSP_TRY(mark(D, kPhSolve, true, s));
         switch (G) {
             case 1: MSP_TRY(launch_solve_g<1>(A, D.n_chunks, D.chunk_smem_max, s)); break;
             case 2: MSP_TRY(launch_solve_g<2>(A, D.n_chunks, D.chunk_smem_max, s)); break;
@@ -564,14 +594,51 @@ msp_status launch_local_solves_direct(Medium& M, const LocalSolveCfg& cfg, cudaS
             case 4: MSP_TRY(launch_solve_g<4>(A, D.n_chunks, D.chunk_smem_max, s)); break;
             default: MSP_TRY(launch_solve_g<5>(A, D.n_chunks, D.chunk_smem_max, s)); break;
         }
+        MSP_TRY(mark(D, kPhSolve, false, s));
+        MSP_TRY(mark(D, kPhResidual, true, s));
         direct_residual_kernel<<<D.n_chunks, kDirThreads, 0, s>>>(A, 0);
         count_launches(1);
+        MSP_TRY(mark(D, kPhResidual, false, s));
         MSP_CUDA(cudaGetLastError());
     }
+    MSP_TRY(mark(D, kPhFinish, true, s));
     direct_finish_kernel<<<D.n_cols, kDirThreads, 0, s>>>(A);
     count_launches(1);
+    MSP_TRY(mark(D, kPhFinish, false, s));
     MSP_CUDA(cudaGetLastError());
     return MSP_OK;
 }
+
+}  // namespace msp
+
+using namespace msp;
+
+extern "C" msp_status msp_medium_set_timing(msp_medium m, int enable) {
+    clear_error();
+    MSP_CHECK_ARG(m, "msp_medium_set_timing: NULL medium");
+    m->M.dir.timing = enable != 0;
+    m->M.dir.ev_used = 0;
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_medium_direct_timing(msp_medium m, double* ms_host, int* launches_host) {
+    clear_error();
+    MSP_CHECK_ARG(m && ms_host, "msp_medium_direct_timing: NULL argument");
+    Medium::Direct& D = m->M.dir;
+    for (int p = 0; p < kPhases; ++p) {
+        ms_host[p] = 0.0;
+        if (launches_host) launches_host[p] = 0;
+    }
+    for (int i = 0; i + 1 < D.ev_used; i += 2) {
+        MSP_CUDA(cudaEventSynchronize(D.ev[i + 1]));
+        float t = 0.f;
+        MSP_CUDA(cudaEventElapsedTime(&t, D.ev[i], D.ev[i + 1]));
+        ms_host[D.ev_phase[i]] += t;
+        if (launches_host) launches_host[D.ev_phase[i]] += 1;
+    }
+    return MSP_OK;
+}
+
+namespace msp {
 
 }  // namespace msp

@@ -5,8 +5,8 @@ FMA kernels, and both against the oracle.
 The Gram and triangular products of Cholesky-QR and the projection onto the
 singular vectors (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) are FP64-accurate
 either way, so the bases agree far inside the parity bounds: singular values to
-1e-12 sigma_1, bases orthonormal to 1e-12, principal angles of the leading
-subspaces to 1e-8, online fields (Eq. elliptic_cond_reduced) to 1e-10; against
+1e-12 sigma_1, bases orthonormal to 1e-11 (the corner patches, rank-deficient, lose about 1e-12 in either engine), principal angles of the leading
+subspaces to 1e-10 (sine of the largest principal angle), online fields (Eq. elliptic_cond_reduced) to 1e-10; against
 the oracle the usual bounds hold (sigma 1e-6 sigma_1, online field 1e-8 for the
 plain FP64 path)."""
 import numpy as np
@@ -24,9 +24,12 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def max_angle(Qa, Qb):
-    s = np.linalg.svd(Qa.T @ Qb, compute_uv=False)
-    return float(np.arccos(np.clip(s.min(), -1.0, 1.0))) if s.size else 0.0
+def sin_angle(Qa, Qb):
+    """Sine of the largest principal angle, |(I - Qa Qa^T) Qb|_2: unlike the arccos
+    of the smallest singular value of Qa^T Qb it stays accurate for tiny angles
+    (a basis orthonormal to 1e-12 puts that cosine 1e-12 below 1, whose arccos
+    reads 1.5e-6)."""
+    return float(np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2)) if Qb.size else 0.0
 
 
 def extract_both(med, tau, precision):
@@ -62,12 +65,12 @@ def test_engines_agree_and_match_the_oracle(case):
         assert np.max(np.abs(s_tc - off.sigma[m])) <= 1e-6 * off.sigma[m][0], m
         assert b_tc.k(m) == b_cc.k(m) == off.Q[m].shape[1], m
         Qt, Qc = b_tc.Q(m).cpu().numpy(), b_cc.Q(m).cpu().numpy()
-        np.testing.assert_allclose(Qt.T @ Qt, np.eye(Qt.shape[1]), atol=1e-12)
+        np.testing.assert_allclose(Qt.T @ Qt, np.eye(Qt.shape[1]), atol=1e-11)
         # leading subspaces separated from the rest by a relative gap of 1e-3
         s = off.sigma[m]
         for j in range(1, Qt.shape[1]):
             if (s[j - 1] - s[j]) > 1e-3 * s[0]:
-                assert max_angle(Qt[:, :j], Qc[:, :j]) <= 1e-8, (m, j)
+                assert sin_angle(Qt[:, :j], Qc[:, :j]) <= 1e-10, (m, j)
     phi = torch.tensor(synth.phi_sin_cos(N), device="cuda")
     u_cc, _ = b_cc.solve(phi, tol=1e-12, max_iter=20000)
     u_tc, _ = b_tc.solve(phi, tol=1e-12, max_iter=20000)
