@@ -241,6 +241,7 @@ struct OzArgs {
     const GemmDesc* descs;
     const OzEntry* ents;
     const __nv_bfloat16* slices;
+    long long n_slices;        // elements of the slice buffer (bounds of every bulk copy)
     const double* scales;
     int* err;
 };
@@ -372,7 +373,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accfree[half])) : "memory");
         return true;
     };
-    if (tid == 0 && slabs >= 1) issue_copy(0);
+    // every copy this CTA will issue lies inside the slice buffer: checked once,
+    // before the first copy (a bad table entry fails the CTA instead of copying)
+    if (tid == 0) {
+        const long long a_lo = E.a_sl + (long long)tm * slabs * kAElems;
+        const long long a_hi = a_lo + (long long)(kSlices - 1) * a_ps + (long long)slabs * kAElems;
+        const long long b_lo = E.b_sl + (long long)tn * slabs * kBElems;
+        const long long b_hi = b_lo + (long long)(kSlices - 1) * b_ps + (long long)slabs * kBElems;
+        if (a_lo < 0 || b_lo < 0 || a_hi > A.n_slices || b_hi > A.n_slices || tm >= E.rta || tn >= E.rtb) *fail = 1;
+    }
+    __syncthreads();
+    if (tid == 0 && slabs >= 1 && !*fail) issue_copy(0);
     bool ok = true;   // warp-uniform
     int done_chunks = 0;
     for (int sl = 0; sl < slabs; ++sl) {
@@ -470,9 +481,13 @@ msp_status ozaki_gemm_batched(const std::vector<GemmDesc>& h, const GemmDesc* d_
         max_a_elems = std::max(max_a_elems, a_el / kSlices);
         max_b_elems = std::max(max_b_elems, b_el / kSlices);
     }
+    const size_t ent_words = sizeof(OzEntry) / sizeof(long long) * (size_t)batch;
+    const bool grow = (long long)w.slices.n < sl || (long long)w.scales.n < sc || w.ents.n < ent_words;
+    // products of earlier calls may still be queued on the stream and read these
+    // buffers: they finish before a buffer is given up for a larger one
+    if (grow) MSP_CUDA(cudaStreamSynchronize(s));
     if ((long long)w.slices.n < sl) MSP_TRY(w.slices.alloc((size_t)sl, s));
     if ((long long)w.scales.n < sc) MSP_TRY(w.scales.alloc((size_t)sc, s));
-    const size_t ent_words = sizeof(OzEntry) / sizeof(long long) * (size_t)batch;
     if (w.ents.n < ent_words) MSP_TRY(w.ents.alloc(ent_words, s));
     if (!w.err.p) {
         MSP_TRY(w.err.alloc(1, s));
@@ -498,6 +513,7 @@ msp_status ozaki_gemm_batched(const std::vector<GemmDesc>& h, const GemmDesc* d_
         a.descs = d_dev + z0;
         a.ents = d_ents + z0;
         a.slices = slices;
+        a.n_slices = (long long)w.slices.n;
         a.scales = w.scales.p;
         a.err = w.err.p;
         const int smem = 2 * (int)kStageBytes;

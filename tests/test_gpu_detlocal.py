@@ -85,7 +85,7 @@ def test_singular_value_decay_with_and_without_buffer(faces):
     out = {}
     for buffer in (10, 0):
         med = full_medium(buffer)
-        basis = med.extract(1e-13, "fp64")      # sigma() returns every singular value
+        basis = med.extract(1e-8, "fp64")       # sigma() returns every singular value, kept or not
         s = basis.sigma(PATCH)
         P = E.patch_boxes(N, synth.uniform_patches(N, 5, 5, buffer, 1))[PATCH]
         so = np.linalg.svd(E.full_green(aE, aN, P), compute_uv=False)
@@ -130,7 +130,9 @@ def test_global_full_basis_is_the_fine_solution_and_random_error_curve(faces):
     phi = synth.phi_sin_cos(N)
     u_ref = E.global_reference(aE, aN, N, phi)
     full = full_medium(10)
-    basis = full.extract(1e-13, "fp64")
+    # the full basis truncated at 1e-10: the directions below it are numerically
+    # null and would leave the normal matrix of the online system singular
+    basis = full.extract(1e-10, "fp64")
     u, _ = basis.solve(torch.tensor(phi, device="cuda"), tol=1e-12, max_iter=20000)
     assert rel(u.cpu().numpy(), u_ref) <= 1e-8
     errs = []
@@ -138,9 +140,9 @@ def test_global_full_basis_is_the_fine_solution_and_random_error_curve(faces):
         ps = synth.uniform_patches(N, 5, 5, 10, km)
         med = msp.Medium(synth.hou_wu(N, 2.0 ** -4), ps)
         med.sample(SEED, "fp64", tol=1e-13, max_iter=20000)
-        b = med.extract(1e-13, "fp64")
+        b = med.extract(1e-10, "fp64")
         u, _ = b.solve(torch.tensor(phi, device="cuda"), tol=1e-12, max_iter=20000)
-        off = E.offline(synth.hou_wu(N, 2.0 ** -4), ps, SEED, 1e-13)
+        off = E.offline(synth.hou_wu(N, 2.0 ** -4), ps, SEED, 1e-10)
         u_or, *_ = E.online(off, ps, N, phi)
         assert rel(u.cpu().numpy(), u_or) <= 1e-8, km
         errs.append(rel(u.cpu().numpy(), u_ref))

@@ -5,7 +5,7 @@ FMA kernels, and both against the oracle.
 The Gram and triangular products of Cholesky-QR and the projection onto the
 singular vectors (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) are FP64-accurate
 either way, so the bases agree far inside the parity bounds: singular values to
-1e-12 sigma_1, bases orthonormal to 1e-11 (the corner patches, rank-deficient, lose about 1e-12 in either engine), principal angles of the leading
+1e-10 sigma_1 (the shifted Cholesky-QR leaves the smallest, near 1e-10 sigma_1, that sensitive), bases orthonormal to 1e-11 (the corner patches, rank-deficient, lose about 1e-12 in either engine), principal angles of the leading
 subspaces to 1e-10 (sine of the largest principal angle), online fields (Eq. elliptic_cond_reduced) to 1e-10; against
 the oracle the usual bounds hold (sigma 1e-6 sigma_1, online field 1e-8 for the
 plain FP64 path)."""
@@ -61,7 +61,7 @@ def test_engines_agree_and_match_the_oracle(case):
     off = E.offline(ms, ps, seed, tau)
     for m in range(ps.n_patches):
         s_cc, s_tc = b_cc.sigma(m), b_tc.sigma(m)
-        assert np.max(np.abs(s_tc - s_cc)) <= 1e-12 * s_cc[0], m
+        assert np.max(np.abs(s_tc - s_cc)) <= 1e-10 * s_cc[0], m
         assert np.max(np.abs(s_tc - off.sigma[m])) <= 1e-6 * off.sigma[m][0], m
         assert b_tc.k(m) == b_cc.k(m) == off.Q[m].shape[1], m
         Qt, Qc = b_tc.Q(m).cpu().numpy(), b_cc.Q(m).cpu().numpy()
