@@ -6,7 +6,7 @@ The Gram and triangular products of Cholesky-QR and the projection onto the
 singular vectors (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) are FP64-accurate
 either way, so the bases agree far inside the parity bounds: singular values to
 1e-10 sigma_1 (the shifted Cholesky-QR leaves the smallest, near 1e-10 sigma_1, that sensitive), bases as orthonormal as the CUDA-core engine's, principal angles of the leading
-subspaces to 1e-11 sigma_1 / gap (sine of the largest principal angle), online fields (Eq. elliptic_cond_reduced) to 1e-10; against
+subspaces to 1e-11 sigma_1 / gap (sine of the largest principal angle), online fields (Eq. elliptic_cond_reduced) to 1e-9 (the CGLS stopping error); against
 the oracle the usual bounds hold (sigma 1e-6 sigma_1, online field 1e-8 for the
 plain FP64 path)."""
 import numpy as np
@@ -82,7 +82,7 @@ def test_engines_agree_and_match_the_oracle(case):
     phi = torch.tensor(synth.phi_sin_cos(N), device="cuda")
     u_cc, _ = b_cc.solve(phi, tol=1e-12, max_iter=20000)
     u_tc, _ = b_tc.solve(phi, tol=1e-12, max_iter=20000)
-    assert rel(u_tc.cpu().numpy(), u_cc.cpu().numpy()) <= 1e-10
+    assert rel(u_tc.cpu().numpy(), u_cc.cpu().numpy()) <= 1e-9     # each within the CGLS stopping error of the LS solution
     u_ref, *_ = E.online(off, ps, N, synth.phi_sin_cos(N))
     assert rel(u_tc.cpu().numpy(), u_ref) <= 1e-8
 
