@@ -78,7 +78,7 @@ struct DevBuf {
 // Work buffers of the tensor-core FP64 GEMM (ozaki_gemm.cu), grown on demand.
 struct OzakiWork {
     DevBuf<unsigned short> slices;   // BF16 slices of both operands of every product
-    DevBuf<double> scales;           // power-of-two row / column scales
+    DevBuf<int> scales;              // power-of-two scale exponents of the rows / columns
     DevBuf<long long> ents;          // per-product tables
     DevBuf<int> err;                 // set by a timed-out wait
 };

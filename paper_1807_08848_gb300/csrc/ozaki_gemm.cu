@@ -174,35 +174,48 @@ __device__ __forceinline__ double op_elem(const OpView& v, int r, int k) {
     return v.base[(long long)r * v.sr + (long long)k * v.sk];
 }
 
-// Per row: the scale 2^e with 2^(e-1) <= max|x| < 2^e (1 for an all-zero row).
-// One warp per row.
+// Per row: the scale 2^e with 2^(e-1) <= max|x| < 2^e (1 for an all-zero row),
+// stored as the exponent e.  The magnitude of an FP64 value orders like its bit
+// pattern with the sign cleared, so the maximum is an integer maximum (no FP64
+// arithmetic: the FP64 pipe is the narrow one on this part).  One warp per row.
 template <bool IS_B>
 __global__ void __launch_bounds__(256) oz_scale_kernel(const GemmDesc* descs, const OzEntry* ents, bool tA, bool tB,
-                                                       double* scales, int max_rows) {
+                                                       int* scale_exp, int max_rows) {
     const int z = blockIdx.y;
     const GemmDesc D = descs[z];
     const OpView v = IS_B ? view_b(D, tB) : view_a(D, tA);
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (r >= v.R || r >= max_rows) return;
-    double mx = 0.0;
-    for (int k = lane; k < v.K; k += 32) mx = fmax(mx, fabs(op_elem(v, r, k)));
+    unsigned long long mx = 0;
+    for (int k = lane; k < v.K; k += 32) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(op_elem(v, r, k)) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
     if (lane == 0) {
+        // mx = f 2^E with f in [1, 2) (normal) or a subnormal: scale exponent E + 1
         int e = 0;
-        if (mx > 0.0) {
-            frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): 2^(e-1) <= mx < 2^e
+        if (mx != 0) {
+            const int be = (int)(mx >> 52);
+            e = be > 0 ? be - 1023 + 1 : -1022;   // subnormals lie below 2^-1022
         }
-        scales[(IS_B ? ents[z].b_sc : ents[z].a_sc) + r] = mx > 0.0 ? ldexp(1.0, e) : 1.0;
+        scale_exp[(IS_B ? ents[z].b_sc : ents[z].a_sc) + r] = e;
     }
 }
 
 // Slices of every element of the tiled layout (one thread per element, all
-// slices): x = a / scale in (-1, 1); d_t = trunc(2^7 x), x = 2^7 x - d_t.
+// slices).  With the scale 2^e and |a| = m 2^(E-52) (m the 53-bit significand),
+// F = floor(|a| 2^(56-e)) = m shifted by E - e + 4 holds the 8 x 7 leading bits of
+// |a| / 2^e in (0, 1); slice t is bits 55-7t .. 49-7t of F with the sign of a --
+// the digits of the truncated base-128 expansion, found with integer operations.
 template <bool IS_B>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, const OzEntry* ents, bool tA, bool tB,
-                                                       const double* scales, __nv_bfloat16* out) {
+                                                       const int* scale_exp, __nv_bfloat16* out) {
     const int z = blockIdx.y;
     const GemmDesc D = descs[z];
     const OzEntry E = ents[z];
@@ -211,7 +224,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, co
     const int tiles = IS_B ? E.rtb : E.rta;
     const long long per_slice = (long long)tiles * E.slabs * RT * kSlabK;
     const long long base = IS_B ? E.b_sl : E.a_sl;
-    const double* sc = scales + (IS_B ? E.b_sc : E.a_sc);
+    const int* se = scale_exp + (IS_B ? E.b_sc : E.a_sc);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per_slice;
          e += (long long)gridDim.x * blockDim.x) {
         // e = [tile][slab][row group][k core][row][k]
@@ -224,14 +237,22 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, co
         const int slab = (int)(q % E.slabs);
         const int tile = (int)(q / E.slabs);
         const int r = tile * RT + rg * 8 + rr, k = slab * kSlabK + kc * 8 + kk;
-        double x = 0.0;
-        if (r < v.R && k < v.K) x = op_elem(v, r, k) / sc[r];
+        unsigned long long F = 0;
+        bool neg = false;
+        if (r < v.R && k < v.K) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(op_elem(v, r, k));
+            neg = (bits >> 63) != 0;
+            const int be = (int)((bits >> 52) & 0x7FF);
+            const unsigned long long frac = bits & 0xFFFFFFFFFFFFFull;
+            const unsigned long long m = be ? (frac | (1ull << 52)) : frac;   // significand
+            const int E2 = be ? be - 1023 : -1022;                             // |a| = m 2^(E2 - 52)
+            const int sh = E2 - se[r] + 4;                                     // F = m 2^sh
+            if (m != 0) F = sh >= 0 ? (sh < 8 ? m << sh : 0ull) : (sh > -64 ? m >> -sh : 0ull);
+        }
 #pragma unroll
         for (int t = 0; t < kSlices; ++t) {
-            const double y = x * (double)(1 << kBeta);
-            const double d = trunc(y);
-            x = y - d;
-            out[base + (long long)t * per_slice + e] = __float2bfloat16_rn((float)d);
+            const int d = (int)((F >> (kSlices * kBeta - kBeta * (t + 1))) & ((1u << kBeta) - 1u));
+            out[base + (long long)t * per_slice + e] = __float2bfloat16_rn((float)(neg ? -d : d));
         }
     }
 }
@@ -242,7 +263,7 @@ struct OzArgs {
     const OzEntry* ents;
     const __nv_bfloat16* slices;
     long long n_slices;        // elements of the slice buffer (bounds of every bulk copy)
-    const double* scales;
+    const int* scale_exp;      // power-of-two scale exponents of the rows / columns
     int* err;
 };
 
@@ -414,7 +435,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     if (!failed) {
         const int i = tm * kTM + (warp & 3) * 32 + lane;
         if (i < D.M) {
-            const double si = A.scales[E.a_sc + i];
+            const int ei = A.scale_exp[E.a_sc + i];
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const int j = tn * kTN + (warp >> 2) * 16 + c;
@@ -422,7 +443,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
                     double v = 0.0;
 #pragma unroll
                     for (int g = kDiag - 1; g >= 0; --g) v += ldexp((double)vacc[g][c], -kBeta * (g + 2));
-                    v *= si * A.scales[E.b_sc + j];
+                    v = ldexp(v, ei + A.scale_exp[E.b_sc + j]);
                     double* cp = D.C + (long long)j * D.ldc + i;
                     *cp = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*cp);
                 }
@@ -514,7 +535,7 @@ msp_status ozaki_gemm_batched(const std::vector<GemmDesc>& h, const GemmDesc* d_
         a.ents = d_ents + z0;
         a.slices = slices;
         a.n_slices = (long long)w.slices.n;
-        a.scales = w.scales.p;
+        a.scale_exp = w.scales.p;
         a.err = w.err.p;
         const int smem = 2 * (int)kStageBytes;
         MSP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
