@@ -14,7 +14,9 @@
 // After each chunk the accumulators are read out of tensor memory and added into
 // int32 registers (exact for K up to 16256), so
 //     C_ij = alpha sigma_i tau_j sum_g 2^(-kBeta g) V_g(i, j) + beta C_ij
-// is formed in FP64 once per element at the end.  Pairs with t + u > kSlices + 1
+// is formed once per element at the end: the diagonals are folded in integers
+// into two exactly representable halves, so an element costs a few FP64
+// operations (the FP64 pipe issues about two FMAs per clock and SM here).  Pairs with t + u > kSlices + 1
 // are dropped: with 8 slices of 7 bits each dropped or truncated term is below
 // about 2^-56 sigma_i tau_j, under the rounding of an FP64 product.
 //
@@ -225,17 +227,18 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, co
     const long long per_slice = (long long)tiles * E.slabs * RT * kSlabK;
     const long long base = IS_B ? E.b_sl : E.a_sl;
     const int* se = scale_exp + (IS_B ? E.b_sc : E.a_sc);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per_slice;
-         e += (long long)gridDim.x * blockDim.x) {
+    // per_slice < 2^31 (checked on the host): the tiled index fits 32 bits
+    const unsigned slabs_u = (unsigned)E.slabs;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)per_slice; e += gridDim.x * blockDim.x) {
         // e = [tile][slab][row group][k core][row][k]
         const int kk = (int)(e & 7);
         const int rr = (int)((e >> 3) & 7);
         const int kc = (int)((e >> 6) & 3);
-        long long q = e >> 8;
+        unsigned q = e >> 8;
         const int rg = (int)(q % (RT / 8));
         q /= (RT / 8);
-        const int slab = (int)(q % E.slabs);
-        const int tile = (int)(q / E.slabs);
+        const int slab = (int)(q % slabs_u);
+        const int tile = (int)(q / slabs_u);
         const int r = tile * RT + rg * 8 + rr, k = slab * kSlabK + kc * 8 + kk;
         unsigned long long F = 0;
         bool neg = false;
@@ -440,12 +443,27 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
             for (int c = 0; c < 16; ++c) {
                 const int j = tn * kTN + (warp >> 2) * 16 + c;
                 if (j < D.N) {
-                    double v = 0.0;
+                    // sum_g V_g 2^(-7(g+2)) = T_hi 2^-35 + T_lo 2^-63 with the diagonals folded
+                    // by Horner's rule in integers: T_hi from g = 0..3, T_lo from g = 4..7,
+                    // each below 2^53 in magnitude, so both convert to FP64 exactly and the
+                    // element costs two conversions and two FMAs of the FP64 pipe
+                    long long th = vacc[0][c], tl = vacc[4][c];
 #pragma unroll
-                    for (int g = kDiag - 1; g >= 0; --g) v += ldexp((double)vacc[g][c], -kBeta * (g + 2));
-                    v = ldexp(v, ei + A.scale_exp[E.b_sc + j]);
+                    for (int g = 1; g < 4; ++g) {
+                        th = th * (1LL << kBeta) + vacc[g][c];
+                        tl = tl * (1LL << kBeta) + vacc[g + 4][c];
+                    }
+                    const int ex = ei + A.scale_exp[E.b_sc + j];
+                    double v;
+                    if (ex - 63 > -1022 && ex - 35 < 1023) {   // both powers of two normal: build them
+                        const double ph = __longlong_as_double((long long)(ex - 35 + 1023) << 52);
+                        const double pl = __longlong_as_double((long long)(ex - 63 + 1023) << 52);
+                        v = fma((double)th, ph, (double)tl * pl);
+                    } else {
+                        v = ldexp((double)th, ex - 35) + ldexp((double)tl, ex - 63);
+                    }
                     double* cp = D.C + (long long)j * D.ldc + i;
-                    *cp = (D.beta == 0.0) ? D.alpha * v : D.alpha * v + D.beta * (*cp);
+                    *cp = (D.beta == 0.0) ? D.alpha * v : fma(D.alpha, v, D.beta * (*cp));
                 }
             }
         }
@@ -466,8 +484,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
 }  // namespace
 
 bool ozaki_gemm_supported(const std::vector<GemmDesc>& h) {
-    for (const GemmDesc& d : h)
+    for (const GemmDesc& d : h) {
         if (d.K > kOzMaxK) return false;
+        // one slice of either operand, tiled, must index with 32 bits
+        const long long ka = (long long)(d.K + kSlabK - 1) / kSlabK * kSlabK;
+        if ((long long)(d.M + kTM - 1) / kTM * kTM * ka >= (1LL << 31)) return false;
+        if ((long long)(d.N + kTN - 1) / kTN * kTN * ka >= (1LL << 31)) return false;
+    }
     return true;
 }
 
