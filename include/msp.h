@@ -302,6 +302,16 @@ typedef struct {
 } msp_basis_stats;
 msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out);
 
+/* Phase timing of msp_extract_basis (CUDA events on the caller's stream at the
+ * phase boundaries; off by default, process-wide switch): after an extraction made
+ * with timing on, msp_basis_extract_timing waits for its events and returns the
+ * milliseconds of ms_host[5] = Cholesky-QR, Jacobi SVD, truncation and projection,
+ * online operators, online factorisation (zeros if the basis was extracted with
+ * timing off or loaded from a file), and optionally the algorithmic FP64 work of
+ * the Jacobi SVD (22 c flop per column pair and sweep, summed over the patches). */
+msp_status msp_set_extract_timing(int enable);
+msp_status msp_basis_extract_timing(msp_basis b, double* ms_host, double* jacobi_flop_host);
+
 /* Preconditioner of the online least-squares iteration (the iteration itself,
  * its residuals and iterates are FP64 in every case):
  *   MSP_PRECOND_BLOCK_ROWS (default): block-tridiagonal Cholesky of the scaled

@@ -21,7 +21,7 @@ from . import _native as N
 from ._native import MspError, MSP_FP64, MSP_MIXED
 
 __all__ = ["Medium", "Basis", "Server", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
-           "precision_code", "set_wait_limit", "set_gemm_engine"]
+           "precision_code", "set_wait_limit", "set_gemm_engine", "set_extract_timing"]
 
 
 def load_library():
@@ -32,6 +32,11 @@ def set_wait_limit(polls: int = 0):
     """Poll bound of the device-side grid barriers (msp_set_wait_limit); 0 restores
     the default."""
     N.check(N.load().msp_set_wait_limit(int(polls)))
+
+
+def set_extract_timing(enable: bool = True):
+    """CUDA-event timing of the extraction's phases (msp_set_extract_timing)."""
+    N.check(N.load().msp_set_extract_timing(1 if enable else 0))
 
 
 def set_gemm_engine(engine: str = "tensor_cores"):
@@ -262,6 +267,15 @@ class Basis:
     @property
     def handle(self):
         return self._h
+
+    def extract_timing(self) -> dict:
+        """Milliseconds per phase of the extraction that built this basis (timing on
+        through set_extract_timing) and the Jacobi SVD's algorithmic FP64 flop."""
+        ms = (C.c_double * 5)()
+        jf = C.c_double()
+        N.check(N.load().msp_basis_extract_timing(self._h, ms, C.byref(jf)))
+        names = ("cholqr", "jacobi", "projection", "online_operators", "online_factor")
+        return {**{n: ms[i] for i, n in enumerate(names)}, "jacobi_flop": jf.value}
 
     def stats(self) -> dict:
         st = N.BasisStats()

@@ -101,6 +101,8 @@ SIGNATURES = {
     "msp_get_basis": (_i, [_vp, _i, _vp, _vp]),
     "msp_online_counts": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
     "msp_basis_get_stats": (_i, [_vp, C.POINTER(BasisStats)]),
+    "msp_set_extract_timing": (_i, [_i]),
+    "msp_basis_extract_timing": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
     "msp_basis_set_preconditioner": (_i, [_vp, _i]),
     "msp_kinetic_build": (_i, [_i, _d, _i, _i, _i, _i, _vp, C.POINTER(_vp)]),
     "msp_kinetic_destroy": (None, [_vp]),

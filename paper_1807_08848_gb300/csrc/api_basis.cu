@@ -56,6 +56,32 @@ extern "C" msp_status msp_online_counts(msp_basis b, int* n_unknowns, int* n_row
     return MSP_OK;
 }
 
+extern "C" msp_status msp_basis_extract_timing(msp_basis b, double* ms_host, double* jacobi_flop_host) {
+    clear_error();
+    MSP_CHECK_ARG(b && ms_host, "msp_basis_extract_timing: NULL argument");
+    const Basis& B = b->B;
+    for (int p = 0; p < 5; ++p) ms_host[p] = 0.0;
+    if (B.ext_ev.size() == 6) {
+        MSP_CUDA(cudaEventSynchronize(B.ext_ev[5]));
+        for (int p = 0; p < 5; ++p) {
+            float t = 0.f;
+            MSP_CUDA(cudaEventElapsedTime(&t, B.ext_ev[p], B.ext_ev[p + 1]));
+            ms_host[p] = t;
+        }
+    }
+    if (jacobi_flop_host) {
+        // per column pair and sweep: three inner products (3c multiply-adds) and the
+        // rotation of the pair's columns of W and of V (4c + 4c): 22c flop
+        double f = 0.0;
+        for (size_t m = 0; m < B.jac_cols.size() && m < B.jac_sweeps.size(); ++m) {
+            const double c = B.jac_cols[m];
+            f += (double)B.jac_sweeps[m] * 0.5 * c * (c - 1.0) * 22.0 * c;
+        }
+        *jacobi_flop_host = f;
+    }
+    return MSP_OK;
+}
+
 extern "C" msp_status msp_online_solve(msp_basis b, const double* phi, int batch, double tol, int max_iter, double* u,
                                        double* c_dev, int* iters_host, void* stream) {
     clear_error();

@@ -19,6 +19,17 @@ constexpr long long kDefaultWaitLimit = 1LL << 24;
 static std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
 long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
+static std::atomic<int> g_extract_timing{0};
+bool extract_timing() { return g_extract_timing.load(std::memory_order_relaxed) != 0; }
+msp_status phase_mark(std::vector<cudaEvent_t>* marks, cudaStream_t s) {
+    if (!marks || !extract_timing()) return MSP_OK;
+    cudaEvent_t e;
+    MSP_CUDA(cudaEventCreate(&e));
+    marks->push_back(e);
+    MSP_CUDA(cudaEventRecord(e, s));
+    return MSP_OK;
+}
+
 // Engine of the FP64 products of the extraction and the online factorisation.
 static std::atomic<int> g_gemm_engine{0};
 int fp64_gemm_engine() { return g_gemm_engine.load(std::memory_order_relaxed); }
@@ -60,6 +71,12 @@ extern "C" msp_status msp_set_gemm_engine(int engine) {
     clear_error();
     MSP_CHECK_ARG(engine == MSP_GEMM_TENSOR_CORES || engine == MSP_GEMM_CUDA_CORES, "msp_set_gemm_engine: unknown engine");
     g_gemm_engine.store(engine, std::memory_order_relaxed);
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_set_extract_timing(int enable) {
+    clear_error();
+    g_extract_timing.store(enable != 0 ? 1 : 0, std::memory_order_relaxed);
     return MSP_OK;
 }
 

@@ -430,10 +430,11 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
                      const std::vector<int>& n_rows, const std::vector<int>& cols, double tau, cudaStream_t s,
                      DevBuf<double>& Q, std::vector<int>& k, std::vector<double>& sigma,
                      std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries,
-                     float* mean_sweeps) {
+                     float* mean_sweeps, std::vector<cudaEvent_t>* marks, std::vector<int>* sweeps_out) {
     const int np = (int)cols.size();
     max_sweeps = 0;
     max_tries = 0;
+    MSP_TRY(phase_mark(marks, s));
     // ---- small-matrix layout
     std::vector<SmallMat> mats(np);
     std::vector<long long> sig_off(np);
@@ -534,6 +535,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         }
         X = Y;
     }
+    MSP_TRY(phase_mark(marks, s));
     // ---- SVD of the triangular factor
     MSP_TRY(W.alloc(mo, s));
     MSP_TRY(V.alloc(mo, s));
@@ -567,6 +569,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         jacobi_svd_kernel<<<np, 512, sm64, s>>>(d_by_size.p, W.p, V.p, 40, maxc * 1.12e-16, small_rel, c64, sweeps.p);
         count_launches(1);
         MSP_CUDA(cudaGetLastError());
+        MSP_TRY(phase_mark(marks, s));
     }
     sort_truncate_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, tau, sig_tmp.p, sig.p, d_sig_off.p, order.p, kdev.p);
     count_launches(1);
@@ -579,6 +582,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         MSP_CUDA(cudaMemcpyAsync(sw.data(), sweeps.p, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
         for (int v : sw) max_sweeps = std::max(max_sweeps, v);
+        if (sweeps_out) *sweeps_out = sw;
         if (mean_sweeps) {
             double t = 0.0;
             for (int v : sw) t += v;
@@ -607,6 +611,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
                          mats[m].n, mats[m].c, mats[m].n, 1.0, 0.0};
     }
     MSP_TRY(run_gemm(false, maxn, std::max(maxk, 1)));
+    MSP_TRY(phase_mark(marks, s));
     return MSP_OK;
 }
 
@@ -624,7 +629,8 @@ msp_status build_basis(Medium& M, double tau, int precision, cudaStream_t s, Bas
             cols[m] = M.patches[m].cols;
         }
         MSP_TRY(svd_bases(M.snaps.p, M.snap_elems, snap_off, n_rows, cols, tau, s, B.Q, B.k, B.sigma, B.sigma_off, B.q_off,
-                          B.max_jacobi_sweeps, B.max_cholqr_tries, &B.mean_jacobi_sweeps));
+                          B.max_jacobi_sweeps, B.max_cholqr_tries, &B.mean_jacobi_sweeps, &B.ext_ev, &B.jac_sweeps));
+        B.jac_cols.assign(cols.begin(), cols.end());
     }
     return finish_basis(B, M.aE.p, M.aN.p, s);
 }
@@ -779,7 +785,9 @@ msp_status finish_basis(Basis& B, const double* aE_dev, const double* aN_dev, cu
             return MSP_ERR_BREAKDOWN;
         }
     // ---- block-tridiagonal factor of the scaled normal matrix (online preconditioner)
+    MSP_TRY(phase_mark(B.ext_ev.empty() ? nullptr : &B.ext_ev, s));
     MSP_TRY(build_online_factor(B, row_ptr, row_slot, s));
+    MSP_TRY(phase_mark(B.ext_ev.empty() ? nullptr : &B.ext_ev, s));
     return MSP_OK;
 }
 

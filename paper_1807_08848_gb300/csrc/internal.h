@@ -240,6 +240,15 @@ struct Basis {
     BtStore<double> bt64;
     DevBuf<double> w_s;                 // normal-equation residual s = P^T r
     bool use_block_jacobi = false;      // online preconditioner: patch blocks only
+    // CUDA events at the phase boundaries of the extraction that built this basis
+    // (when extraction timing is on): Cholesky-QR | Jacobi SVD | truncation and
+    // projection | online operators | online factor
+    std::vector<cudaEvent_t> ext_ev;
+    std::vector<double> jac_cols;       // per patch: snapshot columns (Jacobi work)
+    std::vector<int> jac_sweeps;        // per patch: Jacobi sweeps
+    ~Basis() {
+        for (cudaEvent_t e : ext_ev) cudaEventDestroy(e);
+    }
     int max_jacobi_sweeps = 0, max_cholqr_tries = 0;
     float mean_jacobi_sweeps = 0.f;
     int device = 0;
@@ -308,6 +317,10 @@ msp_status apply_online_factor(Basis& B, const double* s_in, double* z_out, int 
 int num_sms();
 // Poll bound of the device-side grid barriers (msp_set_wait_limit).
 long long wait_limit();
+// Extraction phase timing on (msp_set_extract_timing); records an event on s
+// into marks when it is on and marks is not null.
+bool extract_timing();
+msp_status phase_mark(std::vector<cudaEvent_t>* marks, cudaStream_t s);
 
 // Count of kernel launches issued by the library (for launch accounting).
 void count_launches(long long n);

@@ -74,7 +74,8 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
                      const std::vector<int>& n_rows, const std::vector<int>& cols, double tau, cudaStream_t s,
                      DevBuf<double>& Q, std::vector<int>& k, std::vector<double>& sigma,
                      std::vector<long long>& sigma_off, std::vector<long long>& q_off, int& max_sweeps, int& max_tries,
-                     float* mean_sweeps = nullptr);
+                     float* mean_sweeps = nullptr, std::vector<cudaEvent_t>* marks = nullptr,
+                     std::vector<int>* sweeps_out = nullptr);
 
 namespace {
 
