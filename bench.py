@@ -288,6 +288,8 @@ def run_profile_case(args):
     ms = synth.lognormal(N, 2.0 ** -5, 64, 11)
     ps = synth.uniform_patches(N, 8, 8, 16, 128)
     med = msp.Medium(ms, ps)
+    if args.precision == "mixed" and args.local_solver == "direct":
+        med.set_launch("mixed", "direct")
     st = med.sample(1, args.precision, tol=1e-10, max_iter=20000)
     basis = med.extract(1e-6, args.precision)
     from paper_1807_08848_gb300 import _native
