@@ -1,16 +1,21 @@
 """Kinetic example (Sec. 4): plain FP64 restatement, discrete ordinates.
 
-Problem (Eq. RTE with isotropic scattering, i.e. the Henyey-Greenstein kernel
-of Eq. HG at g = 0, k = 1/2):
+Problem (Eq. RTE with the Henyey-Greenstein kernel of Eq. HG):
 
-    v d_x f(x, v) = (1/eps) (rho(x) - f(x, v)),   rho = (1/2) int_{-1}^{1} f dv',
+    v d_x f(x, v) = (1/eps) L f,
+    L f(v) = int k(v, v') f(v') dv' - (int k(v', v) dv') f(v),
+    k(v, v') = (1/2) (1 - g^2) / (1 + g^2 + 2 g v v'),
     x in [0, 1], incoming data on Gamma_-: f(0, v>0) and f(1, v<0).
+At g = 0, k = 1/2 and L f = rho - f with rho = (1/2) int f dv' (isotropic
+scattering, the default throughout).
 
 Discretisation (reading R11; the paper's own test uses a uniform velocity grid,
 Sec. 4.3): nodes x_i = i dx, dx = 1/N; n_v Gauss-Legendre velocities v_l with
-weights w_l (sum w = 2), rho_i = (1/2) sum_l w_l f_{i,l}; implicit upwind
-    v_l > 0:  v_l (f_i - f_{i-1}) / dx = (rho_i - f_i) / eps,  i = X0+1 .. X1
-    v_l < 0:  v_l (f_{i+1} - f_i) / dx = (rho_i - f_i) / eps,  i = X0 .. X1-1
+weights w_l (sum w = 2); the collision by the same quadrature,
+    (L f)_l = sum_l' w_l' k(v_l, v_l') f_l' - sigma_l f_l,  sigma_l = sum_l' w_l' k(v_l', v_l),
+(at g = 0: rho - f with rho = (1/2) sum_l w_l f_l); implicit upwind
+    v_l > 0:  v_l (f_i - f_{i-1}) / dx = (L f_i)_l / eps,  i = X0+1 .. X1
+    v_l < 0:  v_l (f_{i+1} - f_i) / dx = (L f_i)_l / eps,  i = X0 .. X1-1
 on a node range [X0, X1] with f_{X0, v>0} and f_{X1, v<0} given.
 
 Method (Algorithm alg:summary with RanLocalSolu, Sec. 4.2):
@@ -66,7 +71,18 @@ def patches(n_cells, n_patches, buffer, samples):
     return out
 
 
-def range_operator(n_cells, eps, n_v, X0, X1):
+def scattering(n_v, g=0.0):
+    """Quadrature form of the Henyey-Greenstein collision (Eq. HG): the matrix
+    Kw[l, l'] = w_l' k(v_l, v_l') and the loss rates sigma_l = sum_l' w_l' k(v_l', v_l),
+    with k(v, v') = (1/2)(1 - g^2) / (1 + g^2 + 2 g v v')."""
+    v, w = velocities(n_v)
+    k = 0.5 * (1.0 - g * g) / (1.0 + g * g + 2.0 * g * np.outer(v, v))
+    Kw = k * w[None, :]
+    sigma = (w[:, None] * k).sum(axis=0)
+    return Kw, sigma
+
+
+def range_operator(n_cells, eps, n_v, X0, X1, g=0.0):
     """Sparse system for the unknowns of node range [X0, X1] and the map from the
     incoming data.  Unknown ordering: node-major, velocity fastest, over the
     (node, velocity) pairs that are not incoming data; incoming data ordering:
@@ -74,6 +90,7 @@ def range_operator(n_cells, eps, n_v, X0, X1):
     velocities at X1 (ascending v).  Returns (A, Bin, unknown_index, data_index)
     with A u = Bin g, and the (node, velocity) -> index tables."""
     v, w = velocities(n_v)
+    Kw, sigma = scattering(n_v, g)
     dx = 1.0 / n_cells
     pos = np.nonzero(v > 0)[0]
     neg = np.nonzero(v < 0)[0]
@@ -97,33 +114,34 @@ def range_operator(n_cells, eps, n_v, X0, X1):
             brows.append(r); bcols.append(didx[key]); bvals.append(-val)
 
     for (i, l), r in uidx.items():
-        # v_l (f_i - f_nbr)/dx + f_i/eps - rho_i/eps = 0 with the upwind neighbour
+        # v_l (f_i - f_nbr)/dx + sigma_l f_i/eps - sum_l' Kw[l, l'] f_{i,l'}/eps = 0 with the
+        # upwind neighbour
         nb = i - 1 if v[l] > 0 else i + 1
         a = abs(v[l]) / dx
-        add(r, (i, l), a + 1.0 / eps)
+        add(r, (i, l), a + sigma[l] / eps)
         add(r, (nb, l), -a)
         for ll in range(n_v):
-            add(r, (i, ll), -0.5 * w[ll] / eps)
+            add(r, (i, ll), -Kw[l, ll] / eps)
     n = len(uidx)
     A = sp.csc_matrix((vals, (rows, cols)), shape=(n, n))
     Bin = sp.csc_matrix((bvals, (brows, bcols)), shape=(n, len(didx)))
     return A, Bin, uidx, didx
 
 
-def range_solve(n_cells, eps, n_v, X0, X1, data):
+def range_solve(n_cells, eps, n_v, X0, X1, data, g=0.0):
     """Solve on [X0, X1] for incoming data (n_v,) or (n_v, S); returns the full
-    field, shape (X1-X0+1, n_v[, S])."""
-    g = np.asarray(data, dtype=np.float64)
-    vec = g.ndim == 1
+    field, shape (X1-X0+1, n_v[, S]).  g: anisotropy of Eq. HG."""
+    d = np.asarray(data, dtype=np.float64)
+    vec = d.ndim == 1
     if vec:
-        g = g[:, None]
-    A, Bin, uidx, didx = range_operator(n_cells, eps, n_v, X0, X1)
-    sol = spla.splu(A).solve(np.ascontiguousarray((Bin @ g)))
-    F = np.zeros((X1 - X0 + 1, n_v, g.shape[1]))
+        d = d[:, None]
+    A, Bin, uidx, didx = range_operator(n_cells, eps, n_v, X0, X1, g)
+    sol = spla.splu(A).solve(np.ascontiguousarray((Bin @ d)))
+    F = np.zeros((X1 - X0 + 1, n_v, d.shape[1]))
     for (i, l), r in uidx.items():
         F[i - X0, l] = sol[r]
     for (i, l), t in didx.items():
-        F[i - X0, l] = g[t]
+        F[i - X0, l] = d[t]
     return F[..., 0] if vec else F
 
 
@@ -132,9 +150,9 @@ def sample_matrix(seed, patch, n_v):
     return philox.normals(seed, patch.m, n_v, patch.S, philox.TAG_KINETIC)
 
 
-def snapshots(n_cells, eps, n_v, patch, seed):
+def snapshots(n_cells, eps, n_v, patch, seed, g=0.0):
     """Restricted local solutions: (n_nodes n_v, S), node-major, velocity fastest."""
-    F = range_solve(n_cells, eps, n_v, patch.X0, patch.X1, sample_matrix(seed, patch, n_v))
+    F = range_solve(n_cells, eps, n_v, patch.X0, patch.X1, sample_matrix(seed, patch, n_v), g)
     sub = F[patch.x0 - patch.X0:patch.x1 - patch.X0 + 1]
     return sub.reshape(patch.n_nodes * n_v, -1)
 
@@ -197,11 +215,11 @@ class KOffline:
     sigma: list
 
 
-def offline(n_cells, eps, n_v, n_patches, buffer, samples, seed, tau):
+def offline(n_cells, eps, n_v, n_patches, buffer, samples, seed, tau, g=0.0):
     pts = patches(n_cells, n_patches, buffer, samples)
     R, Q, S = [], [], []
     for P in pts:
-        r = snapshots(n_cells, eps, n_v, P, seed)
+        r = snapshots(n_cells, eps, n_v, P, seed, g)
         q, s = basis(r, tau)
         R.append(r); Q.append(q); S.append(s)
     return KOffline(pts, R, Q, S)
@@ -213,8 +231,16 @@ def online(off: KOffline, n_cells, n_v, inflow_left, inflow_right):
     return reconstruct(off.patches, off.Q, c, o, n_cells, n_v, inflow_left, inflow_right), c
 
 
-def global_reference(n_cells, eps, n_v, inflow_left, inflow_right):
+def global_reference(n_cells, eps, n_v, inflow_left, inflow_right, g=0.0):
     """Direct solve of the whole slab with the incoming data."""
     v, _ = velocities(n_v)
-    g = np.concatenate([inflow_left[v > 0], inflow_right[v < 0]])
-    return range_solve(n_cells, eps, n_v, 0, n_cells, g)
+    d = np.concatenate([inflow_left[v > 0], inflow_right[v < 0]])
+    return range_solve(n_cells, eps, n_v, 0, n_cells, d, g)
+
+
+def full_green(n_cells, eps, n_v, patch, g=0.0):
+    """Restricted Green's matrix of the buffered patch (DetLocalSolu for the slab:
+    one unit datum per incoming component), (n_nodes n_v, n_v)."""
+    F = range_solve(n_cells, eps, n_v, patch.X0, patch.X1, np.eye(n_v), g)
+    sub = F[patch.x0 - patch.X0:patch.x1 - patch.X0 + 1]
+    return sub.reshape(patch.n_nodes * n_v, -1)
