@@ -647,9 +647,35 @@ def run_stencil(args):
     print(json.dumps(out), flush=True)
 
 
+def kinetic_direct_rates(msp, torch, kw, stream, g, precision, reps=2):
+    """The kinetic slab's local solves by the direct block solver: the first call
+    (factorisation + solve) and the steady state (factor reused), CUDA events."""
+    km = msp.KineticMedium(kw["n_cells"], kw["eps"], kw["n_v"], kw["n_patches"], kw["buffer"], kw["samples"], g=g)
+    km.set_solver("direct")
+    out = {"g": g}
+    for r in range(1 + reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = km.sample(kw["seed"], tol=1e-13, max_iter=16, precision=precision)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if r == 0:
+            out["first_call_ms"] = ms
+        else:
+            out["ms"] = min(out.get("ms", ms), ms)
+        out["passes_max"] = int(st.max_iters)
+    out["solves_per_s"] = int(st.n_solves) / (out["ms"] / 1e3)
+    out["factor_ms"] = out["first_call_ms"] - out["ms"]
+    del km
+    return out
+
+
 def run_kinetic(args):
     """The kinetic slab workload alone (8192 cells, 64 GL velocities, 64 patches x 96
-    samples): one sample pass per precision, CUDA-event times, for profiler captures."""
+    samples): one sample pass per precision and solver, CUDA-event times, for
+    profiler captures; the direct solver also with the Henyey-Greenstein
+    collision at g = 1/2."""
     import torch
     import paper_1807_08848_gb300 as msp
     torch.cuda.set_device(0)
@@ -665,6 +691,10 @@ def run_kinetic(args):
         torch.cuda.synchronize()
         out[kp] = {"ms": e0.elapsed_time(e1), "solves": int(st.n_solves),
                    "sweeps_per_solve": st.total_iters / max(1, int(st.n_solves))}
+        del km
+    for g in (0.0, 0.5):
+        for kp in ("mixed", "fp64"):
+            out[f"direct_g{g}_{kp}"] = kinetic_direct_rates(msp, torch, kw, stream, g, kp)
     print(json.dumps(out), flush=True)
 
 
@@ -994,6 +1024,10 @@ def run_ours(args, rank, world):
             kinetic[kp] = {"solves_per_s": int(kst.n_solves) / kt, "ms": kt * 1e3,
                            "sweeps_per_solve": kst.total_iters / max(1, int(kst.n_solves))}
             del km
+        # the direct block solver (isotropic, and the Henyey-Greenstein collision at g = 1/2)
+        for g in (0.0, 0.5):
+            for kp in ("mixed", "fp64"):
+                kinetic[f"direct_g{g}_{kp}"] = kinetic_direct_rates(msp, torch, kw, stream, g, kp, reps=1)
 
     # ---- the plain FP64 path's local solves on the same medium, for comparison
     fp64_rate = None

@@ -547,9 +547,33 @@ void msp_server_destroy(msp_server s);
  * cells (clipped); `samples` random incoming data sets per patch.  Snapshot
  * rows are node-major with the velocity fastest ((W+1) n_v rows).
  * INVALID_ARG unless N is a multiple of n_patches, n_v is even in 2..256,
- * eps > 0. */
+ * eps > 0.  Same as msp_kinetic_build_hg with g = 0. */
 msp_status msp_kinetic_build(int n_cells, double eps, int n_v, int n_patches, int buffer, int samples,
                              void* stream, msp_kmedium* out);
+
+/* The slab with the Henyey-Greenstein collision of Eq. HG (Sec. 4):
+ *     v d_x f = (1/eps) [ int k(v, v') f(v') dv' - (int k(v', v) dv') f(v) ],
+ *     k(v, v') = (1/2) (1 - g^2) / (1 + g^2 + 2 g v v'),
+ * both integrals by the Gauss-Legendre rule.  g in (-1, 1) (INVALID_ARG
+ * otherwise); g != 0 needs n_v <= 128 and selects the direct solver
+ * (msp_kinetic_set_solver).  Everything else as msp_kinetic_build. */
+msp_status msp_kinetic_build_hg(int n_cells, double eps, double g, int n_v, int n_patches, int buffer, int samples,
+                                void* stream, msp_kmedium* out);
+
+/* Local solver of msp_kinetic_sample.
+ * MSP_KINETIC_SOURCE_ITERATION (default at g = 0; g = 0 only): transport sweeps
+ *   with the lagged density, as described at msp_kinetic_sample.
+ * MSP_KINETIC_DIRECT (default at g != 0; n_v <= 128): block LU of the upwind
+ *   operator over the nodes of each buffered patch (the inverse of every
+ *   n_v x n_v Schur complement kept; factorised at the first sample call of
+ *   each precision and reused), FP64 residual refinement: precision MSP_FP64
+ *   factors in FP64, MSP_MIXED in FP32; stops when max_l |r_l| / D_ll <=
+ *   tol max |f| (r the FP64 residual, D the operator's diagonal) after at most
+ *   min(max_iter, 16) corrections; iterations in the stats count corrections.
+ * INVALID_ARG for another value or a solver the medium cannot take. */
+#define MSP_KINETIC_SOURCE_ITERATION 0
+#define MSP_KINETIC_DIRECT 1
+msp_status msp_kinetic_set_solver(msp_kmedium k, int solver);
 void msp_kinetic_destroy(msp_kmedium k);
 /* Gauss-Legendre velocities and weights (host arrays of n_v, either may be NULL). */
 msp_status msp_kinetic_velocities(msp_kmedium k, double* v_host, double* w_host);

@@ -442,17 +442,27 @@ class Server:
             pass
 
 
-class KineticMedium:
-    """Slab radiative transfer (isotropic scattering, discrete ordinates)."""
+KINETIC_SOLVERS = {"source_iteration": 0, "direct": 1}
 
-    def __init__(self, n_cells: int, eps: float, n_v: int, n_patches: int, buffer: int, samples: int, stream=None):
+
+class KineticMedium:
+    """Slab radiative transfer, discrete ordinates, with the Henyey-Greenstein
+    collision of anisotropy g (g = 0: isotropic scattering)."""
+
+    def __init__(self, n_cells: int, eps: float, n_v: int, n_patches: int, buffer: int, samples: int, stream=None,
+                 g: float = 0.0):
         h = C.c_void_p()
-        N.check(N.load().msp_kinetic_build(n_cells, eps, n_v, n_patches, buffer, samples, _stream_ptr(stream),
-                                           C.byref(h)))
+        N.check(N.load().msp_kinetic_build_hg(n_cells, eps, float(g), n_v, n_patches, buffer, samples,
+                                              _stream_ptr(stream), C.byref(h)))
         self._h = h
         self.n_cells, self.eps, self.n_v, self.n_patches, self.buffer, self.samples = (
             n_cells, eps, n_v, n_patches, buffer, samples)
+        self.g = float(g)
         self.n_k = (n_cells // n_patches + 1) * n_v
+
+    def set_solver(self, solver: str):
+        """"source_iteration" (isotropic only) or "direct" (msp_kinetic_set_solver)."""
+        N.check(N.load().msp_kinetic_set_solver(self._h, KINETIC_SOLVERS[solver]))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -471,25 +481,6 @@ class KineticMedium:
         N.check(N.load().msp_kinetic_sample(self._h, C.c_uint64(seed), precision_code(precision), tol, max_iter,
                                             _stream_ptr(stream), C.byref(st) if stats else None))
         return st if stats else None
-
-    def sample_patches(self, patches, seed: int, precision="fp64", tol: float = 1e-12, max_iter: int = 20000,
-                       stream=None):
-        """Local solves of the listed patches only (msp_sample_patch_list)."""
-        lst = np.ascontiguousarray(np.asarray(patches, dtype=np.int32).ravel())
-        st = N.SolveStats()
-        N.check(N.load().msp_sample_patch_list(self._h, _i32p(lst), int(lst.size), C.c_uint64(seed),
-                                               precision_code(precision), tol, max_iter, _stream_ptr(stream),
-                                               C.byref(st)))
-        return st
-
-    def set_snapshots(self, m: int, block: torch.Tensor, stream=None):
-        """Write patch m's snapshot block, an (n_k, cols) tensor as snapshots()
-        returns it (stored column-major)."""
-        info = self.patch(m)
-        assert tuple(block.shape) == (info.n_k, info.cols)
-        t = block.to(dtype=torch.float64, device="cuda").T.contiguous()     # (cols, n_k) row-major
-        N.check(N.load().msp_set_snapshots(self._h, m, _dptr(t), _stream_ptr(stream)))
-        (stream or torch.cuda.current_stream()).synchronize()
 
     def snapshots(self, m: int, stream=None) -> torch.Tensor:
         t = torch.empty((self.samples, self.n_k), dtype=torch.float64, device="cuda")

@@ -105,6 +105,8 @@ SIGNATURES = {
     "msp_basis_extract_timing": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
     "msp_basis_set_preconditioner": (_i, [_vp, _i]),
     "msp_kinetic_build": (_i, [_i, _d, _i, _i, _i, _i, _vp, C.POINTER(_vp)]),
+    "msp_kinetic_build_hg": (_i, [_i, _d, _d, _i, _i, _i, _i, _vp, C.POINTER(_vp)]),
+    "msp_kinetic_set_solver": (_i, [_vp, _i]),
     "msp_kinetic_destroy": (None, [_vp]),
     "msp_kinetic_velocities": (_i, [_vp, C.POINTER(_d), C.POINTER(_d)]),
     "msp_kinetic_sample": (_i, [_vp, _u64, _i, _d, _i, _vp, C.POINTER(SolveStats)]),

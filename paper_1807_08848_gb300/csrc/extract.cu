@@ -406,13 +406,6 @@ __global__ void precond_inverse_kernel(const SmallMat* mats, const double* Fi, c
     }
 }
 
-template <class T>
-msp_status upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
-    MSP_TRY(d.alloc(std::max<size_t>(1, h.size()), s));
-    if (!h.empty()) MSP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
-    return MSP_OK;
-}
-
 int domain_ring_pos(int N, int i, int j) {
     if (j == 0 && i < N) return i;
     if (i == N && j < N) return N + j;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -74,6 +75,15 @@ struct DevBuf {
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
 };
+
+// Stream-ordered copy of a host vector into a (re)allocated device buffer (at
+// least one element, so that the pointer is valid for empty tables).
+template <class T>
+msp_status upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+    MSP_TRY(d.alloc(std::max<size_t>(1, h.size()), s));
+    if (!h.empty()) MSP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+    return MSP_OK;
+}
 
 // Work buffers of the tensor-core FP64 GEMM (ozaki_gemm.cu), grown on demand.
 struct OzakiWork {

@@ -1,42 +1,26 @@
-// Kinetic example (Sec. 4): slab radiative transfer with isotropic scattering
-// (Eq. RTE, Henyey-Greenstein kernel Eq. HG at g = 0), discrete ordinates.
+// Kinetic example (Sec. 4): slab radiative transfer (Eq. RTE) with the
+// Henyey-Greenstein collision (Eq. HG), discrete ordinates.
 //
-//   v d_x f = (1/eps)(rho - f),  rho = (1/2) sum_l w_l f_l  (Gauss-Legendre v_l, w_l)
+//   v d_x f = (1/eps) L f,  (L f)_l = sum_l' w_l' k(v_l, v_l') f_l' - sigma_l f_l
+//   (Gauss-Legendre v_l, w_l; at g = 0: L f = rho - f, rho = (1/2) sum_l w_l f_l)
 //   implicit upwind on nodes x_i = i/N;  incoming data f(0, v>0), f(1, v<0).
 //
 // Offline (Eq. rte_random): per patch and sample, i.i.d. N(0,1) incoming data on the
-// buffered patch, solved by source iteration -- a transport sweep of every
-// velocity with the lagged density, then the density update -- restricted to K_m.
+// buffered patch, restricted to K_m.  Isotropic media default to source iteration
+// -- a transport sweep of every velocity with the lagged density, then the density
+// update; anisotropic ones use the direct block solver of kinetic_direct.cu.
 // Extraction: the shared SVD-basis routine.  Online (Eq. rte_cond_reduced): all
 // velocity components continuous at every interface plus the incoming data, least
 // squares by the normal equations, which are block tridiagonal along the chain of
 // patches: factorised once (FP64 block Cholesky), solved per data set with two
 // corrected-semi-normal-equation refinement steps.
-#include "internal.h"
+#include "kinetic_internal.h"
 #include "device_util.cuh"
 
 #include <algorithm>
 #include <cmath>
 
 namespace msp {
-
-struct KPatchDev {
-    int x0, x1, X0, X1, nn, n_k;
-    long long snap_offset;
-};
-
-struct KMedium {
-    int N = 0, n_v = 0, M = 0, buffer = 0, S = 0;
-    double eps = 0;
-    std::vector<double> v, w;
-    std::vector<KPatchDev> patches;
-    DevBuf<double> d_v, d_w;
-    DevBuf<KPatchDev> d_patches;
-    DevBuf<double> snaps;
-    long long snap_elems = 0;
-    DevBuf<int> stats;    // per (patch, sample): iterations, flag
-    bool sampled = false;
-};
 
 struct KBasis {
     int N = 0, n_v = 0, M = 0;
@@ -651,10 +635,27 @@ __global__ void kinetic_online_kernel(KOnArgs A, const double* inflow, double* w
     }
 }
 
-template <class T>
-msp_status upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
-    MSP_TRY(d.alloc(std::max<size_t>(1, h.size()), s));
-    if (!h.empty()) MSP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+// Per-sample iteration counts and flags to the caller's stats (optional; reading
+// them synchronises the stream).
+msp_status kinetic_stats(const KMedium& K, bool mixed, cudaStream_t s, msp_solve_stats* stats, const char* what) {
+    if (!stats) return MSP_OK;
+    std::vector<int> h(2 * (size_t)K.M * K.S);
+    MSP_CUDA(cudaMemcpyAsync(h.data(), K.stats.p, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s));
+    MSP_CUDA(cudaStreamSynchronize(s));
+    msp_solve_stats r{};
+    r.n_solves = (int64_t)K.M * K.S;
+    for (size_t i = 0; i < h.size() / 2; ++i) {
+        r.total_iters += h[2 * i];
+        r.max_iters = std::max(r.max_iters, h[2 * i]);
+        r.n_not_converged += h[2 * i + 1];
+        r.unknown_iters += (long long)h[2 * i] * K.patches[i / K.S].nn * K.n_v;
+    }
+    r.max_refinements = (K.solver == MSP_KINETIC_DIRECT) ? r.max_iters : (mixed ? 0 : 1);
+    *stats = r;
+    if (r.n_not_converged) {
+        set_error(what);
+        return MSP_ERR_NOT_CONVERGED;
+    }
     return MSP_OK;
 }
 
@@ -665,6 +666,11 @@ using namespace msp;
 
 extern "C" msp_status msp_kinetic_build(int n_cells, double eps, int n_v, int n_patches, int buffer, int samples,
                                         void* stream, msp_kmedium* out) {
+    return msp_kinetic_build_hg(n_cells, eps, 0.0, n_v, n_patches, buffer, samples, stream, out);
+}
+
+extern "C" msp_status msp_kinetic_build_hg(int n_cells, double eps, double g, int n_v, int n_patches, int buffer,
+                                           int samples, void* stream, msp_kmedium* out) {
     clear_error();
     MSP_CHECK_ARG(out, "msp_kinetic_build: NULL output");
     *out = nullptr;
@@ -672,6 +678,8 @@ extern "C" msp_status msp_kinetic_build(int n_cells, double eps, int n_v, int n_
                   "msp_kinetic_build: n_cells must be a positive multiple of n_patches");
     MSP_CHECK_ARG(n_v >= 2 && n_v % 2 == 0 && n_v <= 256, "msp_kinetic_build: n_v must be even, 2..256");
     MSP_CHECK_ARG(eps > 0 && buffer >= 0 && samples >= 1, "msp_kinetic_build: eps > 0, buffer >= 0, samples >= 1");
+    MSP_CHECK_ARG(g > -1.0 && g < 1.0, "msp_kinetic_build: the anisotropy g must lie in (-1, 1)");
+    MSP_CHECK_ARG(g == 0.0 || n_v <= 128, "msp_kinetic_build: anisotropic scattering takes at most 128 velocities");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         set_error("msp_kinetic_build: no usable CUDA device");
@@ -679,8 +687,19 @@ extern "C" msp_status msp_kinetic_build(int n_cells, double eps, int n_v, int n_
     }
     auto* h = new msp_kmedium_s();
     KMedium& K = h->K;
-    K.N = n_cells; K.eps = eps; K.n_v = n_v; K.M = n_patches; K.buffer = buffer; K.S = samples;
+    K.N = n_cells; K.eps = eps; K.g = g; K.n_v = n_v; K.M = n_patches; K.buffer = buffer; K.S = samples;
+    K.solver = (g == 0.0) ? MSP_KINETIC_SOURCE_ITERATION : MSP_KINETIC_DIRECT;
     gauss_legendre(n_v, K.v, K.w);
+    // Eq. HG in quadrature form: k(v, v') = (1/2)(1 - g^2) / (1 + g^2 + 2 g v v'), gain
+    // weights w_l' k(v_l, v_l'), loss rates sigma_l = sum_l' w_l' k(v_l', v_l)
+    K.Kw.assign((size_t)n_v * n_v, 0.0);
+    K.sigma.assign(n_v, 0.0);
+    for (int l = 0; l < n_v; ++l)
+        for (int q = 0; q < n_v; ++q) {
+            const double k = 0.5 * (1.0 - g * g) / (1.0 + g * g + 2.0 * g * K.v[l] * K.v[q]);
+            K.Kw[(size_t)l * n_v + q] = K.w[q] * k;
+            K.sigma[q] += K.w[l] * k;
+        }
     const int W = n_cells / n_patches;
     long long off = 0;
     for (int m = 0; m < n_patches; ++m) {
@@ -697,6 +716,7 @@ extern "C" msp_status msp_kinetic_build(int n_cells, double eps, int n_v, int n_
     cudaStream_t s = (cudaStream_t)stream;
     msp_status st;
     if ((st = upload(K.d_v, K.v, s)) || (st = upload(K.d_w, K.w, s)) || (st = upload(K.d_patches, K.patches, s)) ||
+        (st = upload(K.d_Kw, K.Kw, s)) || (st = upload(K.d_sigma, K.sigma, s)) ||
         (st = K.snaps.alloc((size_t)off, s)) || (st = K.stats.alloc((size_t)2 * n_patches * samples, s))) {
         delete h;
         return st;
@@ -722,6 +742,19 @@ extern "C" msp_status msp_kinetic_velocities(msp_kmedium k, double* v_host, doub
     return MSP_OK;
 }
 
+extern "C" msp_status msp_kinetic_set_solver(msp_kmedium k, int solver) {
+    clear_error();
+    MSP_CHECK_ARG(k, "msp_kinetic_set_solver: NULL medium");
+    MSP_CHECK_ARG(solver == MSP_KINETIC_SOURCE_ITERATION || solver == MSP_KINETIC_DIRECT,
+                  "msp_kinetic_set_solver: unknown solver");
+    MSP_CHECK_ARG(solver == MSP_KINETIC_DIRECT || k->K.g == 0.0,
+                  "msp_kinetic_set_solver: source iteration takes isotropic scattering (g = 0) only");
+    MSP_CHECK_ARG(solver == MSP_KINETIC_SOURCE_ITERATION || k->K.n_v <= 128,
+                  "msp_kinetic_set_solver: the direct solver takes at most 128 velocities");
+    k->K.solver = solver;
+    return MSP_OK;
+}
+
 extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, int precision, double tol, int max_iter,
                                          void* stream, msp_solve_stats* stats) {
     clear_error();
@@ -732,6 +765,11 @@ extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, int preci
     MSP_CHECK_ARG(tol > 0 && tol < 1 && max_iter >= 1, "msp_kinetic_sample: tol in (0,1), max_iter >= 1");
     KMedium& K = k->K;
     cudaStream_t s = (cudaStream_t)stream;
+    if (K.solver == MSP_KINETIC_DIRECT) {
+        MSP_TRY(kinetic_direct_sample(K, seed, mixed, tol, max_iter, s));
+        K.sampled = true;
+        return kinetic_stats(K, mixed, s, stats, "msp_kinetic_sample: direct solve stopped at its pass limit for some samples");
+    }
     int max_nn = 0;
     for (auto& P : K.patches) max_nn = std::max(max_nn, P.nn);
     const size_t per = sizeof(double) * ((size_t)max_nn * K.n_v + max_nn) +
@@ -757,26 +795,7 @@ extern "C" msp_status msp_kinetic_sample(msp_kmedium k, uint64_t seed, int preci
     count_launches(1);
     MSP_CUDA(cudaGetLastError());
     K.sampled = true;
-    if (stats) {
-        std::vector<int> h(2 * (size_t)K.M * K.S);
-        MSP_CUDA(cudaMemcpyAsync(h.data(), K.stats.p, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s));
-        MSP_CUDA(cudaStreamSynchronize(s));
-        msp_solve_stats r{};
-        r.n_solves = (int64_t)K.M * K.S;
-        for (size_t i = 0; i < h.size() / 2; ++i) {
-            r.total_iters += h[2 * i];
-            r.max_iters = std::max(r.max_iters, h[2 * i]);
-            r.n_not_converged += h[2 * i + 1];
-            r.unknown_iters += (long long)h[2 * i] * K.patches[i / K.S].nn * K.n_v;
-        }
-        r.max_refinements = mixed ? 0 : 1;
-        *stats = r;
-        if (r.n_not_converged) {
-            set_error("msp_kinetic_sample: source iteration stopped at max_iter for some samples");
-            return MSP_ERR_NOT_CONVERGED;
-        }
-    }
-    return MSP_OK;
+    return kinetic_stats(K, mixed, s, stats, "msp_kinetic_sample: source iteration stopped at max_iter for some samples");
 }
 
 extern "C" msp_status msp_kinetic_get_snapshots(msp_kmedium k, int patch, double* dst, void* stream) {

@@ -420,13 +420,6 @@ __global__ void __launch_bounds__(kDirThreads) direct_finish_kernel(DirArgs A) {
     }
 }
 
-template <class T>
-msp_status upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
-    MSP_TRY(d.alloc(std::max<size_t>(1, h.size()), s));
-    if (!h.empty()) MSP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
-    return MSP_OK;
-}
-
 // Tables and buffers of the direct solver (once per medium).
 msp_status direct_plan(Medium& M, cudaStream_t s) {
     Medium::Direct& D = M.dir;

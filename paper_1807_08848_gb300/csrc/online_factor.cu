@@ -403,13 +403,6 @@ __global__ void transpose_kernel(const T* src, T* dst, int nr, int nc) {
     }
 }
 
-template <class T>
-msp_status upload(DevBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
-    MSP_TRY(d.alloc(std::max<size_t>(1, h.size()), s));
-    if (!h.empty()) MSP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
-    return MSP_OK;
-}
-
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
 
 }  // namespace

@@ -58,6 +58,11 @@ def test_null_arguments_are_rejected(lib):
     assert lib.msp_online_solve_map(None, None, 1, None, None) == N.MSP_ERR_INVALID_ARG
     assert lib.msp_apply_operator(None, 1, 1, None, None, 4, 4, None, None) == N.MSP_ERR_INVALID_ARG
     assert lib.msp_kinetic_sample(None, 0, 0, 1e-8, 10, None, None) == N.MSP_ERR_INVALID_ARG
+    # anisotropy outside (-1, 1), too many velocities for the direct solver, NULL medium
+    assert lib.msp_kinetic_build_hg(128, 0.1, 1.0, 8, 4, 8, 12, None, C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_kinetic_build_hg(128, 0.1, -1.5, 8, 4, 8, 12, None, C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_kinetic_build_hg(128, 0.1, 0.5, 130, 4, 8, 12, None, C.byref(out)) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_kinetic_set_solver(None, 1) == N.MSP_ERR_INVALID_ARG
 
 
 def test_basis_files_are_checked_before_any_device_work(lib, tmp_path):
