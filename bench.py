@@ -782,6 +782,20 @@ def run_extract(args):
     uc, _ = bc.solve(phi, tol=1e-10, max_iter=1000)
     out["online_rel_diff"] = float(torch.linalg.norm(ut - uc) / torch.linalg.norm(uc))
     out["stats_tc"] = bt.stats()
+    # the Jacobi SVD from the identity in FP64 against the FP32-started one (default),
+    # tensor-core products both, with the phase times
+    msp.set_extract_timing(True)
+    for mode in ("fp64", "fp32_preconditioned"):
+        msp.set_svd_mode(mode)
+        b = med.extract(w["tau"], "mixed")
+        out["svd_" + mode] = {"phases_ms": b.extract_timing(), "max_jacobi_sweeps": b.stats()["max_jacobi_sweeps"],
+                              "mean_jacobi_sweeps": b.stats()["mean_jacobi_sweeps"]}
+        bases["svd_" + mode] = b
+    msp.set_extract_timing(False)
+    b64, b32 = bases["svd_fp64"], bases["svd_fp32_preconditioned"]
+    out["svd_max_sigma_diff_rel_sigma1"] = max(float(np.max(np.abs(b32.sigma(m) - b64.sigma(m))) / b64.sigma(m)[0])
+                                               for m in range(0, med.n_patches, 37))
+    out["svd_k_equal"] = all(b32.k(m) == b64.k(m) for m in range(med.n_patches))
     print(json.dumps(out), flush=True)
 
 

@@ -173,6 +173,20 @@ msp_status msp_set_wait_limit(int64_t polls);
 #define MSP_GEMM_CUDA_CORES   1
 msp_status msp_set_gemm_engine(int engine);
 
+/* The SVD of the triangular Cholesky-QR factor T in the extraction (Sec. 3.2,
+ * Eq. svd), one-sided Jacobi on the columns of T^T either way:
+ *   MSP_SVD_FP32_PRECONDITIONED (default): sweeps in FP32 first (V32
+ *     orthogonal to about 1e-6), V re-orthogonalised in FP64 by two
+ *     Newton-Schulz steps V (3 I - V^T V) / 2, then FP64 sweeps on T^T V to the
+ *     FP64 convergence level -- the FP64 sweeps start from nearly orthogonal
+ *     columns and converge in a few sweeps instead of 8 to 20;
+ *   MSP_SVD_FP64: FP64 sweeps from V = I.
+ * Both end at the same FP64 stopping test; process-wide, read by every
+ * extraction.  INVALID_ARG on an unknown mode. */
+#define MSP_SVD_FP64                0
+#define MSP_SVD_FP32_PRECONDITIONED 1
+msp_status msp_set_svd_mode(int mode);
+
 /* --------------------------------------------------------------------- medium */
 
 /* Build the patch tables and evaluate the face coefficients on the device
@@ -305,10 +319,13 @@ msp_status msp_basis_get_stats(msp_basis b, msp_basis_stats* out);
 /* Phase timing of msp_extract_basis (CUDA events on the caller's stream at the
  * phase boundaries; off by default, process-wide switch): after an extraction made
  * with timing on, msp_basis_extract_timing waits for its events and returns the
- * milliseconds of ms_host[5] = Cholesky-QR, Jacobi SVD, truncation and projection,
- * online operators, online factorisation (zeros if the basis was extracted with
- * timing off or loaded from a file), and optionally the algorithmic FP64 work of
- * the Jacobi SVD (22 c flop per column pair and sweep, summed over the patches). */
+ * milliseconds of ms_host[6] = Cholesky-QR, the start of the Jacobi SVD (FP32
+ * sweeps, re-orthogonalisation and T^T V in MSP_SVD_FP32_PRECONDITIONED mode, the
+ * copy T^T otherwise), the FP64 Jacobi sweeps, truncation and projection, online
+ * operators, online factorisation (zeros if the basis was extracted with timing
+ * off or loaded from a file), and optionally the algorithmic FP64 work of the
+ * FP64 Jacobi sweeps (22 c flop per column pair and sweep, summed over the
+ * patches). */
 msp_status msp_set_extract_timing(int enable);
 msp_status msp_basis_extract_timing(msp_basis b, double* ms_host, double* jacobi_flop_host);
 

@@ -21,7 +21,7 @@ from . import _native as N
 from ._native import MspError, MSP_FP64, MSP_MIXED
 
 __all__ = ["Medium", "Basis", "Server", "KineticMedium", "KineticBasis", "MspError", "MSP_FP64", "MSP_MIXED", "load_library",
-           "precision_code", "set_wait_limit", "set_gemm_engine", "set_extract_timing"]
+           "precision_code", "set_wait_limit", "set_gemm_engine", "set_extract_timing", "set_svd_mode"]
 
 
 def load_library():
@@ -43,6 +43,12 @@ def set_gemm_engine(engine: str = "tensor_cores"):
     """FP64 products of the extraction and the online factorisation on the tensor
     cores (error-free BF16 slicing, the default) or on the CUDA cores."""
     N.check(N.load().msp_set_gemm_engine({"tensor_cores": 0, "cuda_cores": 1}[engine]))
+
+
+def set_svd_mode(mode: str = "fp32_preconditioned"):
+    """Jacobi SVD of the extraction: FP32 sweeps, re-orthogonalised, then FP64
+    sweeps (the default), or FP64 sweeps from the identity (msp_set_svd_mode)."""
+    N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1}[mode]))
 
 
 def precision_code(p) -> int:
@@ -271,10 +277,10 @@ class Basis:
     def extract_timing(self) -> dict:
         """Milliseconds per phase of the extraction that built this basis (timing on
         through set_extract_timing) and the Jacobi SVD's algorithmic FP64 flop."""
-        ms = (C.c_double * 5)()
+        ms = (C.c_double * 6)()
         jf = C.c_double()
         N.check(N.load().msp_basis_extract_timing(self._h, ms, C.byref(jf)))
-        names = ("cholqr", "jacobi", "projection", "online_operators", "online_factor")
+        names = ("cholqr", "jacobi_start", "jacobi", "projection", "online_operators", "online_factor")
         return {**{n: ms[i] for i, n in enumerate(names)}, "jacobi_flop": jf.value}
 
     def stats(self) -> dict:

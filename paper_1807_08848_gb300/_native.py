@@ -95,6 +95,7 @@ SIGNATURES = {
     "msp_sample_patch_static": (_i, [_vp, _vp, _i, C.POINTER(_i), _i, _i, _u64, _i, _d, _i, _vp, _vp, C.POINTER(_i)]),
     "msp_set_wait_limit": (_i, [C.c_int64]),
     "msp_set_gemm_engine": (_i, [_i]),
+    "msp_set_svd_mode": (_i, [_i]),
     "msp_extract_basis": (_i, [_vp, _d, _i, _vp, C.POINTER(_vp)]),
     "msp_basis_destroy": (None, [_vp]),
     "msp_basis_info": (_i, [_vp, _i, C.POINTER(_i), C.POINTER(_d)]),

@@ -60,10 +60,10 @@ extern "C" msp_status msp_basis_extract_timing(msp_basis b, double* ms_host, dou
     clear_error();
     MSP_CHECK_ARG(b && ms_host, "msp_basis_extract_timing: NULL argument");
     const Basis& B = b->B;
-    for (int p = 0; p < 5; ++p) ms_host[p] = 0.0;
-    if (B.ext_ev.size() == 6) {
-        MSP_CUDA(cudaEventSynchronize(B.ext_ev[5]));
-        for (int p = 0; p < 5; ++p) {
+    for (int p = 0; p < 6; ++p) ms_host[p] = 0.0;
+    if (B.ext_ev.size() == 7) {
+        MSP_CUDA(cudaEventSynchronize(B.ext_ev[6]));
+        for (int p = 0; p < 6; ++p) {
             float t = 0.f;
             MSP_CUDA(cudaEventElapsedTime(&t, B.ext_ev[p], B.ext_ev[p + 1]));
             ms_host[p] = t;

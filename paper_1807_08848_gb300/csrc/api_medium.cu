@@ -33,6 +33,8 @@ msp_status phase_mark(std::vector<cudaEvent_t>* marks, cudaStream_t s) {
 // Engine of the FP64 products of the extraction and the online factorisation.
 static std::atomic<int> g_gemm_engine{0};
 int fp64_gemm_engine() { return g_gemm_engine.load(std::memory_order_relaxed); }
+static std::atomic<int> g_svd_mode{MSP_SVD_FP32_PRECONDITIONED};
+bool svd_mixed() { return g_svd_mode.load(std::memory_order_relaxed) == MSP_SVD_FP32_PRECONDITIONED; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
@@ -66,6 +68,13 @@ using namespace msp;
 extern "C" const char* msp_last_error(void) { return g_err.c_str(); }
 extern "C" const char* msp_version(void) { return "msp 0.1 (sm_103a)"; }
 extern "C" int64_t msp_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" msp_status msp_set_svd_mode(int mode) {
+    clear_error();
+    MSP_CHECK_ARG(mode == MSP_SVD_FP64 || mode == MSP_SVD_FP32_PRECONDITIONED, "msp_set_svd_mode: unknown mode");
+    g_svd_mode.store(mode, std::memory_order_relaxed);
+    return MSP_OK;
+}
 
 extern "C" msp_status msp_set_gemm_engine(int engine) {
     clear_error();

@@ -26,6 +26,7 @@ struct SmallMat {
     long long off;   // offset of this patch's c x c block
     int c;           // order
     int n;           // rows of the tall matrix
+    int idx;         // patch index (the Jacobi kernels run the blocks largest first)
 };
 
 // Cholesky of (G + shift I) = L L^T in global memory (one CTA per matrix),
@@ -120,72 +121,35 @@ __global__ void jacobi_init_kernel(const SmallMat* mats, const double* T, double
 constexpr int kJacGroup = 8;       // threads per column pair
 constexpr int kJacMaxPairs = 512;  // c <= 1024
 
-// One-sided (Hestenes) Jacobi in FP64 on the columns of W = T^T (c x c): rotate
-// column pairs (p, q) until every pair is orthogonal to relative level tol; V
-// accumulates the rotations, so at the end W = Z S and T = V S Z^T: the
-// singular values are the column norms of W and V holds the left singular
-// vectors of T.  (On T^T the sweeps converge in about a third of the sweeps
-// needed on the columns of T.)  Pairs follow the round-robin tournament order,
-// c/2 disjoint pairs per round.  Each round has three phases: groups of
-// kJacGroup threads take one pair each and form its three inner products; one
-// thread per pair decides whether to rotate and takes the angle (the FP64 pipe
-// is the bound, so the square roots and divisions are done once per pair, not
-// once per lane of a group); then the whole block applies the round's
-// rotations to the columns of W and V with row-wise accesses.  W lives in
-// shared memory (leading dimension c + 1) when c <= smem_c, else in global
-// memory.
+// One-sided (Hestenes) Jacobi on the columns of w (c x c, leading dimension ldw):
+// rotate column pairs (p, q) until every pair is orthogonal to relative level
+// tol; v (leading dimension ldv) accumulates the same rotations.  Started from
+// w = T^T V0 with V0 orthogonal, it ends with w = Z S and T = (V0 J) S Z^T, J the
+// product of the rotations: the singular values are the column norms of w and
+// v = V0 J holds the left singular vectors of T.  (On T^T the sweeps converge in
+// about a third of the sweeps needed on the columns of T.)  Pairs follow the
+// round-robin tournament order, c/2 disjoint pairs per round.  Each round has
+// three phases: groups of kJacGroup threads take one pair each and form its
+// three inner products; one thread per pair decides whether to rotate and takes
+// the angle (the square roots and divisions are done once per pair, not once per
+// lane of a group); then the whole block applies the round's rotations to the
+// columns of w and v with row-wise accesses.
 // Skips: columns below u |T|_F are numerically zero; a pair orthogonal to the
 // rounding floor of its inner product is left alone; and a pair whose columns
 // are both below small_rel |T|_F (far under the truncation level) is left alone,
-// since rotating it only mixes directions that are dropped.
-__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, double* W, double* V, int max_sweeps,
-                                                         double tol, double small_rel, int smem_c, int* sweeps_out) {
-    extern __shared__ __align__(16) unsigned char jac_smem[];
-    __shared__ double s_cs[kJacMaxPairs], s_sn[kJacMaxPairs], s_ga[kJacMaxPairs];
+// since rotating it only mixes directions that are dropped.  Returns the sweeps
+// taken (max_sweeps if it did not converge).  fro2 = |T|_F^2, u = unit roundoff
+// of T.  Called by all threads of the block.
+template <class T>
+__device__ int jacobi_sweeps(T* w, int ldw, T* v, int ldv, int c, int max_sweeps, T tol, T small_rel, T fro2, T u) {
+    __shared__ T s_cs[kJacMaxPairs], s_sn[kJacMaxPairs], s_ga[kJacMaxPairs];
     __shared__ int s_p[kJacMaxPairs], s_q[kJacMaxPairs];
-    __shared__ double s_red[32];
-    __shared__ double s_fro;
     __shared__ int s_rot;
-    const SmallMat S = mats[blockIdx.x];
-    const int c = S.c;
-    if (c <= 1 || c > 2 * kJacMaxPairs) {
-        if (threadIdx.x == 0) sweeps_out[blockIdx.x] = 0;
-        return;
-    }
-    const bool in_smem = c <= smem_c;
-    const int ldw = in_smem ? c + 1 : c;
-    double* w = in_smem ? reinterpret_cast<double*>(jac_smem) : W + S.off;
-    double* v = V + S.off;
-    if (in_smem) {
-        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
-            const int i = (int)(e % c), j = (int)(e / c);
-            w[i + (long long)j * ldw] = W[S.off + e];
-        }
-    }
-    // |T|_F^2
-    {
-        double a = 0.0;
-        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
-            const int i = (int)(e % c), j = (int)(e / c);
-            const double x = w[i + (long long)j * ldw];
-            a += x * x;
-        }
-        a = warp_sum(a);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = a;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            double t = (threadIdx.x < (blockDim.x >> 5)) ? s_red[threadIdx.x] : 0.0;
-            t = warp_sum(t);
-            if (threadIdx.x == 0) s_fro = t;
-        }
-        __syncthreads();
-    }
-    const double eps = 1.1102230246251565e-16;
-    const double negligible = eps * eps * s_fro;   // (u |T|_F)^2
+    const T negligible = u * u * fro2;   // (u |T|_F)^2
     // rounding floor of an inner product of columns of norms a and b: the columns
     // carry absolute errors ~ c u |T|_F, so orthogonality below that is noise
-    const double floor_abs = 2.0 * c * eps * sqrt(s_fro);
-    const double small2 = small_rel * small_rel * s_fro;
+    const T floor_abs = T(2) * c * u * sqrt(fro2);
+    const T small2 = small_rel * small_rel * fro2;
     const int np = c + (c & 1);   // players, even
     const int npairs = np / 2;
     const int g = threadIdx.x % kJacGroup;
@@ -210,12 +174,12 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
                     q = max(a, b);
                 }
                 const bool real = live && q < c;
-                const double* wp = w + (long long)p * ldw;
-                const double* wq = w + (long long)q * ldw;
-                double al = 0.0, be = 0.0, ga = 0.0;
+                const T* wp = w + (long long)p * ldw;
+                const T* wq = w + (long long)q * ldw;
+                T al = 0, be = 0, ga = 0;
                 if (real) {
                     for (int i = g; i < c; i += kJacGroup) {
-                        const double x = wp[i], y = wq[i];
+                        const T x = wp[i], y = wq[i];
                         al = fma(x, x, al);
                         be = fma(y, y, be);
                         ga = fma(x, y, ga);
@@ -239,37 +203,37 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
             // phase 2: one thread per pair, the decision and the rotation angle
             for (int pr = threadIdx.x; pr < npairs; pr += blockDim.x) {
                 if (s_p[pr] < 0) continue;
-                const double al = s_cs[pr], be = s_sn[pr], ga = s_ga[pr];
-                const double na = sqrt(al), nb = sqrt(be);
+                const T al = s_cs[pr], be = s_sn[pr], ga = s_ga[pr];
+                const T na = sqrt(al), nb = sqrt(be);
                 if (al <= negligible || be <= negligible || (al < small2 && be < small2) ||
                     fabs(ga) <= tol * na * nb + floor_abs * (na + nb)) {
                     s_p[pr] = -1;
                     continue;
                 }
-                const double zeta = (be - al) / (2.0 * ga);
-                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double cs = 1.0 / sqrt(1.0 + t * t);
+                const T zeta = (be - al) / (T(2) * ga);
+                const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                const T cs = T(1) / sqrt(T(1) + t * t);
                 s_cs[pr] = cs;
                 s_sn[pr] = cs * t;
                 s_rot = 1;
             }
             __syncthreads();
-            // phase 3: the round's rotations applied to the columns of W and V, rows
+            // phase 3: the round's rotations applied to the columns of w and v, rows
             // fastest
             for (int e = threadIdx.x; e < npairs * c; e += blockDim.x) {
                 const int pr = e / c, i = e - pr * c;
                 const int p = s_p[pr];
                 if (p < 0) continue;
                 const int q = s_q[pr];
-                const double cs = s_cs[pr], sn = s_sn[pr];
-                double* wp = w + (long long)p * ldw;
-                double* wq = w + (long long)q * ldw;
-                const double x = wp[i], y = wq[i];
+                const T cs = s_cs[pr], sn = s_sn[pr];
+                T* wp = w + (long long)p * ldw;
+                T* wq = w + (long long)q * ldw;
+                const T x = wp[i], y = wq[i];
                 wp[i] = cs * x - sn * y;
                 wq[i] = sn * x + cs * y;
-                double* vp = v + (long long)p * c;
-                double* vq = v + (long long)q * c;
-                const double xv = vp[i], yv = vq[i];
+                T* vp = v + (long long)p * ldv;
+                T* vq = v + (long long)q * ldv;
+                const T xv = vp[i], yv = vq[i];
                 vp[i] = cs * xv - sn * yv;
                 vq[i] = sn * xv + cs * yv;
             }
@@ -278,13 +242,104 @@ __global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, d
         if (s_rot == 0) break;
         __syncthreads();
     }
+    return sweep;
+}
+
+template <class T>
+__device__ T block_sum_sq(const T* w, int ldw, int c, T* red) {
+    T a = 0;
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        const T x = w[i + (long long)j * ldw];
+        a += x * x;
+    }
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    T t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    __syncthreads();
+    return t;
+}
+
+// FP64 Jacobi of W (global, c x c per patch; copied to shared memory with leading
+// dimension c + 1 when c <= smem_c), V (global) accumulating.
+__global__ void __launch_bounds__(512) jacobi_svd_kernel(const SmallMat* mats, double* W, double* V, int max_sweeps,
+                                                         double tol, double small_rel, int smem_c, int* sweeps_out) {
+    extern __shared__ __align__(16) unsigned char jac_smem[];
+    __shared__ double s_red[32];
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    if (c <= 1 || c > 2 * kJacMaxPairs) {
+        if (threadIdx.x == 0) sweeps_out[S.idx] = 0;
+        return;
+    }
+    const bool in_smem = c <= smem_c;
+    const int ldw = in_smem ? c + 1 : c;
+    double* w = in_smem ? reinterpret_cast<double*>(jac_smem) : W + S.off;
+    if (in_smem) {
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            w[i + (long long)j * ldw] = W[S.off + e];
+        }
+        __syncthreads();
+    }
+    const double fro2 = block_sum_sq(w, ldw, c, s_red);
+    const int sweep = jacobi_sweeps<double>(w, ldw, V + S.off, c, c, max_sweeps, tol, small_rel, fro2,
+                                            1.1102230246251565e-16);
     if (in_smem) {
         for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
             const int i = (int)(e % c), j = (int)(e / c);
             W[S.off + e] = w[i + (long long)j * ldw];
         }
     }
-    if (threadIdx.x == 0) sweeps_out[blockIdx.x] = sweep;
+    if (threadIdx.x == 0) sweeps_out[S.idx] = sweep;
+}
+
+// FP32 Jacobi of (float) T^T with V = I, both in shared memory (leading dimension
+// c + 1) when c <= smem_c, else in the scratch (2 c^2 floats per patch at 2 off).
+// Writes V (FP64 copy of the FP32 rotations, orthogonal to about 1e-6), the
+// starting point of the FP64 sweeps after re-orthogonalisation.
+__global__ void __launch_bounds__(512) jacobi_svd32_kernel(const SmallMat* mats, const double* Tm, float* scratch,
+                                                           double* V, int max_sweeps, float tol, float small_rel,
+                                                           int smem_c, int* sweeps_out) {
+    extern __shared__ __align__(16) unsigned char jac_smem[];
+    __shared__ float s_red[32];
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    if (c < 1 || c > 2 * kJacMaxPairs) {
+        if (threadIdx.x == 0) sweeps_out[S.idx] = 0;
+        return;
+    }
+    const bool in_smem = c <= smem_c;
+    const int ld = in_smem ? c + 1 : c;
+    float* w = in_smem ? reinterpret_cast<float*>(jac_smem) : scratch + 2 * S.off;
+    float* v = w + (long long)c * ld;
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        w[i + (long long)j * ld] = (float)Tm[S.off + j + (long long)i * c];
+        v[i + (long long)j * ld] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const float fro2 = block_sum_sq(w, ld, c, s_red);
+    int sweep = 0;
+    if (c > 1) sweep = jacobi_sweeps<float>(w, ld, v, ld, c, max_sweeps, tol, small_rel, fro2, 5.9604645e-8f);
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        V[S.off + e] = (double)v[i + (long long)j * ld];
+    }
+    if (threadIdx.x == 0) sweeps_out[S.idx] = sweep;
+}
+
+// Newton-Schulz scaling for X (3 I - X^T X) / 2 in place of G = X^T X: the
+// multiplier M = (3 I - G) / 2, so that X M is the next iterate (c x c).
+__global__ void newton_schulz_kernel(const SmallMat* mats, double* G) {
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        G[S.off + e] = ((i == j) ? 1.5 : 0.0) - 0.5 * G[S.off + e];
+    }
 }
 
 
@@ -434,7 +489,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
     long long mo = 0, so = 0;
     int maxc = 0, maxn = 0;
     for (int m = 0; m < np; ++m) {
-        mats[m] = SmallMat{mo, cols[m], n_rows[m]};
+        mats[m] = SmallMat{mo, cols[m], n_rows[m], m};
         mo += (long long)cols[m] * cols[m];
         sig_off[m] = so;
         so += cols[m];
@@ -446,13 +501,14 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
     MSP_TRY(upload(d_mats, mats, s));
     MSP_TRY(upload(d_sig_off, sig_off, s));
     DevBuf<double> G, L, F, Fi, T0, T1, W, V, ping, pong, sig_tmp, sig;
-    DevBuf<int> order, kdev, status, sweeps;
+    DevBuf<int> order, kdev, status, sweeps, sweeps32;
     DevBuf<double> shift_scale;
     MSP_TRY(G.alloc(mo, s)); MSP_TRY(L.alloc(mo, s)); MSP_TRY(F.alloc(mo, s)); MSP_TRY(Fi.alloc(mo, s));
     MSP_TRY(T0.alloc(mo, s)); MSP_TRY(T1.alloc(mo, s));
     MSP_TRY(ping.alloc(snap_elems, s)); MSP_TRY(pong.alloc(snap_elems, s));
     MSP_TRY(sig_tmp.alloc(so, s)); MSP_TRY(sig.alloc(so, s));
     MSP_TRY(order.alloc(so, s)); MSP_TRY(kdev.alloc(np, s)); MSP_TRY(status.alloc(np, s)); MSP_TRY(sweeps.alloc(np, s));
+    MSP_TRY(sweeps32.alloc(np, s));
     {
         // shift of the first pass: 11 (n c + c (c+1)) u, times |R|_F^2 (= trace of the Gram)
         std::vector<double> sc(np);
@@ -537,21 +593,9 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         return MSP_ERR_INVALID_ARG;
     }
     {
-        jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
-        count_launches(1);
-        // largest order whose W is held in shared memory: the opt-in limit per
-        // block less the kernel's static shared memory
-        cudaFuncAttributes fa{};
-        MSP_CUDA(cudaFuncGetAttributes(&fa, jacobi_svd_kernel));
         int dev = 0, optin = 0;
         MSP_CUDA(cudaGetDevice(&dev));
         MSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const long long dyn_max = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
-        int c64 = 0;
-        while ((long long)(c64 + 1) * (c64 + 2) * (long long)sizeof(double) <= dyn_max) ++c64;
-        c64 = std::min(c64, maxc);
-        const size_t sm64 = (size_t)c64 * (c64 + 1) * sizeof(double);
-        MSP_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));
         // pairs of columns both below 1e-3 tau sigma_1 (|T|_F / sqrt(c) <= sigma_1) are not rotated
         const double small_rel = 1e-3 * tau / std::sqrt((double)std::max(maxc, 1));
         // the largest blocks first (their sweeps cost the most), so the last wave is short
@@ -559,6 +603,72 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         std::stable_sort(by_size.begin(), by_size.end(), [](const SmallMat& a, const SmallMat& b) { return a.c > b.c; });
         DevBuf<SmallMat> d_by_size;
         MSP_TRY(upload(d_by_size, by_size, s));
+        if (svd_mixed()) {
+            // FP32 sweeps on (float) T^T from V = I, then V re-orthogonalised in FP64
+            // by two Newton-Schulz steps (orthogonal to ~1e-6 -> ~1e-12 -> rounding),
+            // W = T^T V; the FP64 sweeps below then start from nearly orthogonal
+            // columns and converge in a few sweeps.
+            cudaFuncAttributes fa{};
+            MSP_CUDA(cudaFuncGetAttributes(&fa, jacobi_svd32_kernel));
+            const long long dyn_max = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
+            int c32 = 0;
+            while (2LL * (c32 + 1) * (c32 + 2) * (long long)sizeof(float) <= dyn_max) ++c32;
+            c32 = std::min(c32, maxc);
+            const size_t sm32 = 2 * (size_t)c32 * (c32 + 1) * sizeof(float);
+            MSP_CUDA(cudaFuncSetAttribute(jacobi_svd32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32));
+            // FP32 scratch of the blocks too large for shared memory (2 c^2 floats
+            // each): the second Cholesky-QR output buffer, free now, when it holds
+            // them all (sum of c^2 <= sum of n c doubles)
+            DevBuf<float> scratch32;
+            float* scr = reinterpret_cast<float*>(pong.p);
+            if (maxc > c32 && snap_elems < mo) {
+                MSP_TRY(scratch32.alloc(2 * (size_t)mo, s));
+                scr = scratch32.p;
+            }
+            jacobi_svd32_kernel<<<np, 512, sm32, s>>>(d_by_size.p, Tacc, scr, V.p, 30,
+                                                      (float)(maxc * 5.96e-8), (float)small_rel, c32, sweeps32.p);
+            count_launches(1);
+            MSP_CUDA(cudaGetLastError());
+            double* Vp = V.p;
+            double* Vq = L.p;
+            for (int it = 0; it < 2; ++it) {
+                for (int m = 0; m < np; ++m) {
+                    const int c = mats[m].c;
+                    gd[m] = GemmDesc{Vp + mats[m].off, Vp + mats[m].off, G.p + mats[m].off, c, c, c, c, c, c, 1.0, 0.0};
+                }
+                MSP_TRY(run_gemm(true, maxc, maxc));
+                newton_schulz_kernel<<<np, 256, 0, s>>>(d_mats.p, G.p);
+                count_launches(1);
+                MSP_CUDA(cudaGetLastError());
+                for (int m = 0; m < np; ++m) {
+                    const int c = mats[m].c;
+                    gd[m] = GemmDesc{Vp + mats[m].off, G.p + mats[m].off, Vq + mats[m].off, c, c, c, c, c, c, 1.0, 0.0};
+                }
+                MSP_TRY(run_gemm(false, maxc, maxc));
+                std::swap(Vp, Vq);
+            }
+            // two swaps: the re-orthogonalised V is back in V
+            for (int m = 0; m < np; ++m) {
+                const int c = mats[m].c;
+                gd[m] = GemmDesc{Tacc + mats[m].off, V.p + mats[m].off, W.p + mats[m].off, c, c, c, c, c, c, 1.0, 0.0};
+            }
+            MSP_TRY(run_gemm(true, maxc, maxc));
+        } else {
+            jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
+            count_launches(1);
+            MSP_CUDA(cudaGetLastError());
+        }
+        MSP_TRY(phase_mark(marks, s));
+        // largest order whose W is held in shared memory: the opt-in limit per
+        // block less the kernel's static shared memory
+        cudaFuncAttributes fa{};
+        MSP_CUDA(cudaFuncGetAttributes(&fa, jacobi_svd_kernel));
+        const long long dyn_max = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
+        int c64 = 0;
+        while ((long long)(c64 + 1) * (c64 + 2) * (long long)sizeof(double) <= dyn_max) ++c64;
+        c64 = std::min(c64, maxc);
+        const size_t sm64 = (size_t)c64 * (c64 + 1) * sizeof(double);
+        MSP_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64));
         jacobi_svd_kernel<<<np, 512, sm64, s>>>(d_by_size.p, W.p, V.p, 40, maxc * 1.12e-16, small_rel, c64, sweeps.p);
         count_launches(1);
         MSP_CUDA(cudaGetLastError());

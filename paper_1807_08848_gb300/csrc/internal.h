@@ -103,6 +103,8 @@ msp_status ozaki_check(OzakiWork& w, cudaStream_t s);
 // Engine of the FP64 products of the extraction and the online factorisation:
 // 0 tensor cores (default), 1 CUDA cores.
 int fp64_gemm_engine();
+// Jacobi SVD of the extraction: FP32 sweeps first, then FP64 (msp_set_svd_mode).
+bool svd_mixed();
 
 // ------------------------------------------------------------------ geometry
 

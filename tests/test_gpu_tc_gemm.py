@@ -1,6 +1,7 @@
 """The FP64 products of the extraction on the tensor cores (error-free BF16
 slicing, tcgen05 kind::f16) against the same extraction on the CUDA cores' FP64
-FMA kernels, and both against the oracle.
+FMA kernels, and both against the oracle; likewise the Jacobi SVD started by
+FP32 sweeps (re-orthogonalised in FP64) against plain FP64 sweeps.
 
 The Gram and triangular products of Cholesky-QR and the projection onto the
 singular vectors (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) are FP64-accurate
@@ -32,19 +33,24 @@ def sin_angle(Qa, Qb):
     return float(np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2)) if Qb.size else 0.0
 
 
-def extract_both(med, tau, precision):
+def extract_both(med, tau, precision, switch="engine"):
+    """Two extractions of the same snapshots: (reference setting, setting under
+    test) -- CUDA-core vs tensor-core products, or FP64 vs FP32-started Jacobi."""
+    set_, ref, new = {"engine": (msp.set_gemm_engine, "cuda_cores", "tensor_cores"),
+                      "svd": (msp.set_svd_mode, "fp64", "fp32_preconditioned")}[switch]
     try:
-        msp.set_gemm_engine("cuda_cores")
+        set_(ref)
         b_cc = med.extract(tau, precision)
-        msp.set_gemm_engine("tensor_cores")
+        set_(new)
         b_tc = med.extract(tau, precision)
     finally:
-        msp.set_gemm_engine("tensor_cores")
+        set_(new)
     return b_cc, b_tc
 
 
+@pytest.mark.parametrize("switch", ["engine", "svd"])
 @pytest.mark.parametrize("case", ["small", "lognormal-256", "ragged"])
-def test_engines_agree_and_match_the_oracle(case):
+def test_engines_agree_and_match_the_oracle(case, switch):
     if case == "small":
         w = synth.workload_small()
         ms, ps, seed, tau, N = w["medium"], w["patches"], w["seed"], w["tau"], 128
@@ -57,7 +63,7 @@ def test_engines_agree_and_match_the_oracle(case):
         ms, seed, tau = synth.hou_wu(N, 1 / 6), 21, 1e-6
     med = msp.Medium(ms, ps)
     med.sample(seed, "fp64", tol=1e-13, max_iter=20000)
-    b_cc, b_tc = extract_both(med, tau, "fp64")
+    b_cc, b_tc = extract_both(med, tau, "fp64", switch)
     off = E.offline(ms, ps, seed, tau)
     for m in range(ps.n_patches):
         s_cc, s_tc = b_cc.sigma(m), b_tc.sigma(m)
@@ -92,3 +98,14 @@ def test_engine_argument():
         msp.set_gemm_engine("other")
     from paper_1807_08848_gb300 import _native as N
     assert N.load().msp_set_gemm_engine(7) == N.MSP_ERR_INVALID_ARG
+    assert N.load().msp_set_svd_mode(7) == N.MSP_ERR_INVALID_ARG
+
+
+def test_fp32_started_jacobi_takes_fewer_fp64_sweeps():
+    """The FP64 sweeps after the FP32 start converge in a few sweeps."""
+    w = synth.workload_small()
+    med = msp.Medium(w["medium"], w["patches"])
+    med.sample(w["seed"], "fp64", tol=1e-13, max_iter=20000)
+    b64, b32 = extract_both(med, w["tau"], "fp64", "svd")
+    assert b32.stats()["max_jacobi_sweeps"] <= 5
+    assert b32.stats()["max_jacobi_sweeps"] < b64.stats()["max_jacobi_sweeps"]
