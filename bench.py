@@ -785,7 +785,7 @@ def run_extract(args):
     # the Jacobi SVD from the identity in FP64 against the FP32-started one (default),
     # tensor-core products both, with the phase times
     msp.set_extract_timing(True)
-    for mode in ("fp64", "fp32_preconditioned"):
+    for mode in ("fp32_preconditioned", "fp64"):
         msp.set_svd_mode(mode)
         b = med.extract(w["tau"], "mixed")
         out["svd_" + mode] = {"phases_ms": b.extract_timing(), "max_jacobi_sweeps": b.stats()["max_jacobi_sweeps"],

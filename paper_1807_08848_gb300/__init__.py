@@ -45,9 +45,9 @@ def set_gemm_engine(engine: str = "tensor_cores"):
     N.check(N.load().msp_set_gemm_engine({"tensor_cores": 0, "cuda_cores": 1}[engine]))
 
 
-def set_svd_mode(mode: str = "fp32_preconditioned"):
-    """Jacobi SVD of the extraction: FP32 sweeps, re-orthogonalised, then FP64
-    sweeps (the default), or FP64 sweeps from the identity (msp_set_svd_mode)."""
+def set_svd_mode(mode: str = "fp64"):
+    """Jacobi SVD of the extraction: FP64 sweeps from the identity (the default),
+    or FP32 sweeps, re-orthogonalised, then FP64 sweeps (msp_set_svd_mode)."""
     N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1}[mode]))
 
 

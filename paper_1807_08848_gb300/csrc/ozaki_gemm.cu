@@ -22,14 +22,15 @@
 //
 // Structure flags of the descriptors (zero ranges of op(A) or op(B)) are applied
 // while slicing: those entries become zero slices whatever the memory holds.
-// Layout of a sliced operand: [slice][row tile][K slab of 32][row group of 8]
+// Layout of a sliced operand: [slice][row tile][K slab of 16][row group of 8]
 // [k core of 8][row][k], BF16 -- the no-swizzle K-major layout of the MMA, 16-byte
-// core matrices, K-adjacent cores 128 B apart, 8-row groups 512 B apart; one
+// core matrices, K-adjacent cores 128 B apart, 8-row groups 256 B apart; one
 // (slice, row tile, slab) block is contiguous and moves with one bulk copy.
 //
 // MMA kernel: one CTA of 256 threads per 128 x 32 output tile of one product.
-// Thread 0 issues the bulk copies (two stages of 80 KB: 8 A slices of 128 x 32
-// and 8 B slices of 32 x 32) and the MMAs; the 8 diagonal accumulators of a chunk
+// Thread 0 issues the bulk copies (five stages of 40 KB: 8 A slices of 128 x 16
+// and 8 B slices of 32 x 16; four slabs are in flight while one is multiplied)
+// and the MMAs; the 8 diagonal accumulators of a chunk
 // (8 x 32 columns) alternate between two halves of tensor memory, so the read-out
 // of one chunk overlaps the MMAs of the next.  Every wait is bounded: on timeout
 // the CTA records the failure, stops issuing work, waits (bounded) for its issued
@@ -50,8 +51,10 @@ constexpr int kBeta = 7;
 constexpr int kDiag = kSlices;            // diagonals g = t + u = 2 .. kSlices + 1
 constexpr int kTM = 128;                  // output rows per CTA (MMA M)
 constexpr int kTN = 32;                   // output columns per CTA (MMA N)
-constexpr int kSlabK = 32;                // K per staged slab
-constexpr int kChunkSlabs = 4;            // slabs per exactness chunk (K = 128)
+constexpr int kSlabK = 16;                // K per staged slab (one MMA)
+constexpr int kCoresK = kSlabK / 8;       // 8 x 8 core matrices along K per slab
+constexpr int kChunkSlabs = 128 / kSlabK; // slabs per exactness chunk (K = 128)
+constexpr int kStages = 5;                // slabs in flight: four copies ahead of the MMAs
 constexpr int kOzThreads = 256;
 constexpr unsigned kAElems = kTM * kSlabK;                    // one A slice block
 constexpr unsigned kBElems = kTN * kSlabK;
@@ -233,8 +236,8 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, co
         // e = [tile][slab][row group][k core][row][k]
         const int kk = (int)(e & 7);
         const int rr = (int)((e >> 3) & 7);
-        const int kc = (int)((e >> 6) & 3);
-        unsigned q = e >> 8;
+        const int kc = (int)((e >> 6) % kCoresK);
+        unsigned q = e / (64u * kCoresK);
         const int rg = (int)(q % (RT / 8));
         q /= (RT / 8);
         const int slab = (int)(q % slabs_u);
@@ -272,7 +275,7 @@ struct OzArgs {
 
 __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
-    __shared__ __align__(8) unsigned long long full[2], empty[2], accb[2], accfree[2];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], accb[2], accfree[2];
     __shared__ unsigned s_tmem;
     __shared__ int s_fail;
     const int z = blockIdx.z;
@@ -283,11 +286,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     if (D.lower && tn * kTN > tm * kTM + kTM - 1) return;          // tile above the diagonal
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&accb[s], 1);
-            mbar_init(&accfree[s], kOzThreads);
+        }
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(&accb[h], 1);
+            mbar_init(&accfree[h], kOzThreads);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
@@ -314,9 +319,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     auto b_stage = [&](int st, int u) {
         return stage0 + (size_t)st * kStageBytes + (size_t)kSlices * kAElems * 2 + (size_t)u * kBElems * 2;
     };
-    int last_copy[2] = {-1, -1};   // thread 0: last slab copied into each stage
+    int last_copy[kStages];        // thread 0: last slab copied into each stage
+    for (int st = 0; st < kStages; ++st) last_copy[st] = -1;
     auto issue_copy = [&](int slab) {
-        const int st = slab & 1;
+        const int st = slab % kStages;
         last_copy[st] = slab;
         mbar_expect_tx(&full[st], kStageBytes);
         for (int t = 0; t < kSlices; ++t)
@@ -324,19 +330,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         for (int u = 0; u < kSlices; ++u)
             bulk_g2s(b_stage(st, u), b0 + u * b_ps + (long long)slab * kBElems, kBElems * 2, &full[st]);
     };
-    const unsigned lbo = 128, sbo = 512;
+    const unsigned lbo = 128, sbo = kCoresK * 128;   // K-adjacent cores, 8-row groups
     int last_commit[2] = {-1, -1};   // thread 0: last chunk committed to each accumulator half
-    // thread 0: the MMAs of one slab; false on a timed-out wait
+    // thread 0: the MMAs of one slab, then the refill of the stage the slab before
+    // it used (slab sl + kStages - 1), so that the tensor pipe always holds the
+    // MMAs of the slabs already staged; false on a timed-out wait.  Slab j is the
+    // (j / kStages)-th use of stage j % kStages, which sets both barriers' parities.
     auto mma_slab = [&](int sl) -> bool {
         const int chunk = sl / kChunkSlabs, first = (sl % kChunkSlabs) == 0;
         const int half = chunk & 1;
-        if (sl + 1 < slabs) {   // refill the other stage once its MMAs are done
-            if (sl >= 1 && !mbar_wait_or_fail(&empty[(sl - 1) & 1], (unsigned)(((sl - 1) >> 1) & 1), fail))
-                return false;
-            issue_copy(sl + 1);
-        }
-        const int st = sl & 1;
-        if (!mbar_wait_or_fail(&full[st], (unsigned)((sl >> 1) & 1), fail)) return false;
+        const int st = sl % kStages;
+        if (!mbar_wait_or_fail(&full[st], (unsigned)((sl / kStages) & 1), fail)) return false;
         if (first && chunk >= 2 && !mbar_wait_or_fail(&accfree[half], (unsigned)(((chunk - 2) >> 1) & 1), fail))
             return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -360,6 +364,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         if ((sl % kChunkSlabs) == kChunkSlabs - 1 || sl == slabs - 1) {
             mma_commit(&accb[half]);
             last_commit[half] = chunk;
+        }
+        const int nxt = sl + kStages - 1;
+        if (nxt < slabs) {
+            const int prev = sl - 1;   // nxt goes into the stage of slab sl - 1 (a fresh one for sl = 0)
+            if (prev >= 0 && !mbar_wait_or_fail(&empty[prev % kStages], (unsigned)((prev / kStages) & 1), fail))
+                return false;
+            issue_copy(nxt);
         }
         return true;
     };
@@ -407,7 +418,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         if (a_lo < 0 || b_lo < 0 || a_hi > A.n_slices || b_hi > A.n_slices || tm >= E.rta || tn >= E.rtb) *fail = 1;
     }
     __syncthreads();
-    if (tid == 0 && slabs >= 1 && !*fail) issue_copy(0);
+    if (tid == 0 && !*fail)
+        for (int j = 0; j < kStages - 1 && j < slabs; ++j) issue_copy(j);
     bool ok = true;   // warp-uniform
     int done_chunks = 0;
     for (int sl = 0; sl < slabs; ++sl) {
@@ -471,8 +483,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     if (failed && tid == 0) {
         // bounded waits for the copies and MMAs already issued, before the shared
         // and tensor memory they use is given up
-        for (int st = 0; st < 2; ++st)
-            if (last_copy[st] >= 0) mbar_wait_or_fail(&full[st], (unsigned)((last_copy[st] >> 1) & 1), nullptr);
+        for (int st = 0; st < kStages; ++st)
+            if (last_copy[st] >= 0) mbar_wait_or_fail(&full[st], (unsigned)((last_copy[st] / kStages) & 1), nullptr);
         for (int h = 0; h < 2; ++h)
             if (last_commit[h] >= 0) mbar_wait_or_fail(&accb[h], (unsigned)((last_commit[h] >> 1) & 1), nullptr);
     }
@@ -560,7 +572,7 @@ msp_status ozaki_gemm_batched(const std::vector<GemmDesc>& h, const GemmDesc* d_
         a.n_slices = (long long)w.slices.n;
         a.scale_exp = w.scales.p;
         a.err = w.err.p;
-        const int smem = 2 * (int)kStageBytes;
+        const int smem = kStages * (int)kStageBytes;
         MSP_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         oz_mma_kernel<<<dim3(max_tiles, 1, nb), kOzThreads, smem, s>>>(a);
         count_launches(1);
