@@ -183,11 +183,16 @@ msp_status msp_set_gemm_engine(int engine);
  *     above about 1e-7 sigma_1, and the snapshot blocks of the elliptic
  *     workloads keep most of their columns below that, so the FP64 sweeps still
  *     need nearly as many sweeps (measured at 2049^2: 283 ms of FP64 sweeps after
- *     71 ms of FP32 start, against 371 ms from V = I).
+ *     71 ms of FP32 start, against 371 ms from V = I);
+ *   MSP_SVD_QR_PRECONDITIONED: Householder QR with column pivoting T P = Q R in
+ *     FP64 first (Drmac and Veselic 2008), then FP64 sweeps on the columns of
+ *     R^T with V started at Q: the rows of R decay with the pivots, so the
+ *     sweeps start from graded, nearly orthogonal columns.
  * Both end at the same FP64 stopping test; process-wide, read by every
  * extraction.  INVALID_ARG on an unknown mode. */
 #define MSP_SVD_FP64                0
 #define MSP_SVD_FP32_PRECONDITIONED 1
+#define MSP_SVD_QR_PRECONDITIONED   2
 msp_status msp_set_svd_mode(int mode);
 
 /* --------------------------------------------------------------------- medium */

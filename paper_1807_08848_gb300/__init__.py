@@ -47,8 +47,9 @@ def set_gemm_engine(engine: str = "tensor_cores"):
 
 def set_svd_mode(mode: str = "fp64"):
     """Jacobi SVD of the extraction: FP64 sweeps from the identity (the default),
-    or FP32 sweeps, re-orthogonalised, then FP64 sweeps (msp_set_svd_mode)."""
-    N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1}[mode]))
+    FP32 sweeps re-orthogonalised then FP64 sweeps, or a pivoted QR first and the
+    sweeps on R^T (msp_set_svd_mode)."""
+    N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1, "qr_preconditioned": 2}[mode]))
 
 
 def precision_code(p) -> int:

@@ -343,6 +343,152 @@ __global__ void newton_schulz_kernel(const SmallMat* mats, double* G) {
 }
 
 
+// Householder QR with column pivoting of T (c x c, column-major; one CTA of 512
+// threads per patch), the preconditioner of the one-sided Jacobi SVD in the
+// manner of Drmac and Veselic (2008): with T P = Q R, the Jacobi sweeps run on
+// the columns of W = R^T, whose rows decay with the pivots, and V starts at Q, so
+// that the rotations J of the sweeps leave V = Q J, the left singular vectors of
+// T (the permutation only acts on the right).  Step j: squared norms of the
+// trailing columns over rows j.. (recomputed, no downdating), the largest swapped
+// into place, the reflector H_j = I - tau v v^T (v_0 = 1) that maps it onto
+// R(j, j) e_0, applied to the trailing columns.  Q = H_0 H_1 ... H_{c-1} is then
+// formed backwards in V.  A lives in shared memory (leading dimension c + 1) when
+// c <= smem_c, else in W, which is overwritten by R^T at the end either way.
+__global__ void __launch_bounds__(512) qrcp_kernel(const SmallMat* mats, const double* Tm, double* W, double* V,
+                                                   int smem_c) {
+    extern __shared__ __align__(16) unsigned char qr_smem[];
+    __shared__ double s_nrm[2 * kJacMaxPairs];
+    __shared__ double s_tau[2 * kJacMaxPairs];
+    __shared__ int s_piv;
+    const SmallMat S = mats[blockIdx.x];
+    const int c = S.c;
+    if (c < 1 || c > 2 * kJacMaxPairs) return;
+    const bool in_smem = c <= smem_c;
+    const int lda = in_smem ? c + 1 : c;
+    double* a = in_smem ? reinterpret_cast<double*>(qr_smem) : W + S.off;
+    double* q = V + S.off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        a[i + (long long)j * lda] = Tm[S.off + e];
+    }
+    __syncthreads();
+    for (int j = 0; j < c; ++j) {
+        // squared norms of columns j.. over rows j..
+        for (int col = j + warp; col < c; col += nw) {
+            const double* ac = a + (long long)col * lda;
+            double t = 0.0;
+            for (int i = j + lane; i < c; i += 32) t = fma(ac[i], ac[i], t);
+            t = warp_sum(t);
+            if (lane == 0) s_nrm[col] = t;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = j;
+            for (int col = j + lane; col < c; col += 32)
+                if (s_nrm[col] > best) { best = s_nrm[col]; bi = col; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) s_piv = bi;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != j) {
+            for (int i = threadIdx.x; i < c; i += blockDim.x) {
+                const double x = a[i + (long long)j * lda];
+                a[i + (long long)j * lda] = a[i + (long long)p * lda];
+                a[i + (long long)p * lda] = x;
+            }
+        }
+        __syncthreads();
+        // reflector of column j: beta = -sign(alpha) |x|, tau = (beta - alpha) / beta,
+        // v = x(1:) / (alpha - beta) below the diagonal, R(j, j) = beta; the squared
+        // norm below the diagonal is summed afresh (a difference of the column norm
+        // and alpha^2 could cancel, and tau must match v for H_j to be orthogonal)
+        double* aj = a + (long long)j * lda;
+        if (warp == 0) {
+            double t = 0.0;
+            for (int i = j + 1 + lane; i < c; i += 32) t = fma(aj[i], aj[i], t);
+            t = warp_sum(t);
+            if (lane == 0) s_nrm[j] = t;
+        }
+        __syncthreads();
+        const double alpha = aj[j];
+        const double xn2 = s_nrm[j];
+        double tau = 0.0, scal = 0.0, beta = alpha;
+        if (xn2 > 0.0) {
+            beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+            tau = (beta - alpha) / beta;
+            scal = 1.0 / (alpha - beta);
+        }
+        __syncthreads();
+        if (tau != 0.0) {
+            for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) aj[i] *= scal;
+        }
+        if (threadIdx.x == 0) {
+            aj[j] = beta;
+            s_tau[j] = tau;
+        }
+        __syncthreads();
+        if (tau != 0.0) {
+            // A(j:, col) -= tau v (v^T A(j:, col)) for the trailing columns, a warp each
+            for (int col = j + 1 + warp; col < c; col += nw) {
+                double* ac = a + (long long)col * lda;
+                double t = (lane == 0) ? ac[j] : 0.0;
+                for (int i = j + 1 + lane; i < c; i += 32) t = fma(aj[i], ac[i], t);
+                t = warp_sum(t) * tau;
+                if (lane == 0) ac[j] -= t;
+                for (int i = j + 1 + lane; i < c; i += 32) ac[i] = fma(-t, aj[i], ac[i]);
+            }
+        }
+        __syncthreads();
+    }
+    // Q = H_0 ... H_{c-1}: from the identity, H_j applied to rows j.. of columns j..
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+        const int i = (int)(e % c), j = (int)(e / c);
+        q[e] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = c - 1; j >= 0; --j) {
+        const double tau = s_tau[j];
+        if (tau != 0.0) {
+            const double* aj = a + (long long)j * lda;
+            for (int col = j + warp; col < c; col += nw) {
+                double* qc = q + (long long)col * c;
+                double t = (lane == 0) ? qc[j] : 0.0;
+                for (int i = j + 1 + lane; i < c; i += 32) t = fma(aj[i], qc[i], t);
+                t = warp_sum(t) * tau;
+                if (lane == 0) qc[j] -= t;
+                for (int i = j + 1 + lane; i < c; i += 32) qc[i] = fma(-t, aj[i], qc[i]);
+            }
+        }
+        __syncthreads();
+    }
+    // W = R^T (lower triangular); in the global case R is read before W is written
+    // over it, column by column of W = row by row of R, through registers
+    if (in_smem) {
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            W[S.off + e] = (i >= j) ? a[j + (long long)i * lda] : 0.0;
+        }
+    } else {
+        // transpose in place: swap (i, j) and (j, i) for i > j, zero the upper part
+        for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
+            const int i = (int)(e % c), j = (int)(e / c);
+            if (i > j) {
+                const double r = a[j + (long long)i * lda];   // R(j, i), upper part
+                a[i + (long long)j * lda] = r;                // W(i, j)
+                a[j + (long long)i * lda] = 0.0;
+            }
+        }
+    }
+}
+
 // Column norms of W = singular values; sort descending (rank by comparison);
 // keep k = #{s_i > tau s_1}.  Writes sigma (sorted), order, k.
 __global__ void sort_truncate_kernel(const SmallMat* mats, const double* W, double tau, double* sig_tmp,
@@ -653,6 +799,18 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
                 gd[m] = GemmDesc{Tacc + mats[m].off, V.p + mats[m].off, W.p + mats[m].off, c, c, c, c, c, c, 1.0, 0.0};
             }
             MSP_TRY(run_gemm(true, maxc, maxc));
+        } else if (svd_qr()) {
+            cudaFuncAttributes fq{};
+            MSP_CUDA(cudaFuncGetAttributes(&fq, qrcp_kernel));
+            const long long dyn_max = (long long)optin - (long long)fq.sharedSizeBytes - 1024;
+            int cq = 0;
+            while ((long long)(cq + 1) * (cq + 2) * (long long)sizeof(double) <= dyn_max) ++cq;
+            cq = std::min(cq, maxc);
+            const size_t smq = (size_t)cq * (cq + 1) * sizeof(double);
+            MSP_CUDA(cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+            qrcp_kernel<<<np, 512, smq, s>>>(d_by_size.p, Tacc, W.p, V.p, cq);
+            count_launches(1);
+            MSP_CUDA(cudaGetLastError());
         } else {
             jacobi_init_kernel<<<np, 256, 0, s>>>(d_mats.p, Tacc, W.p, V.p);
             count_launches(1);

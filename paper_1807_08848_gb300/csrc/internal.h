@@ -105,6 +105,7 @@ msp_status ozaki_check(OzakiWork& w, cudaStream_t s);
 int fp64_gemm_engine();
 // Jacobi SVD of the extraction: FP32 sweeps first, then FP64 (msp_set_svd_mode).
 bool svd_mixed();
+bool svd_qr();
 
 // ------------------------------------------------------------------ geometry
 

@@ -344,19 +344,25 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         if (first && chunk >= 2 && !mbar_wait_or_fail(&accfree[half], (unsigned)(((chunk - 2) >> 1) & 1), fail))
             return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // one thread issues every MMA, so each costs only a few instructions: the
+        // descriptors of slice t / u are the stage's first ones plus a fixed start
+        // offset (the 14-bit start field of an address below 256 KB does not carry)
+        // and the pair loops are unrolled into 36 MMAs with fixed diagonal offsets
+        const unsigned long long da0 = smem_desc(a_stage(st, 0), lbo, sbo);
+        const unsigned long long db0 = smem_desc(b_stage(st, 0), lbo, sbo);
+        const unsigned dh = tmem + (unsigned)(half * (kDiag * kTN));
+        // the first product of diagonal g in a chunk (t = 0 in the chunk's first slab)
+        // overwrites the accumulator; every later one adds to it
+        const unsigned acc0 = first ? 0u : 1u;
+#pragma unroll
         for (int t = 0; t < kSlices; ++t) {
+#pragma unroll
             for (int u = 0; t + u <= kSlices - 1; ++u) {   // t + u (0-based) <= kSlices - 1
-                const int g = t + u;
-                const unsigned d = tmem + (unsigned)(half * (kDiag * kTN) + g * kTN);
 #pragma unroll
                 for (int ks = 0; ks < kSlabK / 16; ++ks) {   // K = 16 per MMA: two core matrices
-                    const unsigned off = ks * 256;
-                    const unsigned long long da = smem_desc(a_stage(st, t) + off, lbo, sbo);
-                    const unsigned long long db = smem_desc(b_stage(st, u) + off, lbo, sbo);
-                    // the first product of diagonal g in a chunk (t = 0, the slab's first K
-                    // step) overwrites the accumulator; every later one adds to it
-                    const unsigned acc = (first && ks == 0 && t == 0) ? 0u : 1u;
-                    mma_bf16(d, da, db, acc);
+                    const unsigned long long da = da0 + (unsigned long long)((t * kAElems * 2 + ks * 256) >> 4);
+                    const unsigned long long db = db0 + (unsigned long long)((u * kBElems * 2 + ks * 256) >> 4);
+                    mma_bf16(dh + (unsigned)((t + u) * kTN), da, db, (t == 0 && ks == 0) ? acc0 : 1u);
                 }
             }
         }

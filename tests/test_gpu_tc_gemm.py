@@ -1,7 +1,8 @@
 """The FP64 products of the extraction on the tensor cores (error-free BF16
 slicing, tcgen05 kind::f16) against the same extraction on the CUDA cores' FP64
 FMA kernels, and both against the oracle; likewise the Jacobi SVD started by
-FP32 sweeps (re-orthogonalised in FP64) against plain FP64 sweeps.
+FP32 sweeps (re-orthogonalised in FP64), or by a pivoted QR, against plain FP64
+sweeps.
 
 The Gram and triangular products of Cholesky-QR and the projection onto the
 singular vectors (Sec. 3.2, Eq. svd; the QR remark of Sec. 3.3) are FP64-accurate
@@ -37,7 +38,8 @@ def extract_both(med, tau, precision, switch="engine"):
     """Two extractions of the same snapshots: (reference setting, setting under
     test) -- CUDA-core vs tensor-core products, or FP64 vs FP32-started Jacobi."""
     set_, ref, new, default = {"engine": (msp.set_gemm_engine, "cuda_cores", "tensor_cores", "tensor_cores"),
-                               "svd": (msp.set_svd_mode, "fp64", "fp32_preconditioned", "fp64")}[switch]
+                               "svd": (msp.set_svd_mode, "fp64", "fp32_preconditioned", "fp64"),
+                               "svd_qr": (msp.set_svd_mode, "fp64", "qr_preconditioned", "fp64")}[switch]
     try:
         set_(ref)
         b_cc = med.extract(tau, precision)
@@ -48,7 +50,7 @@ def extract_both(med, tau, precision, switch="engine"):
     return b_cc, b_tc
 
 
-@pytest.mark.parametrize("switch", ["engine", "svd"])
+@pytest.mark.parametrize("switch", ["engine", "svd", "svd_qr"])
 @pytest.mark.parametrize("case", ["small", "lognormal-256", "ragged"])
 def test_engines_agree_and_match_the_oracle(case, switch):
     if case == "small":
