@@ -175,7 +175,7 @@ msp_status msp_set_gemm_engine(int engine);
 
 /* The SVD of the triangular Cholesky-QR factor T in the extraction (Sec. 3.2,
  * Eq. svd), one-sided Jacobi on the columns of T^T either way:
- *   MSP_SVD_FP64 (default): FP64 sweeps from V = I;
+ *   MSP_SVD_FP64: FP64 sweeps from V = I;
  *   MSP_SVD_FP32_PRECONDITIONED: sweeps in FP32 first (V32 orthogonal to about
  *     1e-6), V re-orthogonalised in FP64 by two Newton-Schulz steps
  *     V (3 I - V^T V) / 2, then FP64 sweeps on T^T V to the FP64 convergence
@@ -184,10 +184,12 @@ msp_status msp_set_gemm_engine(int engine);
  *     workloads keep most of their columns below that, so the FP64 sweeps still
  *     need nearly as many sweeps (measured at 2049^2: 283 ms of FP64 sweeps after
  *     71 ms of FP32 start, against 371 ms from V = I);
- *   MSP_SVD_QR_PRECONDITIONED: Householder QR with column pivoting T P = Q R in
- *     FP64 first (Drmac and Veselic 2008), then FP64 sweeps on the columns of
- *     R^T with V started at Q: the rows of R decay with the pivots, so the
- *     sweeps start from graded, nearly orthogonal columns.
+ *   MSP_SVD_QR_PRECONDITIONED (default): Householder QR with column pivoting
+ *     T P = Q R in FP64 first (Drmac and Veselic 2008), then FP64 sweeps on the
+ *     columns of R^T with V started at Q: the rows of R decay with the pivots,
+ *     so the sweeps start from graded, nearly orthogonal columns (measured at
+ *     2049^2: 37 ms of QR and 228 ms of sweeps, at most 10 and 6.3 on average,
+ *     against 370 ms and 20 / 8.1 sweeps from V = I).
  * Both end at the same FP64 stopping test; process-wide, read by every
  * extraction.  INVALID_ARG on an unknown mode. */
 #define MSP_SVD_FP64                0

@@ -45,10 +45,10 @@ def set_gemm_engine(engine: str = "tensor_cores"):
     N.check(N.load().msp_set_gemm_engine({"tensor_cores": 0, "cuda_cores": 1}[engine]))
 
 
-def set_svd_mode(mode: str = "fp64"):
-    """Jacobi SVD of the extraction: FP64 sweeps from the identity (the default),
-    FP32 sweeps re-orthogonalised then FP64 sweeps, or a pivoted QR first and the
-    sweeps on R^T (msp_set_svd_mode)."""
+def set_svd_mode(mode: str = "qr_preconditioned"):
+    """Jacobi SVD of the extraction: a pivoted QR first and the FP64 sweeps on R^T
+    (the default), FP64 sweeps from the identity, or FP32 sweeps re-orthogonalised
+    then FP64 sweeps (msp_set_svd_mode)."""
     N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1, "qr_preconditioned": 2}[mode]))
 
 

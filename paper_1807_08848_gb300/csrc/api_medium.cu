@@ -33,7 +33,7 @@ msp_status phase_mark(std::vector<cudaEvent_t>* marks, cudaStream_t s) {
 // Engine of the FP64 products of the extraction and the online factorisation.
 static std::atomic<int> g_gemm_engine{0};
 int fp64_gemm_engine() { return g_gemm_engine.load(std::memory_order_relaxed); }
-static std::atomic<int> g_svd_mode{MSP_SVD_FP64};
+static std::atomic<int> g_svd_mode{MSP_SVD_QR_PRECONDITIONED};
 bool svd_mixed() { return g_svd_mode.load(std::memory_order_relaxed) == MSP_SVD_FP32_PRECONDITIONED; }
 bool svd_qr() { return g_svd_mode.load(std::memory_order_relaxed) == MSP_SVD_QR_PRECONDITIONED; }
 

@@ -22,10 +22,10 @@
 //
 // Structure flags of the descriptors (zero ranges of op(A) or op(B)) are applied
 // while slicing: those entries become zero slices whatever the memory holds.
-// Layout of a sliced operand: [slice][row tile][K slab of 16][row group of 8]
+// Layout of a sliced operand: [row tile][K slab of 16][slice][row group of 8]
 // [k core of 8][row][k], BF16 -- the no-swizzle K-major layout of the MMA, 16-byte
-// core matrices, K-adjacent cores 128 B apart, 8-row groups 256 B apart; one
-// (slice, row tile, slab) block is contiguous and moves with one bulk copy.
+// core matrices, K-adjacent cores 128 B apart, 8-row groups 256 B apart; the
+// kSlices blocks of one (row tile, slab) are contiguous and move with one bulk copy.
 //
 // MMA kernel: one CTA of 256 threads per 128 x 32 output tile of one product.
 // Thread 0 issues the bulk copies (five stages of 40 KB: 8 A slices of 128 x 16
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, co
     const int* se = scale_exp + (IS_B ? E.b_sc : E.a_sc);
     // per_slice < 2^31 (checked on the host): the tiled index fits 32 bits
     const unsigned slabs_u = (unsigned)E.slabs;
+    const unsigned blk = (unsigned)(RT * kSlabK);   // one (tile, slab) block of one slice
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)per_slice; e += gridDim.x * blockDim.x) {
         // e = [tile][slab][row group][k core][row][k]
         const int kk = (int)(e & 7);
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const GemmDesc* descs, co
 #pragma unroll
         for (int t = 0; t < kSlices; ++t) {
             const int d = (int)((F >> (kSlices * kBeta - kBeta * (t + 1))) & ((1u << kBeta) - 1u));
-            out[base + (long long)t * per_slice + e] = __float2bfloat16_rn((float)(neg ? -d : d));
+            out[base + ((long long)(e / blk) * kSlices + t) * blk + (e % blk)] = __float2bfloat16_rn((float)(neg ? -d : d));
         }
     }
 }
@@ -310,10 +311,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     volatile int* fail = &s_fail;
     const int slabs = E.slabs;
     const int chunks = (slabs + kChunkSlabs - 1) / kChunkSlabs;
-    const long long a_ps = (long long)E.rta * slabs * kAElems;     // elements per A slice
-    const long long b_ps = (long long)E.rtb * slabs * kBElems;
-    const __nv_bfloat16* a0 = A.slices + E.a_sl + (long long)tm * slabs * kAElems;
-    const __nv_bfloat16* b0 = A.slices + E.b_sl + (long long)tn * slabs * kBElems;
+    // the kSlices blocks of one (tile, slab) lie back to back: one bulk copy each
+    // for A and B per stage
+    const __nv_bfloat16* a0 = A.slices + E.a_sl + (long long)tm * slabs * kSlices * kAElems;
+    const __nv_bfloat16* b0 = A.slices + E.b_sl + (long long)tn * slabs * kSlices * kBElems;
     unsigned char* stage0 = oz_smem;
     auto a_stage = [&](int st, int t) { return stage0 + (size_t)st * kStageBytes + (size_t)t * kAElems * 2; };
     auto b_stage = [&](int st, int u) {
@@ -325,10 +326,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         const int st = slab % kStages;
         last_copy[st] = slab;
         mbar_expect_tx(&full[st], kStageBytes);
-        for (int t = 0; t < kSlices; ++t)
-            bulk_g2s(a_stage(st, t), a0 + t * a_ps + (long long)slab * kAElems, kAElems * 2, &full[st]);
-        for (int u = 0; u < kSlices; ++u)
-            bulk_g2s(b_stage(st, u), b0 + u * b_ps + (long long)slab * kBElems, kBElems * 2, &full[st]);
+        bulk_g2s(a_stage(st, 0), a0 + (long long)slab * kSlices * kAElems, kSlices * kAElems * 2, &full[st]);
+        bulk_g2s(b_stage(st, 0), b0 + (long long)slab * kSlices * kBElems, kSlices * kBElems * 2, &full[st]);
     };
     const unsigned lbo = 128, sbo = kCoresK * 128;   // K-adjacent cores, 8-row groups
     int last_commit[2] = {-1, -1};   // thread 0: last chunk committed to each accumulator half
@@ -417,10 +416,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     // every copy this CTA will issue lies inside the slice buffer: checked once,
     // before the first copy (a bad table entry fails the CTA instead of copying)
     if (tid == 0) {
-        const long long a_lo = E.a_sl + (long long)tm * slabs * kAElems;
-        const long long a_hi = a_lo + (long long)(kSlices - 1) * a_ps + (long long)slabs * kAElems;
-        const long long b_lo = E.b_sl + (long long)tn * slabs * kBElems;
-        const long long b_hi = b_lo + (long long)(kSlices - 1) * b_ps + (long long)slabs * kBElems;
+        const long long a_lo = E.a_sl + (long long)tm * slabs * kSlices * kAElems;
+        const long long a_hi = a_lo + (long long)slabs * kSlices * kAElems;
+        const long long b_lo = E.b_sl + (long long)tn * slabs * kSlices * kBElems;
+        const long long b_hi = b_lo + (long long)slabs * kSlices * kBElems;
         if (a_lo < 0 || b_lo < 0 || a_hi > A.n_slices || b_hi > A.n_slices || tm >= E.rta || tn >= E.rtb) *fail = 1;
     }
     __syncthreads();

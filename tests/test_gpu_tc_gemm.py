@@ -38,8 +38,8 @@ def extract_both(med, tau, precision, switch="engine"):
     """Two extractions of the same snapshots: (reference setting, setting under
     test) -- CUDA-core vs tensor-core products, or FP64 vs FP32-started Jacobi."""
     set_, ref, new, default = {"engine": (msp.set_gemm_engine, "cuda_cores", "tensor_cores", "tensor_cores"),
-                               "svd": (msp.set_svd_mode, "fp64", "fp32_preconditioned", "fp64"),
-                               "svd_qr": (msp.set_svd_mode, "fp64", "qr_preconditioned", "fp64")}[switch]
+                               "svd": (msp.set_svd_mode, "fp64", "fp32_preconditioned", "qr_preconditioned"),
+                               "svd_qr": (msp.set_svd_mode, "fp64", "qr_preconditioned", "qr_preconditioned")}[switch]
     try:
         set_(ref)
         b_cc = med.extract(tau, precision)
