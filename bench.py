@@ -791,6 +791,7 @@ def run_extract(args):
         out["svd_" + mode] = {"phases_ms": b.extract_timing(), "max_jacobi_sweeps": b.stats()["max_jacobi_sweeps"],
                               "mean_jacobi_sweeps": b.stats()["mean_jacobi_sweeps"]}
         bases["svd_" + mode] = b
+    msp.set_svd_mode()
     msp.set_extract_timing(False)
     b64 = bases["svd_fp64"]
     for mode in ("fp32_preconditioned", "qr_preconditioned"):
