@@ -854,6 +854,44 @@ def run_uneven(args):
     print(json.dumps(out), flush=True)
 
 
+def run_step_case(args):
+    """Only the headline step (new medium, local solves, extraction, one online
+    solve) of the 2049^2 workload, --warmup then --steps times, CUDA events per
+    step: the command of the step's launch list (nothing else launches)."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    from paper_1807_08848_gb300 import _native
+    torch.cuda.set_device(0)
+    w = synth.workload_batched()
+    stream = torch.cuda.current_stream()
+    phi = torch.tensor(w["phi"], dtype=torch.float64).reshape(1, -1).cuda()
+    direct = args.precision == "mixed" and args.local_solver == "direct"
+
+    def step():
+        med = msp.Medium(w["medium"], w["patches"])
+        if direct:
+            med.set_launch("mixed", "direct")
+        med.sample(w["seed"], args.precision, tol=1e-10, max_iter=20000, stats=False)
+        basis = med.extract(w["tau"], args.precision)
+        try:
+            basis.solve(phi, tol=w["online_tol"], max_iter=args.online_iters, want_iters=False)
+        except _native.MspError as e:
+            if e.status != _native.MSP_ERR_NOT_CONVERGED:
+                raise
+
+    for _ in range(args.warmup):
+        step()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": "step-2049", "ms_per_step": ms}), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1807_08848_gb300 as msp
@@ -1198,7 +1236,7 @@ def main():
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic",
+    ap.add_argument("--case", default="full", choices=["full", "step", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic",
                                                       "direct", "extract"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
@@ -1209,6 +1247,9 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-mem-gb", type=float, default=16.0)
     args = ap.parse_args()
+    if args.case == "step":
+        run_step_case(args)
+        return
     if args.case == "profile513":
         run_profile_case(args)
         return
