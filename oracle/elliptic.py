@@ -24,6 +24,8 @@ Pipeline, in the order of Algorithm alg:summary:
     sigma_i > tau sigma_1 (Sec. 3.2, Eq. svd)         `basis`
   value / flux / boundary rows (Eq. elliptic_cond_tilde)
     and c = argmin |P c - d| (Eq. elliptic_cond_reduced)  `online_system`, `online_solve`
+  the constrained variant: boundary rows exact, continuity
+    rows in the least-squares sense                   `constrained_solve`
   u = sum_m G_m c_m with a partition of unity          `reconstruct`
 Direct solvers replace every iteration of the GPU path.
 """
@@ -316,6 +318,13 @@ def domain_ring_index(N):
 
 
 def online_system(aE, aN, patches, Qs, N, pspec, phi):
+    """P~, d and the coefficient offsets of Eq. elliptic_cond_reduced (see
+    `online_system_rows`, which also marks the boundary rows)."""
+    Pm, d, off, _ = online_system_rows(aE, aN, patches, Qs, N, pspec, phi)
+    return Pm, d, off
+
+
+def online_system_rows(aE, aN, patches, Qs, N, pspec, phi):
     """Assemble P~ (sparse, rows x N_p) and d for Eq. elliptic_cond_reduced.
 
     Rows, node by node over the patch skeleton (readings R6-R8):
@@ -323,7 +332,8 @@ def online_system(aE, aN, patches, Qs, N, pspec, phi):
       * otherwise, with m_1 < ... < m_r the patches holding x:
         value rows u_{m_1}(x) - u_{m_j}(x) = 0 (j = 2..r) and one flux row
         sum_j F_{m_j}(x) = 0.
-    Returns (P, d, offsets) with offsets[m] the first column of c_m."""
+    Returns (P, d, offsets, is_boundary_row) with offsets[m] the first column
+    of c_m."""
     xb, yb = list(map(int, pspec.x_breaks)), list(map(int, pspec.y_breaks))
     ks = [Q.shape[1] for Q in Qs]
     off = np.concatenate([[0], np.cumsum(ks)]).astype(int)
@@ -336,7 +346,7 @@ def online_system(aE, aN, patches, Qs, N, pspec, phi):
     mx = len(xb) - 1
     # skeleton nodes in row-major order
     skel = sorted({(i, j) for (_, i, j) in rows}, key=lambda ij: (ij[1], ij[0]))
-    r_i, c_i, v_i, d = [], [], [], []
+    r_i, c_i, v_i, d, bnd = [], [], [], [], []
     nrow = 0
 
     def put(m, vec, sign):
@@ -350,17 +360,17 @@ def online_system(aE, aN, patches, Qs, N, pspec, phi):
         if i in (0, N) or j in (0, N):
             for m in ms:
                 put(m, rows[(m, i, j)][0], 1.0)
-                d.append(phi[ring_id[(i, j)]]); nrow += 1
+                d.append(phi[ring_id[(i, j)]]); bnd.append(True); nrow += 1
         else:
             for m in ms[1:]:
                 put(ms[0], rows[(ms[0], i, j)][0], 1.0)
                 put(m, rows[(m, i, j)][0], -1.0)
-                d.append(0.0); nrow += 1
+                d.append(0.0); bnd.append(False); nrow += 1
             for m in ms:
                 put(m, rows[(m, i, j)][1], 1.0)
-            d.append(0.0); nrow += 1
+            d.append(0.0); bnd.append(False); nrow += 1
     Pm = sp.csr_matrix((v_i, (r_i, c_i)), shape=(nrow, off[-1]))
-    return Pm, np.array(d), off
+    return Pm, np.array(d), off, np.array(bnd, dtype=bool)
 
 
 def online_solve(Pm, d, dense_limit=4e7):
@@ -376,6 +386,25 @@ def online_solve(Pm, d, dense_limit=4e7):
     c = lu.solve(Pm.T @ d)
     r = d - Pm @ c
     return c + lu.solve(Pm.T @ r)
+
+
+def constrained_solve(Pm, d, is_bnd, rank_tol=1e-12):
+    """The constrained least-squares variant of the online step (the remark
+    after Eq. elliptic_cond_reduced): minimise the continuity rows |C c|_2 subject
+    to the boundary rows B c = phi exactly, by the null-space method (Golub and
+    Van Loan, Sec. 6.2): with the SVD B = U S V^T of rank r (singular values above
+    rank_tol s_1), c = c_p + N z where c_p = V_r S_r^{-1} U_r^T phi is the
+    minimum-norm solution of the constraints, N = V[:, r:] spans null(B), and
+    z = argmin |C N z + C c_p|_2.  Dense; for the sizes the tests use."""
+    B = Pm[is_bnd].toarray()
+    C = Pm[~is_bnd].toarray()
+    f = d[is_bnd]
+    U, s, Vt = np.linalg.svd(B, full_matrices=True)
+    r = int(np.sum(s > rank_tol * s[0])) if s.size else 0
+    c_p = Vt[:r].T @ ((U[:, :r].T @ f) / s[:r])
+    Nn = Vt[r:].T
+    z, *_ = np.linalg.lstsq(C @ Nn, -(C @ c_p), rcond=None)
+    return c_p + Nn @ z
 
 
 def reconstruct(patches, Qs, c, off, N, phi):
@@ -436,3 +465,11 @@ def online(off: Offline, pspec, N, phi):
     Pm, d, o = online_system(off.aE, off.aN, off.patches, off.Q, N, pspec, phi)
     c = online_solve(Pm, d)
     return reconstruct(off.patches, off.Q, c, o, N, phi), c, Pm, d
+
+
+def online_constrained(off: Offline, pspec, N, phi):
+    """Online stage with the boundary data imposed exactly and only the
+    continuity conditions relaxed (the constrained least-squares variant)."""
+    Pm, d, o, is_bnd = online_system_rows(off.aE, off.aN, off.patches, off.Q, N, pspec, phi)
+    c = constrained_solve(Pm, d, is_bnd)
+    return reconstruct(off.patches, off.Q, c, o, N, phi), c, Pm, d, is_bnd

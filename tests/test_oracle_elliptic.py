@@ -392,3 +392,55 @@ def test_small_workload_method_accuracy():
     u, *_ = E.online(off, w["patches"], 128, w["phi"])
     err = E.rel_l2(u, E.global_reference(off.aE, off.aN, 128, w["phi"]))
     assert err < 5e-3
+
+
+# ------------------------------------------ constrained least-squares variant
+
+@pytest.mark.parametrize("grid", [(32, 2, 2, 4, synth.periodic_sin(32, 1 / 4)),
+                                  (36, 3, 3, 3, synth.hou_wu(36, 1 / 4))])
+def test_constrained_full_basis_reproduces_global_solve(grid):
+    """With full local spaces the global solution meets every boundary row and
+    every continuity row, so it is the constrained minimiser too: the
+    constrained variant reproduces the fine-mesh solution."""
+    N, mx, my, b, ms = grid
+    ring = max(2 * (N // mx + 2 * b) + 2 * (N // my + 2 * b), 1)
+    ps = synth.uniform_patches(N, mx, my, b, ring + 8)
+    off = E.offline(ms, ps, 3, 1e-13)
+    phi = synth.phi_fourier(N, 6, 9, kmax=3)[0]
+    u, c, Pm, d, bnd = E.online_constrained(off, ps, N, phi)
+    assert E.rel_l2(u, E.global_reference(off.aE, off.aN, N, phi)) < 1e-10
+
+
+def test_constrained_solution_is_the_weighted_limit():
+    """An independent route to the same point: the weighted least squares
+    min |C c|^2 + w^2 |B c - phi|^2 tends to the constrained solution as w grows
+    (the method of weighting; the gap shrinks like 1/w^2).  On the small
+    workload's truncated bases: the boundary rows hold to rounding, the weighted
+    solutions approach the constrained one, and the continuity residual is no
+    larger than that of any weighted solution (it is the least among the
+    solutions that meet the boundary rows)."""
+    w = synth.workload_small()
+    off = E.offline(w["medium"], w["patches"], w["seed"], w["tau"])
+    Pm, d, o, bnd = E.online_system_rows(off.aE, off.aN, off.patches, off.Q, 128, w["patches"], w["phi"])
+    c = E.constrained_solve(Pm, d, bnd)
+    B, C, f = Pm[bnd].toarray(), Pm[~bnd].toarray(), d[bnd]
+    assert np.linalg.norm(B @ c - f) <= 1e-10 * np.linalg.norm(f)
+    gaps = []
+    for wt in (1e2, 1e3, 1e4):
+        cw, *_ = np.linalg.lstsq(np.vstack([C, wt * B]), np.concatenate([np.zeros(C.shape[0]), wt * f]), rcond=None)
+        gaps.append(np.linalg.norm(cw - c) / np.linalg.norm(c))
+    assert gaps[2] < 1e-5 and gaps[1] < gaps[0] and gaps[2] < gaps[1]
+    # the unconstrained LS trades boundary error for continuity: its continuity
+    # residual is smaller, its boundary residual larger
+    cu = E.online_solve(Pm, d)
+    assert np.linalg.norm(C @ cu) <= np.linalg.norm(C @ c) + 1e-12
+    assert np.linalg.norm(B @ cu - f) >= np.linalg.norm(B @ c - f)
+
+
+def test_constrained_small_workload_accuracy():
+    """The constrained variant on the small workload solves the global problem
+    to the same order as the least-squares glue (a method check)."""
+    w = synth.workload_small()
+    off = E.offline(w["medium"], w["patches"], w["seed"], w["tau"])
+    u, *_ = E.online_constrained(off, w["patches"], 128, w["phi"])
+    assert E.rel_l2(u, E.global_reference(off.aE, off.aN, 128, w["phi"])) < 5e-3
