@@ -461,6 +461,23 @@ msp_status msp_medium_set_graph(msp_medium m, int enable);
 msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
                             double* u_dev, double* c_dev, int* iters_host, void* stream);
 
+/* The constrained least-squares variant of the online stage (the remark after
+ * Eq. elliptic_cond_reduced): the boundary rows u_m(x) = phi(x) on the domain
+ * boundary hold exactly, the continuity rows are solved in the least-squares
+ * sense.  The boundary rows of a patch involve only its own coefficients, so
+ * they are eliminated patch by patch (null-space method: pivoted Householder QR
+ * of B_m^T, c_m = Z_m phi_m + N_m z_m with the minimum-norm particular part) and
+ * the reduced unknowns z go through the same preconditioned FP64 CGLS on a
+ * derived basis (bases Q_m N_m, continuity rows only), built on the first call
+ * and kept with the basis (synchronises; its factorisation costs about as much
+ * as the extraction's).  Arguments, layouts, stopping rule and return codes as
+ * msp_online_solve; c_dev receives the full coefficients c.  BREAKDOWN when a
+ * boundary patch keeps fewer basis vectors than it has domain-boundary nodes, or
+ * their boundary rows are not independent to working accuracy (|R_jj| <= 1e-12
+ * |R_00| in the pivoted QR): the data cannot be imposed exactly there. */
+msp_status msp_online_solve_constrained(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
+                                        double* u_dev, double* c_dev, int* iters_host, void* stream);
+
 /* Boundary-to-coefficient map.  The data of Eq. elliptic_cond_reduced enter only
  * through the boundary rows, linearly, so c = G phi with G = P~^+ S (N_p x 4N; S
  * places the ring values phi into the boundary rows).  msp_basis_build_map

@@ -315,8 +315,12 @@ class Basis:
         return t.T
 
     def solve(self, phi: torch.Tensor, tol: float = 1e-10, max_iter: int = 5000, stream=None,
-              want_c: bool = False, want_iters: bool = True, u: torch.Tensor | None = None):
-        """Online solve for phi of shape (B, 4N) (or (4N,)) on the device."""
+              want_c: bool = False, want_iters: bool = True, u: torch.Tensor | None = None,
+              constrained: bool = False):
+        """Online solve for phi of shape (B, 4N) (or (4N,)) on the device: the
+        least-squares glue (msp_online_solve), or with constrained=True the
+        variant that imposes the boundary data exactly
+        (msp_online_solve_constrained)."""
         squeeze = phi.dim() == 1
         phi = phi.reshape(-1, 4 * self.n_cells).to(dtype=torch.float64, device="cuda").contiguous()
         B = phi.shape[0]
@@ -325,8 +329,9 @@ class Basis:
             u = torch.empty((B, n, n), dtype=torch.float64, device="cuda")
         c = torch.empty((B, self.n_unknowns), dtype=torch.float64, device="cuda") if want_c else None
         iters = (C.c_int * B)() if want_iters else None
-        code = N.load().msp_online_solve(self._h, _dptr(phi), B, tol, max_iter, _dptr(u),
-                                         _dptr(c) if c is not None else None, iters, _stream_ptr(stream))
+        fn = N.load().msp_online_solve_constrained if constrained else N.load().msp_online_solve
+        code = fn(self._h, _dptr(phi), B, tol, max_iter, _dptr(u), _dptr(c) if c is not None else None, iters,
+                  _stream_ptr(stream))
         N.check(code)
         it = np.array(list(iters), dtype=np.int64) if want_iters else None
         if squeeze:

@@ -607,14 +607,16 @@ __global__ void precond_inverse_kernel(const SmallMat* mats, const double* Fi, c
     }
 }
 
+}  // namespace
+
+// position of domain-boundary node (i, j) on the global ring (counter-clockwise
+// from (0, 0)), the index of its value in phi
 int domain_ring_pos(int N, int i, int j) {
     if (j == 0 && i < N) return i;
     if (i == N && j < N) return N + j;
     if (j == N && i > 0) return 2 * N + (N - i);
     return 3 * N + (N - j);
 }
-
-}  // namespace
 
 // Orthonormal bases of the snapshot blocks (n_rows[m] x cols[m], column-major at
 // snaps + snap_off[m]): shifted Cholesky-QR3, SVD of the triangular factor,
@@ -966,6 +968,7 @@ msp_status finish_basis(Basis& B, const double* aE_dev, const double* aN_dev, cu
         sk_node.push_back(j * (N + 1) + i);
         sk_ring.push_back(bnd ? domain_ring_pos(N, i, j) : -1);
         if (bnd) {
+            if (B.no_boundary_rows) continue;   // constrained variant: the boundary data hold exactly
             for (auto& mt : lst) {
                 row_slot.push_back(B.slot_off[mt.first] + 2 * mt.second);
                 row_ptr.push_back((int)row_slot.size());

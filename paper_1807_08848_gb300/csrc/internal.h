@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/msp.h"
@@ -265,7 +266,31 @@ struct Basis {
     int max_jacobi_sweeps = 0, max_cholqr_tries = 0;
     float mean_jacobi_sweeps = 0.f;
     int device = 0;
+    // constrained least-squares variant of the online step: the derived basis and
+    // tables, built on first use (online_constrained.cu); a derived basis has no
+    // boundary rows
+    bool no_boundary_rows = false;
+    std::shared_ptr<struct ConstrainedOnline> cons;
 };
+
+// Boundary data imposed exactly: per boundary patch c_m = Z_m phi_m + N_m z_m
+// (null-space method), the reduced problem on the derived basis `red`.
+struct ConstrainedOnline {
+    std::unique_ptr<Basis> red;          // bases Q_m N_m (boundary patches) / Q_m, continuity rows only
+    std::vector<int> nb;                 // domain-boundary nodes of each K_m (0 inside)
+    DevBuf<int> d_nb, d_bring, d_kr, d_cr_off;
+    DevBuf<long long> d_bring_off, d_zp_off, d_np_off;
+    DevBuf<double> Z, Nm;                // per boundary patch: k_m x nb_m and k_m x (k_m - nb_m), column-major
+    DevBuf<double> cp, cf, ep, dq, part; // work: [coefficient][B], [coefficient][B], [slot][B], [row][B], partials
+    int cap = 0;
+};
+msp_status build_constrained(Basis& B, cudaStream_t s);
+void cons_particular(const Basis& B, const ConstrainedOnline& C, const double* phi, int n4, int Bsz, double* cp,
+                     cudaStream_t s);
+void cons_combine(const Basis& B, const ConstrainedOnline& C, const double* cp, const double* z, int Bsz, double* cf,
+                  cudaStream_t s);
+msp_status online_solve_constrained(Basis& B, const double* phi, int batch, double tol, int max_iter, double* u,
+                                    double* c_out, int* iters_host, cudaStream_t s);
 
 // ------------------------------------------------------------------ launchers
 namespace gpath {

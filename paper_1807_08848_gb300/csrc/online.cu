@@ -67,11 +67,13 @@ __device__ __forceinline__ double row_value(const OnArgs& A, const double* e, in
 }
 
 // q = P~ x (from the edge values e), per-chunk partial sums of q.q.  If init
-// is set, r = d - q instead (d from the boundary data phi), and partials hold
-// nothing.  Rows of a chunk are reduced warp by warp, then the four warp sums in
-// order: the order does not depend on the batch size.
+// is set, r = d - q instead (d from the boundary data phi, less dsub[row][b] when
+// dsub is given), and partials hold nothing.  Rows of a chunk are reduced warp by
+// warp, then the four warp sums in order: the order does not depend on the batch
+// size.
 __global__ void __launch_bounds__(kRowChunk) rows_apply_kernel(OnArgs A, const double* e, double* q, double* part,
-                                                               const double* phi, int n4, double* r, int init) {
+                                                               const double* phi, int n4, double* r, int init,
+                                                               const double* dsub = nullptr) {
     __shared__ double sw[kRowChunk / 32][kMaxBatch];
     const int r0 = blockIdx.x * kRowChunk, B = A.B;
     const int row = r0 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -81,7 +83,8 @@ __global__ void __launch_bounds__(kRowChunk) rows_apply_kernel(OnArgs A, const d
             v = row_value(A, e, row, b);
             if (init) {
                 const int rb = A.row_bnd[row];
-                const double d = rb >= 0 ? phi[(long long)b * n4 + rb] : 0.0;
+                double d = rb >= 0 ? phi[(long long)b * n4 + rb] : 0.0;
+                if (dsub) d -= dsub[(long long)row * B + b];
                 r[(long long)row * B + b] = d - v;
                 v = 0.0;
             } else {
@@ -454,9 +457,27 @@ static OnArgs make_args(const Basis& Bs, int B) {
     return A;
 }
 
+// reconstruction u = sum_m chi_m Q_m c_m (interior of the patches, then the
+// skeleton from the edge values, phi on the domain boundary) for coefficients c
+// in the [coefficient][B] layout; e is scratch of n_slots x B
+static void reconstruct(const Basis& Bs, const OnArgs& A, const double* c, double* e, const double* phi, int n4,
+                        double* u, cudaStream_t s) {
+    const int np = (int)Bs.patches.size(), N = Bs.N, B = A.B;
+    recon_interior_kernel<double, double><<<np, 256, 0, s>>>(A, Bs.d_patches.p, Bs.d_q_off.p, Bs.Q.p, c, u, N);
+    count_launches(1);
+    edge_apply_kernel<<<np, 256, 0, s>>>(A, c, e);
+    count_launches(1);
+    const int sk_grid = std::max(1, std::min<int>((int)(((long long)Bs.n_skel * B + 255) / 256), num_sms() * 8));
+    recon_skeleton_kernel<<<sk_grid, 256, 0, s>>>(A, Bs.n_skel, Bs.sk_ptr.p, Bs.sk_slot.p, Bs.sk_node.p, Bs.sk_ring.p,
+                                                  e, phi, n4, u, N);
+    count_launches(1);
+}
+
+// One batch of CGLS.  dsub (optional, [row][B]) is subtracted from the right-hand
+// side d of the rows (the constrained variant's continuity rows carry -P c_p).
 static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, int max_iter, double* u,
                                double* c_out, int* iters_host, cudaStream_t s, bool* not_conv,
-                               bool* nonfinite = nullptr) {
+                               bool* nonfinite = nullptr, const double* dsub = nullptr) {
     const int np = (int)Bs.patches.size();
     const int N = Bs.N, n4 = 4 * N;
     OnArgs A = make_args(Bs, B);
@@ -503,7 +524,7 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
     MSP_CUDA(cudaMemsetAsync(Bs.w_c.p, 0, sizeof(double) * nc, s));
     MSP_CUDA(cudaMemsetAsync(Bs.w_e.p, 0, sizeof(double) * (size_t)Bs.n_slots * B, s));
     // r = d
-    rows_apply_kernel<<<A.n_chunks, kRowChunk, 0, s>>>(A, Bs.w_e.p, Bs.w_q.p, Bs.w_part.p, phi, n4, Bs.w_r.p, 1);
+    rows_apply_kernel<<<A.n_chunks, kRowChunk, 0, s>>>(A, Bs.w_e.p, Bs.w_q.p, Bs.w_part.p, phi, n4, Bs.w_r.p, 1, dsub);
     count_launches(1);
     MSP_TRY(precondition());
     finalize_beta_kernel<<<1, 1024, 0, s>>>(A, Bs.w_part.p, Bs.w_scal.p, tol, max_iter, 0);
@@ -551,16 +572,7 @@ static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, 
     }
     // reconstruction (skipped when only the coefficients are asked for)
     const long long nn = (long long)(N + 1) * (N + 1);
-    if (u) {
-    recon_interior_kernel<double, double><<<np, 256, 0, s>>>(A, Bs.d_patches.p, Bs.d_q_off.p, Bs.Q.p, Bs.w_c.p, u, N);
-    count_launches(1);
-    edge_apply_kernel<<<np, 256, 0, s>>>(A, Bs.w_c.p, Bs.w_e.p);
-    count_launches(1);
-    const int sk_grid = std::max(1, std::min<int>((int)(((long long)Bs.n_skel * B + 255) / 256), num_sms() * 8));
-    recon_skeleton_kernel<<<sk_grid, 256, 0, s>>>(A, Bs.n_skel, Bs.sk_ptr.p, Bs.sk_slot.p, Bs.sk_node.p, Bs.sk_ring.p,
-                                                  Bs.w_e.p, phi, n4, u, N);
-    count_launches(1);
-    }
+    if (u) reconstruct(Bs, A, Bs.w_c.p, Bs.w_e.p, phi, n4, u, s);
     if (c_out) {
         export_c_kernel<<<ew_grid, 256, 0, s>>>(Bs.w_c.p, c_out, Bs.Np, B);
         count_launches(1);
@@ -603,6 +615,60 @@ msp_status online_solve(Basis& Bs, const double* phi, int batch, double tol, int
     }
     if (not_conv) {
         set_error("msp_online_solve: some data sets stopped at max_iter");
+        return MSP_ERR_NOT_CONVERGED;
+    }
+    return MSP_OK;
+}
+
+// The constrained least-squares variant (online_constrained.cu): per batch, the
+// particular coefficients c_p = Z phi, their continuity residual q_p = P' (E c_p)
+// on the derived basis's rows, CGLS on the derived basis for min |P' z + q_p|,
+// then c = c_p + N z and the reconstruction with the original bases.
+msp_status online_solve_constrained(Basis& Bs, const double* phi, int batch, double tol, int max_iter, double* u,
+                                    double* c_out, int* iters_host, cudaStream_t s) {
+    if (!Bs.cons) MSP_TRY(build_constrained(Bs, s));
+    ConstrainedOnline& C = *Bs.cons;
+    Basis& R = *C.red;
+    const int np = (int)Bs.patches.size(), N = Bs.N, n4 = 4 * N;
+    const long long nn = (long long)(N + 1) * (N + 1);
+    if (C.cap < kMaxBatch) {
+        const int cb = kMaxBatch;
+        MSP_TRY(C.cp.alloc((size_t)std::max(Bs.Np, 1) * cb, s));
+        MSP_TRY(C.cf.alloc((size_t)std::max(Bs.Np, 1) * cb, s));
+        MSP_TRY(C.ep.alloc((size_t)std::max(Bs.n_slots, 1) * cb, s));
+        MSP_TRY(C.dq.alloc((size_t)std::max(R.n_rows, 1) * cb, s));
+        MSP_TRY(C.part.alloc((size_t)std::max((R.n_rows + kRowChunk - 1) / kRowChunk, 1) * cb, s));
+        C.cap = cb;
+    }
+    const int cap = std::min(online_batch_cap(Bs), online_batch_cap(R));
+    bool not_conv = false, nonfinite = false;
+    for (int b0 = 0; b0 < batch; b0 += cap) {
+        const int B = std::min(cap, batch - b0);
+        const double* ph = phi + (long long)b0 * n4;
+        const OnArgs AB = make_args(Bs, B), AR = make_args(R, B);
+        cons_particular(Bs, C, ph, n4, B, C.cp.p, s);
+        edge_apply_kernel<<<np, 256, 0, s>>>(AB, C.cp.p, C.ep.p);
+        count_launches(1);
+        rows_apply_kernel<<<AR.n_chunks, kRowChunk, 0, s>>>(AR, C.ep.p, C.dq.p, C.part.p, ph, n4, nullptr, 0);
+        count_launches(1);
+        MSP_CUDA(cudaGetLastError());
+        MSP_TRY(online_batch(R, ph, B, tol, max_iter, nullptr, nullptr, iters_host ? iters_host + b0 : nullptr, s,
+                             &not_conv, &nonfinite, C.dq.p));
+        cons_combine(Bs, C, C.cp.p, R.w_c.p, B, C.cf.p, s);
+        if (u) reconstruct(Bs, AB, C.cf.p, C.ep.p, ph, n4, u + (long long)b0 * nn, s);
+        if (c_out) {
+            const int ew_grid = std::max(1, std::min<int>((int)(((long long)Bs.Np * B + 255) / 256), num_sms() * 8));
+            export_c_kernel<<<ew_grid, 256, 0, s>>>(C.cf.p, c_out + (long long)b0 * Bs.Np, Bs.Np, B);
+            count_launches(1);
+        }
+        MSP_CUDA(cudaGetLastError());
+    }
+    if (nonfinite) {
+        set_error("msp_online_solve_constrained: a data set's residual is not finite (NaN or Inf in phi)");
+        return MSP_ERR_NOT_CONVERGED;
+    }
+    if (not_conv) {
+        set_error("msp_online_solve_constrained: some data sets stopped at max_iter");
         return MSP_ERR_NOT_CONVERGED;
     }
     return MSP_OK;

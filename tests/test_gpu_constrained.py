@@ -1,0 +1,81 @@
+"""GPU parity of the constrained least-squares variant of the online step (the
+remark after Eq. elliptic_cond_reduced: boundary data imposed exactly, only the
+continuity rows in the least-squares sense) against the CPU oracle.
+
+Tolerances: online fields within 1e-8 of the oracle's dense null-space solution
+(FP64 path, CGLS to 1e-12); the boundary rows hold to 1e-10 of the data; with
+full local spaces the fine-grid solution to 1e-9.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import elliptic as E
+
+pytestmark = pytest.mark.gpu
+msp = pytest.importorskip("paper_1807_08848_gb300")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def boundary_residual(Pm, bnd, d, c):
+    return float(np.linalg.norm(Pm[bnd] @ c - d[bnd]) / np.linalg.norm(d[bnd]))
+
+
+@pytest.mark.parametrize("case", ["small", "ragged"])
+def test_constrained_matches_the_oracle(case):
+    if case == "small":
+        w = synth.workload_small()
+        ms, ps, seed, tau, N, phi = w["medium"], w["patches"], w["seed"], w["tau"], 128, w["phi"]
+    else:
+        N = 60
+        ps = synth.PatchSpec(np.array([0, 13, 37, 60]), np.array([0, 22, 41, 60]),
+                             np.array([3, 0, 5, 2, 4, 1, 6, 3, 2]), np.array([60, 60, 60, 60, 60, 60, 60, 60, 60]))
+        ms, seed, tau, phi = synth.hou_wu(N, 1 / 6), 21, 1e-6, synth.phi_fourier(N, 6, 9, kmax=3)[0]
+    med = msp.Medium(ms, ps)
+    med.sample(seed, "fp64", tol=1e-13, max_iter=20000)
+    basis = med.extract(tau, "fp64")
+    off = E.offline(ms, ps, seed, tau)
+    u_ref, c_ref, Pm, d, bnd = E.online_constrained(off, ps, N, phi)
+    u, it, c = basis.solve(torch.tensor(phi, device="cuda"), tol=1e-12, max_iter=20000, want_c=True,
+                           constrained=True)
+    u, c = u.cpu().numpy(), c.cpu().numpy()
+    assert rel(u, u_ref) <= 1e-8
+    assert boundary_residual(Pm, bnd, d, c) <= 1e-10
+    # it differs from the least-squares glue, which trades boundary error for continuity
+    u_ls, _ = basis.solve(torch.tensor(phi, device="cuda"), tol=1e-12, max_iter=20000)
+    u_ls_ref, c_ls, *_ = E.online(off, ps, N, phi)
+    assert rel(u_ls.cpu().numpy(), u_ls_ref) <= 1e-8
+    assert boundary_residual(Pm, bnd, d, c_ls) > boundary_residual(Pm, bnd, d, c)
+
+
+def test_constrained_full_basis_exactness():
+    """Full local spaces: the constrained variant reproduces the fine-grid solve."""
+    N = 32
+    ms = synth.periodic_sin(N, 1 / 4)
+    ps = synth.uniform_patches(N, 2, 2, 4, 90)
+    med = msp.Medium(ms, ps)
+    med.sample(3, "fp64", tol=1e-14, max_iter=5000)
+    basis = med.extract(1e-10, "fp64")
+    phi = synth.phi_fourier(N, 6, 9, kmax=3)[0]
+    u, _ = basis.solve(torch.tensor(phi, device="cuda"), tol=1e-14, max_iter=50000, constrained=True)
+    aE, aN = E.face_coefficients(ms)
+    assert rel(u.cpu().numpy(), E.global_reference(aE, aN, N, phi)) <= 1e-9
+
+
+def test_constrained_batch_and_mixed_basis():
+    """A batch of data sets gives each one's single-request result (bitwise), and
+    the variant runs on a basis extracted on the mixed path."""
+    w = synth.workload_small()
+    med = msp.Medium(w["medium"], w["patches"])
+    med.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000)
+    basis = med.extract(w["tau"], "mixed")
+    phis = synth.phi_fourier(128, 6, 5, kmax=4, batch=3)
+    ub, _ = basis.solve(torch.tensor(phis, device="cuda"), tol=1e-10, max_iter=20000, constrained=True)
+    for b in (0, 2):
+        u1, _ = basis.solve(torch.tensor(phis[b], device="cuda"), tol=1e-10, max_iter=20000, constrained=True)
+        assert torch.equal(u1, ub[b])
+    assert torch.isfinite(ub).all()
