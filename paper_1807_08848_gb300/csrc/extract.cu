@@ -331,20 +331,6 @@ __global__ void __launch_bounds__(512) jacobi_svd32_kernel(const SmallMat* mats,
     if (threadIdx.x == 0) sweeps_out[S.idx] = sweep;
 }
 
-// Z = the columns of W divided by their norms (zero columns stay zero), c x c
-__global__ void normalize_columns_kernel(const SmallMat* mats, const double* W, double* Z) {
-    const SmallMat S = mats[blockIdx.x];
-    const int c = S.c, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < c; j += nw) {
-        const double* w = W + S.off + (long long)j * c;
-        double t = 0.0;
-        for (int i = lane; i < c; i += 32) t = fma(w[i], w[i], t);
-        t = warp_sum(t);
-        const double inv = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
-        for (int i = lane; i < c; i += 32) Z[S.off + (long long)j * c + i] = w[i] * inv;
-    }
-}
-
 // Newton-Schulz scaling for X (3 I - X^T X) / 2 in place of G = X^T X: the
 // multiplier M = (3 I - G) / 2, so that X M is the next iterate (c x c).
 __global__ void newton_schulz_kernel(const SmallMat* mats, double* G) {
@@ -366,14 +352,13 @@ __global__ void newton_schulz_kernel(const SmallMat* mats, double* G) {
 // trailing columns over rows j.. (recomputed, no downdating), the largest swapped
 // into place, the reflector H_j = I - tau v v^T (v_0 = 1) that maps it onto
 // R(j, j) e_0, applied to the trailing columns.  Q = H_0 H_1 ... H_{c-1} is then
-// formed backwards in V.  With second_qr (the two-step preconditioning of the
-// same authors), Q goes to Qout instead, R^T = Q_2 R_2 is factored too (no
-// pivoting, Q_2 not formed) and the sweeps run on the columns of R_2^T from V = I:
-// then T P = Q R_2^T Q_2^T and the left singular vectors of T are Q times the
-// normalised columns of the rotated W.  A lives in shared memory (leading
-// dimension c + 1) when c <= smem_c, else in W, which ends holding R^T or R_2^T.
+// formed backwards in V.  With second_qr, R^T = Q_2 R_2 is factored too (no
+// pivoting, Q_2 not formed) and the sweeps run on the columns of R_2 (the
+// two-step preconditioning of the same authors).  A lives in shared memory
+// (leading dimension c + 1) when c <= smem_c, else in W, which ends holding R^T
+// or R_2 either way.
 __global__ void __launch_bounds__(512) qrcp_kernel(const SmallMat* mats, const double* Tm, double* W, double* V,
-                                                   double* Qout, int smem_c, int second_qr) {
+                                                   int smem_c, int second_qr) {
     extern __shared__ __align__(16) unsigned char qr_smem[];
     __shared__ double s_nrm[2 * kJacMaxPairs];
     __shared__ double s_tau[2 * kJacMaxPairs];
@@ -384,7 +369,7 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const SmallMat* mats, const d
     const bool in_smem = c <= smem_c;
     const int lda = in_smem ? c + 1 : c;
     double* a = in_smem ? reinterpret_cast<double*>(qr_smem) : W + S.off;
-    double* q = (second_qr ? Qout : V) + S.off;
+    double* q = V + S.off;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
         const int i = (int)(e % c), j = (int)(e / c);
@@ -533,17 +518,12 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const SmallMat* mats, const d
             }
             __syncthreads();
         }
-        // W = R_2^T (lower triangle), V = I: the sweeps' left singular vectors are the
-        // normalised columns of the rotated W, and Q times them those of T
+        // W = R_2: the upper triangle
         for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
             const int i = (int)(e % c), j = (int)(e / c);
-            V[S.off + e] = (i == j) ? 1.0 : 0.0;
-            if (in_smem) {
-                W[S.off + e] = (i >= j) ? a[j + (long long)i * lda] : 0.0;
-            } else if (i > j) {
-                a[i + (long long)j * lda] = a[j + (long long)i * lda];
-                a[j + (long long)i * lda] = 0.0;
-            }
+            const double v = (i <= j) ? a[i + (long long)j * lda] : 0.0;
+            if (in_smem) W[S.off + e] = v;
+            else if (i > j) a[i + (long long)j * lda] = 0.0;
         }
     } else if (in_smem) {
         // W = R^T
@@ -875,7 +855,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
             cq = std::min(cq, maxc);
             const size_t smq = (size_t)cq * (cq + 1) * sizeof(double);
             MSP_CUDA(cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
-            qrcp_kernel<<<np, 512, smq, s>>>(d_by_size.p, Tacc, W.p, V.p, G.p, cq, svd_second_qr() ? 1 : 0);
+            qrcp_kernel<<<np, 512, smq, s>>>(d_by_size.p, Tacc, W.p, V.p, cq, svd_second_qr() ? 1 : 0);
             count_launches(1);
             MSP_CUDA(cudaGetLastError());
         } else {
@@ -897,17 +877,6 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
         jacobi_svd_kernel<<<np, 512, sm64, s>>>(d_by_size.p, W.p, V.p, 40, maxc * 1.12e-16, small_rel, c64, sweeps.p);
         count_launches(1);
         MSP_CUDA(cudaGetLastError());
-        if (svd_qr() && svd_second_qr()) {
-            // left singular vectors of T: Q (in G) times the normalised columns of W
-            normalize_columns_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, L.p);
-            count_launches(1);
-            MSP_CUDA(cudaGetLastError());
-            for (int m = 0; m < np; ++m) {
-                const int c = mats[m].c;
-                gd[m] = GemmDesc{G.p + mats[m].off, L.p + mats[m].off, V.p + mats[m].off, c, c, c, c, c, c, 1.0, 0.0};
-            }
-            MSP_TRY(run_gemm(false, maxc, maxc));
-        }
         MSP_TRY(phase_mark(marks, s));
     }
     sort_truncate_kernel<<<np, 256, 0, s>>>(d_mats.p, W.p, tau, sig_tmp.p, sig.p, d_sig_off.p, order.p, kdev.p);
