@@ -785,7 +785,7 @@ def run_extract(args):
     # the Jacobi SVD from the identity in FP64 against the FP32-started one (default),
     # tensor-core products both, with the phase times
     msp.set_extract_timing(True)
-    for mode in ("fp32_preconditioned", "qr_preconditioned", "qr2_preconditioned", "fp64"):
+    for mode in ("fp32_preconditioned", "qr_preconditioned", "fp64"):
         msp.set_svd_mode(mode)
         b = med.extract(w["tau"], "mixed")
         out["svd_" + mode] = {"phases_ms": b.extract_timing(), "max_jacobi_sweeps": b.stats()["max_jacobi_sweeps"],
@@ -794,7 +794,7 @@ def run_extract(args):
     msp.set_svd_mode()
     msp.set_extract_timing(False)
     b64 = bases["svd_fp64"]
-    for mode in ("fp32_preconditioned", "qr_preconditioned", "qr2_preconditioned"):
+    for mode in ("fp32_preconditioned", "qr_preconditioned"):
         bx = bases["svd_" + mode]
         # singular values at 0.1 tau sigma_1 and above (the sweeps leave pairs of
         # columns far below the truncation level unrotated)

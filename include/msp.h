@@ -189,16 +189,12 @@ msp_status msp_set_gemm_engine(int engine);
  *     columns of R^T with V started at Q: the rows of R decay with the pivots,
  *     so the sweeps start from graded, nearly orthogonal columns (measured at
  *     2049^2: 37 ms of QR and 228 ms of sweeps, at most 10 and 6.3 on average,
- *     against 370 ms and 20 / 8.1 sweeps from V = I);
- *   MSP_SVD_QR2_PRECONDITIONED: as the previous mode, then R^T = Q_2 R_2 by an
- *     unpivoted Householder QR and the sweeps on the columns of R_2 (V still
- *     started at Q; Q_2 is not needed).
+ *     against 370 ms and 20 / 8.1 sweeps from V = I).
  * Both end at the same FP64 stopping test; process-wide, read by every
  * extraction.  INVALID_ARG on an unknown mode. */
 #define MSP_SVD_FP64                0
 #define MSP_SVD_FP32_PRECONDITIONED 1
 #define MSP_SVD_QR_PRECONDITIONED   2
-#define MSP_SVD_QR2_PRECONDITIONED  3
 msp_status msp_set_svd_mode(int mode);
 
 /* --------------------------------------------------------------------- medium */

@@ -49,8 +49,7 @@ def set_svd_mode(mode: str = "qr_preconditioned"):
     """Jacobi SVD of the extraction: a pivoted QR first and the FP64 sweeps on R^T
     (the default), FP64 sweeps from the identity, or FP32 sweeps re-orthogonalised
     then FP64 sweeps (msp_set_svd_mode)."""
-    N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1, "qr_preconditioned": 2,
-                                             "qr2_preconditioned": 3}[mode]))
+    N.check(N.load().msp_set_svd_mode({"fp64": 0, "fp32_preconditioned": 1, "qr_preconditioned": 2}[mode]))
 
 
 def precision_code(p) -> int:

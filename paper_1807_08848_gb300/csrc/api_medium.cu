@@ -35,11 +35,7 @@ static std::atomic<int> g_gemm_engine{0};
 int fp64_gemm_engine() { return g_gemm_engine.load(std::memory_order_relaxed); }
 static std::atomic<int> g_svd_mode{MSP_SVD_QR_PRECONDITIONED};
 bool svd_mixed() { return g_svd_mode.load(std::memory_order_relaxed) == MSP_SVD_FP32_PRECONDITIONED; }
-bool svd_qr() {
-    const int m = g_svd_mode.load(std::memory_order_relaxed);
-    return m == MSP_SVD_QR_PRECONDITIONED || m == MSP_SVD_QR2_PRECONDITIONED;
-}
-bool svd_second_qr() { return g_svd_mode.load(std::memory_order_relaxed) == MSP_SVD_QR2_PRECONDITIONED; }
+bool svd_qr() { return g_svd_mode.load(std::memory_order_relaxed) == MSP_SVD_QR_PRECONDITIONED; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
@@ -76,8 +72,7 @@ extern "C" int64_t msp_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" msp_status msp_set_svd_mode(int mode) {
     clear_error();
-    MSP_CHECK_ARG(mode == MSP_SVD_FP64 || mode == MSP_SVD_FP32_PRECONDITIONED || mode == MSP_SVD_QR_PRECONDITIONED ||
-                      mode == MSP_SVD_QR2_PRECONDITIONED,
+    MSP_CHECK_ARG(mode == MSP_SVD_FP64 || mode == MSP_SVD_FP32_PRECONDITIONED || mode == MSP_SVD_QR_PRECONDITIONED,
                   "msp_set_svd_mode: unknown mode");
     g_svd_mode.store(mode, std::memory_order_relaxed);
     return MSP_OK;

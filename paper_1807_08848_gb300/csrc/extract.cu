@@ -352,13 +352,10 @@ __global__ void newton_schulz_kernel(const SmallMat* mats, double* G) {
 // trailing columns over rows j.. (recomputed, no downdating), the largest swapped
 // into place, the reflector H_j = I - tau v v^T (v_0 = 1) that maps it onto
 // R(j, j) e_0, applied to the trailing columns.  Q = H_0 H_1 ... H_{c-1} is then
-// formed backwards in V.  With second_qr, R^T = Q_2 R_2 is factored too (no
-// pivoting, Q_2 not formed) and the sweeps run on the columns of R_2 (the
-// two-step preconditioning of the same authors).  A lives in shared memory
-// (leading dimension c + 1) when c <= smem_c, else in W, which ends holding R^T
-// or R_2 either way.
+// formed backwards in V.  A lives in shared memory (leading dimension c + 1) when
+// c <= smem_c, else in W, which is overwritten by R^T at the end either way.
 __global__ void __launch_bounds__(512) qrcp_kernel(const SmallMat* mats, const double* Tm, double* W, double* V,
-                                                   int smem_c, int second_qr) {
+                                                   int smem_c) {
     extern __shared__ __align__(16) unsigned char qr_smem[];
     __shared__ double s_nrm[2 * kJacMaxPairs];
     __shared__ double s_tau[2 * kJacMaxPairs];
@@ -472,64 +469,22 @@ __global__ void __launch_bounds__(512) qrcp_kernel(const SmallMat* mats, const d
         }
         __syncthreads();
     }
-    // R^T in place (lower triangle; the reflectors are no longer needed)
-    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
-        const int i = (int)(e % c), j = (int)(e / c);
-        if (i > j) {
-            a[i + (long long)j * lda] = a[j + (long long)i * lda];   // R(j, i)
-            a[j + (long long)i * lda] = 0.0;
-        }
-    }
-    __syncthreads();
-    if (second_qr) {
-        // R^T = Q_2 R_2 (unpivoted Householder QR; Q_2 is not needed): with
-        // T P = Q R_2^T Q_2^T the sweeps run on the columns of R_2, whose left
-        // singular vectors, started at Q, are those of T
-        for (int j = 0; j < c; ++j) {
-            double* aj = a + (long long)j * lda;
-            if (warp == 0) {
-                double t = 0.0;
-                for (int i = j + 1 + lane; i < c; i += 32) t = fma(aj[i], aj[i], t);
-                t = warp_sum(t);
-                if (lane == 0) s_nrm[j] = t;
-            }
-            __syncthreads();
-            const double alpha = aj[j], xn2 = s_nrm[j];
-            double tau = 0.0, scal = 0.0, beta = alpha;
-            if (xn2 > 0.0) {
-                beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-                tau = (beta - alpha) / beta;
-                scal = 1.0 / (alpha - beta);
-            }
-            __syncthreads();
-            if (tau != 0.0)
-                for (int i = j + 1 + threadIdx.x; i < c; i += blockDim.x) aj[i] *= scal;
-            if (threadIdx.x == 0) aj[j] = beta;
-            __syncthreads();
-            if (tau != 0.0) {
-                for (int col = j + 1 + warp; col < c; col += nw) {
-                    double* ac = a + (long long)col * lda;
-                    double t = (lane == 0) ? ac[j] : 0.0;
-                    for (int i = j + 1 + lane; i < c; i += 32) t = fma(aj[i], ac[i], t);
-                    t = warp_sum(t) * tau;
-                    if (lane == 0) ac[j] -= t;
-                    for (int i = j + 1 + lane; i < c; i += 32) ac[i] = fma(-t, aj[i], ac[i]);
-                }
-            }
-            __syncthreads();
-        }
-        // W = R_2: the upper triangle
+    // W = R^T (lower triangular); in the global case R is read before W is written
+    // over it, column by column of W = row by row of R, through registers
+    if (in_smem) {
         for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
             const int i = (int)(e % c), j = (int)(e / c);
-            const double v = (i <= j) ? a[i + (long long)j * lda] : 0.0;
-            if (in_smem) W[S.off + e] = v;
-            else if (i > j) a[i + (long long)j * lda] = 0.0;
+            W[S.off + e] = (i >= j) ? a[j + (long long)i * lda] : 0.0;
         }
-    } else if (in_smem) {
-        // W = R^T
+    } else {
+        // transpose in place: swap (i, j) and (j, i) for i > j, zero the upper part
         for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
             const int i = (int)(e % c), j = (int)(e / c);
-            W[S.off + e] = a[i + (long long)j * lda];
+            if (i > j) {
+                const double r = a[j + (long long)i * lda];   // R(j, i), upper part
+                a[i + (long long)j * lda] = r;                // W(i, j)
+                a[j + (long long)i * lda] = 0.0;
+            }
         }
     }
 }
@@ -855,7 +810,7 @@ msp_status svd_bases(const double* snaps, long long snap_elems, const std::vecto
             cq = std::min(cq, maxc);
             const size_t smq = (size_t)cq * (cq + 1) * sizeof(double);
             MSP_CUDA(cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
-            qrcp_kernel<<<np, 512, smq, s>>>(d_by_size.p, Tacc, W.p, V.p, cq, svd_second_qr() ? 1 : 0);
+            qrcp_kernel<<<np, 512, smq, s>>>(d_by_size.p, Tacc, W.p, V.p, cq);
             count_launches(1);
             MSP_CUDA(cudaGetLastError());
         } else {

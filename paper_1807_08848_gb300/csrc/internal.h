@@ -107,7 +107,6 @@ int fp64_gemm_engine();
 // Jacobi SVD of the extraction: FP32 sweeps first, then FP64 (msp_set_svd_mode).
 bool svd_mixed();
 bool svd_qr();
-bool svd_second_qr();
 
 // ------------------------------------------------------------------ geometry
 

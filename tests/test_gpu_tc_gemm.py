@@ -39,8 +39,7 @@ def extract_both(med, tau, precision, switch="engine"):
     test) -- CUDA-core vs tensor-core products, or FP64 vs FP32-started Jacobi."""
     set_, ref, new, default = {"engine": (msp.set_gemm_engine, "cuda_cores", "tensor_cores", "tensor_cores"),
                                "svd": (msp.set_svd_mode, "fp64", "fp32_preconditioned", "qr_preconditioned"),
-                               "svd_qr": (msp.set_svd_mode, "fp64", "qr_preconditioned", "qr_preconditioned"),
-                               "svd_qr2": (msp.set_svd_mode, "fp64", "qr2_preconditioned", "qr_preconditioned")}[switch]
+                               "svd_qr": (msp.set_svd_mode, "fp64", "qr_preconditioned", "qr_preconditioned")}[switch]
     try:
         set_(ref)
         b_cc = med.extract(tau, precision)
@@ -51,7 +50,7 @@ def extract_both(med, tau, precision, switch="engine"):
     return b_cc, b_tc
 
 
-@pytest.mark.parametrize("switch", ["engine", "svd", "svd_qr", "svd_qr2"])
+@pytest.mark.parametrize("switch", ["engine", "svd", "svd_qr"])
 @pytest.mark.parametrize("case", ["small", "lognormal-256", "ragged"])
 def test_engines_agree_and_match_the_oracle(case, switch):
     if case == "small":
