@@ -11,12 +11,12 @@
 // products of one diagonal t + u = g are summed by the tensor core (kind::f16,
 // FP32 accumulation in tensor memory) over K chunks of 128, in which at most 8
 // pairs x 128 terms x 2^14 < 2^24 keep every partial sum an exact integer.
-// After each chunk the accumulators are read out of tensor memory and added into
-// int32 registers (exact for K up to 16256), so
+// After each chunk the accumulators are read out of tensor memory and folded, in
+// integers, into two int64 halves (exact for K up to 16256), so
 //     C_ij = alpha sigma_i tau_j sum_g 2^(-kBeta g) V_g(i, j) + beta C_ij
-// is formed once per element at the end: the diagonals are folded in integers
-// into two exactly representable halves, so an element costs a few FP64
-// operations (the FP64 pipe issues about two FMAs per clock and SM here).  Pairs with t + u > kSlices + 1
+// is formed once per element at the end from two exactly representable halves: an
+// element costs a few FP64 operations (the FP64 pipe issues about two FMAs per
+// clock and SM here).  Pairs with t + u > kSlices + 1
 // are dropped: with 8 slices of 7 bits each dropped or truncated term is below
 // about 2^-56 sigma_i tau_j, under the rounding of an FP64 product.
 //
@@ -27,12 +27,13 @@
 // core matrices, K-adjacent cores 128 B apart, 8-row groups 256 B apart; the
 // kSlices blocks of one (row tile, slab) are contiguous and move with one bulk copy.
 //
-// MMA kernel: one CTA of 256 threads per 128 x 32 output tile of one product.
-// Thread 0 issues the bulk copies (five stages of 40 KB: 8 A slices of 128 x 16
-// and 8 B slices of 32 x 16; four slabs are in flight while one is multiplied)
-// and the MMAs; the 8 diagonal accumulators of a chunk
-// (8 x 32 columns) alternate between two halves of tensor memory, so the read-out
-// of one chunk overlaps the MMAs of the next.  Every wait is bounded: on timeout
+// MMA kernel: one CTA of 256 threads per 128 x 32 output tile of one product, two
+// CTAs per SM.  Thread 0 issues the bulk copies (two stages of 40 KB: 8 A slices of
+// 128 x 16 and 8 B slices of 32 x 16; one slab in flight while one is multiplied)
+// and the MMAs; the 8 diagonal accumulators of a chunk take 8 x 32 = 256 columns of
+// tensor memory, so the two CTAs of an SM hold all 512, and the read-out of one
+// CTA's chunk overlaps the other CTA's MMAs (measured faster than one CTA per SM
+// with two accumulator sets and five stages).  Every wait is bounded: on timeout
 // the CTA records the failure, stops issuing work, waits (bounded) for its issued
 // MMAs, frees its tensor memory and leaves without writing C.
 #include "internal.h"
@@ -54,7 +55,10 @@ constexpr int kTN = 32;                   // output columns per CTA (MMA N)
 constexpr int kSlabK = 16;                // K per staged slab (one MMA)
 constexpr int kCoresK = kSlabK / 8;       // 8 x 8 core matrices along K per slab
 constexpr int kChunkSlabs = 128 / kSlabK; // slabs per exactness chunk (K = 128)
-constexpr int kStages = 5;                // slabs in flight: four copies ahead of the MMAs
+constexpr int kAccBufs = 1;               // accumulator sets in tensor memory per CTA
+constexpr int kCtasPerSm = 3 - kAccBufs;  // one accumulator set: two CTAs share an SM
+constexpr int kStages = kAccBufs == 1 ? 2 : 5;   // slabs in flight per CTA
+constexpr unsigned kTmemCols = (unsigned)(kAccBufs * kDiag * kTN);   // 256 or 512
 constexpr int kOzThreads = 256;
 constexpr unsigned kAElems = kTM * kSlabK;                    // one A slice block
 constexpr unsigned kBElems = kTN * kSlabK;
@@ -274,9 +278,9 @@ struct OzArgs {
     int* err;
 };
 
-__global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
+__global__ void __launch_bounds__(kOzThreads, kCtasPerSm) oz_mma_kernel(OzArgs A) {
     extern __shared__ __align__(1024) unsigned char oz_smem[];
-    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], accb[2], accfree[2];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], accb[kAccBufs], accfree[kAccBufs];
     __shared__ unsigned s_tmem;
     __shared__ int s_fail;
     const int z = blockIdx.z;
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kAccBufs; ++h) {
             mbar_init(&accb[h], 1);
             mbar_init(&accfree[h], kOzThreads);
         }
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(512)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -330,17 +334,19 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         bulk_g2s(b_stage(st, 0), b0 + (long long)slab * kSlices * kBElems, kSlices * kBElems * 2, &full[st]);
     };
     const unsigned lbo = 128, sbo = kCoresK * 128;   // K-adjacent cores, 8-row groups
-    int last_commit[2] = {-1, -1};   // thread 0: last chunk committed to each accumulator half
+    int last_commit[kAccBufs];       // thread 0: last chunk committed to each accumulator set
+    for (int h = 0; h < kAccBufs; ++h) last_commit[h] = -1;
     // thread 0: the MMAs of one slab, then the refill of the stage the slab before
     // it used (slab sl + kStages - 1), so that the tensor pipe always holds the
     // MMAs of the slabs already staged; false on a timed-out wait.  Slab j is the
     // (j / kStages)-th use of stage j % kStages, which sets both barriers' parities.
     auto mma_slab = [&](int sl) -> bool {
         const int chunk = sl / kChunkSlabs, first = (sl % kChunkSlabs) == 0;
-        const int half = chunk & 1;
+        const int half = chunk % kAccBufs;   // chunk c is the (c / kAccBufs)-th use of its set
         const int st = sl % kStages;
         if (!mbar_wait_or_fail(&full[st], (unsigned)((sl / kStages) & 1), fail)) return false;
-        if (first && chunk >= 2 && !mbar_wait_or_fail(&accfree[half], (unsigned)(((chunk - 2) >> 1) & 1), fail))
+        if (first && chunk >= kAccBufs &&
+            !mbar_wait_or_fail(&accfree[half], (unsigned)(((chunk - kAccBufs) / kAccBufs) & 1), fail))
             return false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // one thread issues every MMA, so each costs only a few instructions: the
@@ -379,15 +385,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         }
         return true;
     };
-    // every thread: row (warp & 3) * 32 + lane of the tile, columns (warp >> 2) * 16 + 0..15
-    int vacc[kDiag][16];
+    // every thread: row (warp & 3) * 32 + lane of the tile, columns (warp >> 2) * 16 + 0..15.
+    // sum_g V_g 2^(-7(g+2)) = T_hi 2^-35 + T_lo 2^-63 with T_hi = sum_{g<4} V_g 2^(7(3-g)),
+    // T_lo = sum_{g>=4} V_g 2^(7(7-g)): each chunk's exact integer diagonal sums go
+    // straight into the two int64 halves (|T| < 2^53 for K <= 16256)
+    long long th[16], tl[16];
 #pragma unroll
-    for (int g = 0; g < kDiag; ++g)
-#pragma unroll
-        for (int c = 0; c < 16; ++c) vacc[g][c] = 0;
+    for (int c = 0; c < 16; ++c) th[c] = tl[c] = 0;
     auto readout = [&](int chunk) -> bool {
-        const int half = chunk & 1;
-        const bool got = mbar_wait_or_fail(&accb[half], (unsigned)((chunk >> 1) & 1), fail);
+        const int half = chunk % kAccBufs;
+        const bool got = mbar_wait_or_fail(&accb[half], (unsigned)((chunk / kAccBufs) & 1), fail);
         if (!__all_sync(0xffffffffu, got)) {
             *fail = 1;
             return false;
@@ -406,8 +413,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
                 : "r"(taddr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int sh = kBeta * (3 - (g & 3));
 #pragma unroll
-            for (int c = 0; c < 16; ++c) vacc[g][c] += __float2int_rn(__uint_as_float(r[c]));
+            for (int c = 0; c < 16; ++c) {
+                const long long d = (long long)__float2int_rn(__uint_as_float(r[c])) << sh;
+                if (g < 4) th[c] += d;
+                else tl[c] += d;
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accfree[half])) : "memory");
@@ -435,19 +447,21 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
             ok = false;
             break;
         }
-        // once the MMAs of a chunk are issued, read out the chunk before it
+        // once the MMAs of a chunk are issued, read out the chunk kAccBufs - 1 before
+        // it (with one accumulator set: the chunk itself, before the next may start)
         if ((sl % kChunkSlabs) == kChunkSlabs - 1 || sl == slabs - 1) {
-            const int chunk = sl / kChunkSlabs;
-            if (chunk >= 1) {
-                if (!readout(chunk - 1)) {
+            const int chunk = sl / kChunkSlabs - (kAccBufs - 1);
+            if (chunk >= 0) {
+                if (!readout(chunk)) {
                     ok = false;
                     break;
                 }
-                done_chunks = chunk;
+                done_chunks = chunk + 1;
             }
         }
     }
-    if (ok && chunks >= 1 && done_chunks < chunks && !readout(chunks - 1)) ok = false;
+    for (int c = done_chunks; ok && c < chunks; ++c)
+        if (!readout(c)) ok = false;
     if (!ok) *fail = 1;
     __syncthreads();
     const bool failed = *fail != 0;
@@ -460,24 +474,18 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
             for (int c = 0; c < 16; ++c) {
                 const int j = tn * kTN + (warp >> 2) * 16 + c;
                 if (j < D.N) {
-                    // sum_g V_g 2^(-7(g+2)) = T_hi 2^-35 + T_lo 2^-63 with the diagonals folded
-                    // by Horner's rule in integers: T_hi from g = 0..3, T_lo from g = 4..7,
-                    // each below 2^53 in magnitude, so both convert to FP64 exactly and the
+                    // T_hi (g = 0..3) and T_lo (g = 4..7), folded chunk by chunk at the read-out,
+                    // are each below 2^53 in magnitude, so both convert to FP64 exactly and the
                     // element costs two conversions and two FMAs of the FP64 pipe
-                    long long th = vacc[0][c], tl = vacc[4][c];
-#pragma unroll
-                    for (int g = 1; g < 4; ++g) {
-                        th = th * (1LL << kBeta) + vacc[g][c];
-                        tl = tl * (1LL << kBeta) + vacc[g + 4][c];
-                    }
+                    const long long thc = th[c], tlc = tl[c];
                     const int ex = ei + A.scale_exp[E.b_sc + j];
                     double v;
                     if (ex - 63 > -1022 && ex - 35 < 1023) {   // both powers of two normal: build them
                         const double ph = __longlong_as_double((long long)(ex - 35 + 1023) << 52);
                         const double pl = __longlong_as_double((long long)(ex - 63 + 1023) << 52);
-                        v = fma((double)th, ph, (double)tl * pl);
+                        v = fma((double)thc, ph, (double)tlc * pl);
                     } else {
-                        v = ldexp((double)th, ex - 35) + ldexp((double)tl, ex - 63);
+                        v = ldexp((double)thc, ex - 35) + ldexp((double)tlc, ex - 63);
                     }
                     double* cp = D.C + (long long)j * D.ldc + i;
                     *cp = (D.beta == 0.0) ? D.alpha * v : fma(D.alpha, v, D.beta * (*cp));
@@ -490,12 +498,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_mma_kernel(OzArgs A) {
         // and tensor memory they use is given up
         for (int st = 0; st < kStages; ++st)
             if (last_copy[st] >= 0) mbar_wait_or_fail(&full[st], (unsigned)((last_copy[st] / kStages) & 1), nullptr);
-        for (int h = 0; h < 2; ++h)
-            if (last_commit[h] >= 0) mbar_wait_or_fail(&accb[h], (unsigned)((last_commit[h] >> 1) & 1), nullptr);
+        for (int h = 0; h < kAccBufs; ++h)
+            if (last_commit[h] >= 0)
+                mbar_wait_or_fail(&accb[h], (unsigned)((last_commit[h] / kAccBufs) & 1), nullptr);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 }  // namespace
