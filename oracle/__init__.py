@@ -18,7 +18,9 @@ a direct solver, so each step yields its exact result up to rounding:
                 (Algorithm alg:summary, RanLocalSolu / DetLocalSolu), snapshot
                 matrices, SVD basis with truncation (Sec. 3.2, Eq. svd),
                 edge operators, the reduced least-squares system Eq.
-                elliptic_cond_reduced and the reconstruction.
+                elliptic_cond_reduced (and its constrained variant), the
+                overlapping restricted additive Schwarz variant of the online
+                step on the reduced bases, and the reconstruction.
 * `kinetic`  -- Sec. 4: discrete-ordinates slab transport, buffered local
                 solves with random inflow (Eq. rte_random), reduced basis and
                 the least-squares glue Eq. rte_cond_reduced.

@@ -26,6 +26,8 @@ Pipeline, in the order of Algorithm alg:summary:
     and c = argmin |P c - d| (Eq. elliptic_cond_reduced)  `online_system`, `online_solve`
   the constrained variant: boundary rows exact, continuity
     rows in the least-squares sense                   `constrained_solve`
+  the overlapping variant: restricted additive Schwarz
+    on the buffered patches, reduced to the bases      `ras_operators`, `ras_solve`
   u = sum_m G_m c_m with a partition of unity          `reconstruct`
 Direct solvers replace every iteration of the GPU path.
 """
@@ -473,3 +475,93 @@ def online_constrained(off: Offline, pspec, N, phi):
     Pm, d, o, is_bnd = online_system_rows(off.aE, off.aN, off.patches, off.Q, N, pspec, phi)
     c = constrained_solve(Pm, d, is_bnd)
     return reconstruct(off.patches, off.Q, c, o, N, phi), c, Pm, d, is_bnd
+
+
+# ---------------------------------------------------------------------------
+# online stage by overlapping Schwarz on the reduced bases
+# ---------------------------------------------------------------------------
+#
+# The paper leaves the online step to "a standard step in domain decomposition"
+# (Sec. 3, before Algorithm alg:summary).  Besides the least-squares glue of Eq.
+# elliptic_cond_reduced, the buffered patches K~_m give the classical overlapping
+# choice: restricted additive Schwarz (Cai and Sarkis, 1999).  One step solves the
+# local problem on every K~_m with the current field's values on its ring,
+# keeps each solution on K_m only and averages shared nodes with the partition
+# of unity chi_m of reading R10; domain-boundary ring nodes take phi.  On the
+# reduced bases the local solve with ring data g is G~_m g restricted to K_m,
+# replaced by its projection onto span Q_m, Q_m Q_m^T G~_m g, so each step is
+#     c_m <- B_m g_m(c),   B_m = Q_m^T G~_m (k_m x n_ring),
+# with g_m(c) the ring values of the reconstruction u(c) = sum_n chi_n Q_n c_n.
+# The fixed point solves (I - T) c = F phi.  With the full basis (Q_m spanning
+# the range of G~_m) the restriction of the global fine-grid solution is a fixed
+# point, so the reconstruction reproduces it exactly.
+
+def ras_ring_table(patches, N):
+    """For every patch m, one entry per ring node of its buffered box, in ring
+    order: ('phi', global ring position) for a node on the domain boundary,
+    else ('u', [(n, local index of the node in K_n, chi_n)]) over the patches n
+    whose closed box K_n holds the node (chi_n = 1 / their number, reading R10)."""
+    ring_id = domain_ring_index(N)
+    table = []
+    for P_ in patches:
+        ents = []
+        for (i, j) in ring_nodes(P_.X0, P_.X1, P_.Y0, P_.Y1):
+            i = int(i); j = int(j)
+            if i in (0, N) or j in (0, N):
+                ents.append(("phi", ring_id[(i, j)]))
+                continue
+            own = [Pn for Pn in patches if Pn.x0 <= i <= Pn.x1 and Pn.y0 <= j <= Pn.y1]
+            ents.append(("u", [(Pn.m, (i - Pn.x0) + (j - Pn.y0) * (Pn.x1 - Pn.x0 + 1), 1.0 / len(own))
+                               for Pn in own]))
+        table.append(ents)
+    return table
+
+
+def ras_operators(aE, aN, patches, Qs, N):
+    """T (N_p x N_p) and F (N_p x 4N), both sparse, of the reduced restricted
+    additive Schwarz step c <- T c + F phi, and the coefficient offsets.
+    B_m = Q_m^T G~_m with G~_m from DetLocalSolu (`full_green`)."""
+    ks = [Q.shape[1] for Q in Qs]
+    off = np.concatenate([[0], np.cumsum(ks)]).astype(int)
+    table = ras_ring_table(patches, N)
+    Tb = sp.lil_matrix((off[-1], off[-1]))
+    Fb = sp.lil_matrix((off[-1], 4 * N))
+    for P_, Q in zip(patches, Qs):
+        m = P_.m
+        Bm = Q.T @ full_green(aE, aN, P_)
+        rows = slice(off[m], off[m + 1])
+        Tm = np.zeros((ks[m], off[-1]))
+        Fm = np.zeros((ks[m], 4 * N))
+        for r, (kind, val) in enumerate(table[m]):
+            if kind == "phi":
+                Fm[:, val] += Bm[:, r]
+            else:
+                for (n, loc, chi) in val:
+                    Tm[:, off[n]:off[n + 1]] += chi * np.outer(Bm[:, r], Qs[n][loc])
+        Tb[rows] = Tm
+        Fb[rows] = Fm
+    return Tb.tocsr(), Fb.tocsr(), off
+
+
+def ras_solve(T, F, phi):
+    """The fixed point of the reduced Schwarz step: (I - T) c = F phi, by one
+    sparse LU (the GPU iterates to it)."""
+    A = (sp.identity(T.shape[0], format="csc") - T.tocsc()).tocsc()
+    return spla.splu(A).solve(F @ np.asarray(phi, dtype=np.float64))
+
+
+def ras_iterate(T, F, phi, c0, steps):
+    """`steps` plain Schwarz steps c <- T c + F phi from c0."""
+    c = np.array(c0, dtype=np.float64)
+    f = F @ np.asarray(phi, dtype=np.float64)
+    for _ in range(steps):
+        c = T @ c + f
+    return c
+
+
+def online_ras(off: Offline, N, phi):
+    """Online stage by the reduced overlapping Schwarz fixed point, then the
+    reconstruction with the partition of unity."""
+    T, F, o = ras_operators(off.aE, off.aN, off.patches, off.Q, N)
+    c = ras_solve(T, F, phi)
+    return reconstruct(off.patches, off.Q, c, o, N, phi), c, T, F
