@@ -478,6 +478,45 @@ msp_status msp_online_solve(msp_basis b, const double* phi_dev, int batch, doubl
 msp_status msp_online_solve_constrained(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
                                         double* u_dev, double* c_dev, int* iters_host, void* stream);
 
+/* The overlapping Schwarz variant of the online stage.  The paper leaves the
+ * online step to a standard domain-decomposition step (Sec. 3, before Algorithm
+ * alg:summary); this one is restricted additive Schwarz on the buffered patches
+ * K~_m (Cai and Sarkis 1999), reduced to the bases: each step sets
+ *     c_m <- B_m g_m(c),   B_m = Q_m^T G~_m  (k_m x n_ring_m),
+ * with G~_m the restricted Green's matrix of DetLocalSolu (Algorithm alg:summary)
+ * and g_m(c) the values on the ring of K~_m of the reconstruction
+ * u = sum_n chi_n Q_n c_n (chi_n = 1/#patches holding the node), phi on the
+ * domain boundary.  Its fixed point solves (I - T) c = F phi.
+ *
+ * msp_ras_setup(b, full, coarse, stream): `full` is a medium built by
+ * msp_build_medium_full on the same medium description and partition as the
+ * basis's medium and sampled by msp_sample_patches (its snapshot blocks are the
+ * G~_m); it is only read and may be destroyed afterwards.  Computes every B_m
+ * (FP64 products on the engine msp_set_gemm_engine selects), gathers the ring
+ * rows chi_n Q_n[node, :], and with coarse != 0 the two-level coarse space of
+ * Nicolaides (one vector z_m = Q_m^T 1 / |Q_m^T 1| per patch) with the coarse
+ * matrix E = Z^T (I - T) Z (M x M, FP64) inverted by Gauss-Jordan elimination with
+ * partial pivoting on the device.  Owns about (sum_m k_m n_ring_m + sum of ring
+ * entries x k) doubles plus 2 M^2 for the coarse space until the basis is
+ * destroyed; a second call replaces the first.  Synchronises.  INVALID_ARG when
+ * `full` is not a sampled full-basis medium of the basis's grid and partition;
+ * BREAKDOWN when E is singular to working precision (call again with coarse = 0).
+ *
+ * msp_online_solve_ras: restarted GMRES (restart 30) on (I - T) c = F phi, right-
+ * preconditioned by the coarse space in the A-DEF2 form M^{-1} = I + Z E^{-1} Z^T T
+ * (Tang, Nabben, Vuik, Erlangga 2009) when it was built, stopped per data set at
+ * |F phi - (I - T) c| <= tol |F phi| or max_iter GMRES iterations; FP64
+ * throughout; data sets in passes of 16, each data set's arithmetic independent of
+ * the others (fixed-order reductions).  Arguments and layouts as msp_online_solve
+ * (phi_dev [batch][4N], u_dev [batch][N+1][N+1] or NULL, c_dev [batch][N_p] or
+ * NULL, iters_host [batch] or NULL: GMRES iterations).  The call reads the stop
+ * test on the host after every iteration, so it synchronises the stream while it
+ * iterates.  NOT_CONVERGED if a data set hit max_iter or its residual is not
+ * finite; INVALID_ARG before msp_ras_setup. */
+msp_status msp_ras_setup(msp_basis b, msp_medium full, int coarse, void* stream);
+msp_status msp_online_solve_ras(msp_basis b, const double* phi_dev, int batch, double tol, int max_iter,
+                                double* u_dev, double* c_dev, int* iters_host, void* stream);
+
 /* Boundary-to-coefficient map.  The data of Eq. elliptic_cond_reduced enter only
  * through the boundary rows, linearly, so c = G phi with G = P~^+ S (N_p x 4N; S
  * places the ring values phi into the boundary rows).  msp_basis_build_map

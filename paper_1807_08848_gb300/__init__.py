@@ -316,11 +316,12 @@ class Basis:
 
     def solve(self, phi: torch.Tensor, tol: float = 1e-10, max_iter: int = 5000, stream=None,
               want_c: bool = False, want_iters: bool = True, u: torch.Tensor | None = None,
-              constrained: bool = False):
+              constrained: bool = False, schwarz: bool = False):
         """Online solve for phi of shape (B, 4N) (or (4N,)) on the device: the
-        least-squares glue (msp_online_solve), or with constrained=True the
+        least-squares glue (msp_online_solve), with constrained=True the
         variant that imposes the boundary data exactly
-        (msp_online_solve_constrained)."""
+        (msp_online_solve_constrained), or with schwarz=True the overlapping
+        Schwarz variant (msp_online_solve_ras; after setup_schwarz)."""
         squeeze = phi.dim() == 1
         phi = phi.reshape(-1, 4 * self.n_cells).to(dtype=torch.float64, device="cuda").contiguous()
         B = phi.shape[0]
@@ -329,7 +330,9 @@ class Basis:
             u = torch.empty((B, n, n), dtype=torch.float64, device="cuda")
         c = torch.empty((B, self.n_unknowns), dtype=torch.float64, device="cuda") if want_c else None
         iters = (C.c_int * B)() if want_iters else None
-        fn = N.load().msp_online_solve_constrained if constrained else N.load().msp_online_solve
+        lib = N.load()
+        fn = lib.msp_online_solve_ras if schwarz else (
+            lib.msp_online_solve_constrained if constrained else lib.msp_online_solve)
         code = fn(self._h, _dptr(phi), B, tol, max_iter, _dptr(u), _dptr(c) if c is not None else None, iters,
                   _stream_ptr(stream))
         N.check(code)
@@ -339,6 +342,11 @@ class Basis:
             c = c[0] if c is not None else None
         return (u, it, c) if want_c else (u, it)
 
+
+    def setup_schwarz(self, full: "Medium", coarse: bool = True, stream=None):
+        """Operators of the overlapping Schwarz online variant (msp_ras_setup) from
+        a sampled full-basis medium of the same grid and partition."""
+        N.check(N.load().msp_ras_setup(self._h, full.handle, 1 if coarse else 0, _stream_ptr(stream)))
 
     def save(self, path: str):
         """Write the bases, singular values, geometry and face coefficients to a file."""

@@ -118,6 +118,8 @@ SIGNATURES = {
     "msp_kinetic_online_solve": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
     "msp_online_solve": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
     "msp_online_solve_constrained": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
+    "msp_ras_setup": (_i, [_vp, _vp, _i, _vp]),
+    "msp_online_solve_ras": (_i, [_vp, _vp, _i, _d, _i, _vp, _vp, C.POINTER(_i), _vp]),
     "msp_operator_tile_shape": (_i, [_vp, C.POINTER(_i), C.POINTER(_i)]),
     "msp_medium_set_launch": (_i, [_vp, _i, _i, _i]),
     "msp_medium_set_graph": (_i, [_vp, _i]),

@@ -104,6 +104,23 @@ extern "C" msp_status msp_online_solve_constrained(msp_basis b, const double* ph
     return online_solve_constrained(b->B, phi, batch, tol, max_iter, u, c_dev, iters_host, (cudaStream_t)stream);
 }
 
+extern "C" msp_status msp_ras_setup(msp_basis b, msp_medium full, int coarse, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(b && full, "msp_ras_setup: NULL argument");
+    return ras_setup(b->B, full->M, coarse != 0, (cudaStream_t)stream);
+}
+
+extern "C" msp_status msp_online_solve_ras(msp_basis b, const double* phi, int batch, double tol, int max_iter,
+                                           double* u, double* c_dev, int* iters_host, void* stream) {
+    clear_error();
+    MSP_CHECK_ARG(b && phi && (u || c_dev), "msp_online_solve_ras: NULL argument");
+    MSP_CHECK_ARG(batch >= 0, "msp_online_solve_ras: negative batch");
+    MSP_CHECK_ARG(tol > 0 && tol < 1, "msp_online_solve_ras: tol must lie in (0, 1)");
+    MSP_CHECK_ARG(max_iter >= 1, "msp_online_solve_ras: max_iter must be >= 1");
+    if (batch == 0) return MSP_OK;
+    return ras_solve(b->B, phi, batch, tol, max_iter, u, c_dev, iters_host, (cudaStream_t)stream);
+}
+
 extern "C" msp_status msp_basis_build_map(msp_basis b, double tol, int max_iter, void* stream) {
     clear_error();
     MSP_CHECK_ARG(b, "msp_basis_build_map: NULL basis");

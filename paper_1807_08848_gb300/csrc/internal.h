@@ -271,6 +271,9 @@ struct Basis {
     // boundary rows
     bool no_boundary_rows = false;
     std::shared_ptr<struct ConstrainedOnline> cons;
+    // overlapping Schwarz variant of the online step: B_m = Q_m^T G~_m, ring tables,
+    // coarse space (online_ras.cu), built by msp_ras_setup
+    std::shared_ptr<struct RasOnline> ras;
 };
 
 // Boundary data imposed exactly: per boundary patch c_m = Z_m phi_m + N_m z_m
@@ -350,6 +353,14 @@ msp_status online_solve(Basis& B, const double* phi, int batch, double tol, int 
                         int* iters_host, cudaStream_t s);
 msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const std::vector<int>& row_slot,
                                cudaStream_t s);
+// u = sum_m chi_m Q_m c_m for B data sets of coefficients c ([coefficient][B]);
+// e is scratch of n_slots x B doubles
+void reconstruct_coefficients(const Basis& Bs, const double* c, int B, double* e, const double* phi, int n4, double* u,
+                              cudaStream_t s);
+// overlapping Schwarz variant of the online step (online_ras.cu)
+msp_status ras_setup(Basis& Bs, const Medium& full, bool coarse, cudaStream_t s);
+msp_status ras_solve(Basis& Bs, const double* phi, int batch, double tol, int max_iter, double* u, double* c_out,
+                     int* iters_host, cudaStream_t s);
 msp_status apply_online_factor(Basis& B, const double* s_in, double* z_out, int Bsz, cudaStream_t s);
 
 int num_sms();

@@ -473,6 +473,11 @@ static void reconstruct(const Basis& Bs, const OnArgs& A, const double* c, doubl
     count_launches(1);
 }
 
+void reconstruct_coefficients(const Basis& Bs, const double* c, int B, double* e, const double* phi, int n4, double* u,
+                              cudaStream_t s) {
+    reconstruct(Bs, make_args(Bs, B), c, e, phi, n4, u, s);
+}
+
 // One batch of CGLS.  dsub (optional, [row][B]) is subtracted from the right-hand
 // side d of the rows (the constrained variant's continuity rows carry -P c_p).
 static msp_status online_batch(Basis& Bs, const double* phi, int B, double tol, int max_iter, double* u,

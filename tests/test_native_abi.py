@@ -63,6 +63,8 @@ def test_null_arguments_are_rejected(lib):
     assert lib.msp_kinetic_build_hg(128, 0.1, -1.5, 8, 4, 8, 12, None, C.byref(out)) == N.MSP_ERR_INVALID_ARG
     assert lib.msp_kinetic_build_hg(128, 0.1, 0.5, 130, 4, 8, 12, None, C.byref(out)) == N.MSP_ERR_INVALID_ARG
     assert lib.msp_kinetic_set_solver(None, 1) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_ras_setup(None, None, 1, None) == N.MSP_ERR_INVALID_ARG
+    assert lib.msp_online_solve_ras(None, None, 1, 1e-8, 10, None, None, None, None) == N.MSP_ERR_INVALID_ARG
 
 
 def test_basis_files_are_checked_before_any_device_work(lib, tmp_path):
