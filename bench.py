@@ -854,6 +854,89 @@ def run_uneven(args):
     print(json.dumps(out), flush=True)
 
 
+def schwarz_block(msp, native, w, basis, phi_dev, prec, tol, direct, online_tol, reps=20, coarse_modes=(True,)):
+    """The overlapping Schwarz variant of the online step on `basis`: the set-up
+    samples the full-basis medium (one delta per ring node of every buffered patch,
+    with the step's local solver and tolerance) and forms B_m = Q_m^T G~_m and the
+    coarse space; then single-request solves (restarted GMRES on the reduced fixed
+    point) timed with CUDA events, and the relative difference of its field from
+    the least-squares glue's (two readings of the online step, not a parity check)."""
+    import torch
+    out = {}
+    try:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        full = msp.Medium(w["medium"], w["patches"], full_basis=True)
+        if direct:
+            full.set_launch("mixed", "direct")
+        full.sample(w["seed"], prec, tol=tol, max_iter=20000, stats=False)
+        ev[1].record()
+        torch.cuda.synchronize()
+        out["full_medium_solves"] = int(sum(full.patch(m).n_ring for m in range(full.n_patches)))
+        out["full_sample_ms"] = ev[0].elapsed_time(ev[1])
+        u_ls, _ = basis.solve(phi_dev, tol=1e-12, max_iter=20000)
+        for coarse in coarse_modes:
+            key = "two_level" if coarse else "one_level"
+            r = {}
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            basis.setup_schwarz(full, coarse=coarse)
+            b.record()
+            torch.cuda.synchronize()
+            r["setup_ms"] = a.elapsed_time(b)
+            a.record()
+            u, it = basis.solve(phi_dev, tol=online_tol, max_iter=5000, schwarz=True)
+            b.record()
+            torch.cuda.synchronize()
+            r["first_call_ms"] = a.elapsed_time(b)
+            times = []
+            for _ in range(reps):
+                a.record()
+                u, it = basis.solve(phi_dev, tol=online_tol, max_iter=5000, schwarz=True)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            r["p50_ms"], r["p99_ms"] = pct(times, 50), pct(times, 99)
+            r["requests"] = reps
+            r["gmres_iters"] = int(it[0])
+            r["rel_diff_vs_least_squares"] = float(torch.linalg.norm(u - u_ls) / torch.linalg.norm(u_ls))
+            out[key] = r
+        del full
+    except native.MspError as e:
+        out["error"] = str(e)
+    return out
+
+
+def run_schwarz(args):
+    """Only the Schwarz variant of the online step at 2049^2: offline stage as in
+    the step (mixed, direct local solver), then one- and two-level solves."""
+    import torch
+    import paper_1807_08848_gb300 as msp
+    from paper_1807_08848_gb300 import _native
+    torch.cuda.set_device(0)
+    msp.load_library()
+    n = args.schwarz_n
+    if n == 2048:
+        w = synth.workload_batched()
+    else:   # the smaller log-normal media of the serving workload (same tiles)
+        sv = synth.workload_serving()["media"][{512: 0, 1024: 1}[n]]
+        w = dict(medium=sv["medium"], patches=sv["patches"], seed=1, tau=1e-6, online_tol=1e-8,
+                 phi=synth.phi_sin_cos(n))
+    med = msp.Medium(w["medium"], w["patches"])
+    med.set_launch("mixed", "direct")
+    med.sample(w["seed"], "mixed", tol=1e-10, max_iter=20000, stats=False)
+    basis = med.extract(w["tau"], "mixed")
+    phi_dev = torch.tensor(w["phi"], dtype=torch.float64, device="cuda").reshape(1, -1)
+    t0 = time.perf_counter()
+    u, it = basis.solve(phi_dev, tol=w["online_tol"], max_iter=args.online_iters)
+    torch.cuda.synchronize()
+    out = {"case": f"schwarz-{n + 1}", "least_squares_first_call_ms": (time.perf_counter() - t0) * 1e3,
+           "least_squares_iters": int(it[0])}
+    out.update(schwarz_block(msp, _native, w, basis, phi_dev, "mixed", 1e-10, True, w["online_tol"],
+                             reps=args.schwarz_reps, coarse_modes=(False, True) if args.schwarz_one_level else (True,)))
+    print(json.dumps(out), flush=True)
+
+
 def run_step_case(args):
     """Only the headline step (new medium, local solves, extraction, one online
     solve) of the 2049^2 workload, --warmup then --steps times, CUDA events per
@@ -1057,6 +1140,9 @@ def run_ours(args, rank, world):
     except _native.MspError as e:
         cons["error"] = str(e)
     stages["online_constrained"] = cons
+    # the overlapping Schwarz variant of the online step on the same basis
+    stages["online_schwarz"] = schwarz_block(msp, _native, w, sbasis, phi_dev, prec, tol, direct,
+                                             online_tol=w["online_tol"])
     del smed, sbasis
 
     # ---- the streaming matrix-free operator on the same tiles (every patch x every
@@ -1251,7 +1337,11 @@ def main():
                     help="skip timing the streaming operator")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false",
                     help="skip timing the plain FP64 local solves beside the mixed ones")
-    ap.add_argument("--case", default="full", choices=["full", "step", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic",
+    ap.add_argument("--schwarz-n", type=int, default=2048, choices=[512, 1024, 2048],
+                    help="cells per side of the schwarz case (2048: the batched workload; 512/1024: serving media)")
+    ap.add_argument("--schwarz-reps", type=int, default=20, help="timed single-request solves of the schwarz case")
+    ap.add_argument("--schwarz-one-level", type=int, default=1, help="schwarz case: also time the one-level form")
+    ap.add_argument("--case", default="full", choices=["full", "step", "profile513", "serving", "uneven", "mapgemm", "stencil", "kinetic", "schwarz",
                                                       "direct", "extract"],
                     help="profile513: one pass of the small 513^2 case for profiler captures; "
                          "serving: the request loop over three prebuilt media")
@@ -1286,6 +1376,8 @@ def main():
     if args.case == "direct":
         run_direct(args)
         return
+    if args.case == "schwarz":
+        return run_schwarz(args)
     if args.case == "extract":
         run_extract(args)
         return

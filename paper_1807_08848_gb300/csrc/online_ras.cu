@@ -219,48 +219,107 @@ __global__ void ras_gj_elim_kernel(double* aug, int M, int k, const double* col)
 
 // ---------------------------------------------------------------- the Schwarz step
 
-// One CTA per patch m.  mode 0: out_m = T x restricted to patch m (ring values of
-// the reconstruction of x; domain-boundary ring nodes give 0), or a_m - (T x)_m
-// when a is given.  mode 1: out_m = B_m g with g = phi on the domain-boundary ring
-// nodes and 0 elsewhere (the right-hand side F phi).  Dynamic shared memory:
-// n_ring_m x B doubles.  Ring values: one warp per ring node, lanes along the
-// owner's coefficients; the product with B_m: one thread per (coefficient, data
-// set), ring nodes in order.
-__global__ void __launch_bounds__(kRasThreads) ras_apply_kernel(RasArgs A, const double* x, const double* phi, int n4,
-                                                              const double* a, double* out, int mode) {
+// The Schwarz step in two kernels.  mode 0: out_m = (T x)_m (ring values of the
+// reconstruction of x; domain-boundary ring nodes give 0), or a_m - (T x)_m when a
+// is given.  mode 1: out_m = B_m g with g = phi on the domain-boundary ring nodes and
+// 0 elsewhere (the right-hand side F phi).  Both kernels stream their operands (the
+// ring rows, B_m) once per call and are bound by the latency of those loads, so
+// each keeps eight loads per thread in flight; every sum runs in an order fixed by
+// the patch alone.
+//
+// Ring values gv[gr][b] of every ring node of every patch: a group of 8 lanes per
+// ring node, eight loads of each operand in flight per lane (one batch covers 64
+// coefficients; 8 lanes measured faster than 16), the lanes' partial sums combined
+// by shuffles inside the group.
+__global__ void __launch_bounds__(kRasThreads) ras_ring_kernel(RasArgs A, int n_ring_tot, const double* x,
+                                                             const double* phi, int n4, double* gv, int mode) {
+    const int B = A.B, sub = threadIdx.x & 7;
+    const unsigned gmask = 0xFFu << ((threadIdx.x & 31) & ~7);
+    for (long long gr = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 3; gr < n_ring_tot;
+         gr += ((long long)gridDim.x * blockDim.x) >> 3) {
+        const int bp = A.bnd[gr];
+        if (mode == 1) {
+            for (int b = sub; b < B; b += 8) gv[gr * B + b] = bp >= 0 ? phi[(long long)b * n4 + bp] : 0.0;
+            continue;
+        }
+        const int e0 = A.ent_ptr[gr], e1 = bp < 0 ? A.ent_ptr[gr + 1] : e0;
+        for (int b = 0; b < B; ++b) {
+            double v = 0.0;
+            for (int e = e0; e < e1; ++e) {
+                const int n = A.ent_patch[e], kn = A.k[n];
+                const double* row = A.rows + A.ent_row[e];
+                const double* xn = x + (long long)A.c_off[n] * B + b;
+                double t = 0.0;
+                for (int j0 = sub; j0 < kn; j0 += 64) {
+                    double rv[8], xv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = j0 + 8 * u;
+                        rv[u] = j < kn ? row[j] : 0.0;
+                        xv[u] = j < kn ? xn[(long long)j * B] : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) t += rv[u] * xv[u];
+                }
+                t += __shfl_xor_sync(gmask, t, 1);
+                t += __shfl_xor_sync(gmask, t, 2);
+                t += __shfl_xor_sync(gmask, t, 4);
+                v += t;
+            }
+            if (sub == 0) gv[gr * B + b] = v;
+        }
+    }
+}
+
+// out_m = B_m g_m (or a_m - B_m g_m), one CTA per patch: g_m staged in shared
+// memory, then for each data set the ring nodes split into nsl contiguous slices
+// (nsl fixed by k_m), thread (i, slice) sums its slice with sixteen loads in flight,
+// the slices added in order.  Dynamic shared memory: n_ring_max x B + max(256,
+// k_max) doubles.
+__global__ void __launch_bounds__(kRasThreads) ras_bm_kernel(RasArgs A, const double* gv, const double* a,
+                                                           double* out) {
     extern __shared__ double g[];
     const int m = blockIdx.x, km = A.k[m], B = A.B;
     const int g0 = A.ring_base[m], nr = A.ring_base[m + 1] - g0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int r = warp; r < nr; r += nw) {
-        const int gr = g0 + r, bp = A.bnd[gr];
-        if (mode == 1) {
-            if (lane < B) g[r * B + lane] = bp >= 0 ? phi[(long long)lane * n4 + bp] : 0.0;
-            continue;
-        }
-        for (int b = 0; b < B; ++b) {
-            double v = 0.0;
-            if (bp < 0)
-                for (int e = A.ent_ptr[gr]; e < A.ent_ptr[gr + 1]; ++e) {
-                    const int n = A.ent_patch[e], kn = A.k[n];
-                    const double* row = A.rows + A.ent_row[e];
-                    const double* xn = x + (long long)A.c_off[n] * B + b;
-                    double s = 0.0;
-                    for (int j = lane; j < kn; j += 32) s += row[j] * xn[(long long)j * B];
-                    v += warp_sum(s);
-                }
-            if (lane == 0) g[r * B + b] = v;
-        }
-    }
+    for (int t = threadIdx.x; t < nr * B; t += blockDim.x) g[t] = gv[(long long)g0 * B + t];
     __syncthreads();
     const double* Bm = A.Bm + A.b_off[m];
     const long long base = (long long)A.c_off[m] * B;
-    for (int w = threadIdx.x; w < km * B; w += blockDim.x) {
-        const int i = w % km, b = w / km;
-        double s = 0.0;
-        for (int r = 0; r < nr; ++r) s += Bm[i + (long long)r * km] * g[r * B + b];
-        const long long t = base + (long long)i * B + b;
-        out[t] = a ? a[t] - s : s;
+    double* part = g + nr * B;
+    const int nsl = km > 0 ? max(1, min(8, (int)blockDim.x / km)) : 1;
+    const int per = (nr + nsl - 1) / nsl;
+    for (int b = 0; b < B; ++b) {
+        for (int w = threadIdx.x; w < km * nsl; w += blockDim.x) {
+            const int i = w % km, sl = w / km;
+            const int r0 = sl * per, r1 = min(nr, r0 + per);
+            const double* bi = Bm + i;
+            const double* gb = g + b;
+            double sv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sv[u] = 0.0;
+            int r = r0;
+            // all sixteen loads of a step are issued before the first product uses one
+            for (; r + 16 <= r1; r += 16) {
+                double bv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) bv[u] = bi[(long long)(r + u) * km];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    sv[u] += bv[u] * gb[(r + u) * B];
+                    sv[u] += bv[u + 8] * gb[(r + 8 + u) * B];
+                }
+            }
+            for (; r < r1; ++r) sv[0] += bi[(long long)r * km] * gb[r * B];
+            part[w] = ((sv[0] + sv[1]) + (sv[2] + sv[3])) + ((sv[4] + sv[5]) + (sv[6] + sv[7]));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < km; i += blockDim.x) {
+            double t = 0.0;
+            for (int sl = 0; sl < nsl; ++sl) t += part[sl * km + i];
+            const long long o = base + (long long)i * B + b;
+            out[o] = a ? a[o] - t : t;
+        }
+        __syncthreads();
     }
 }
 
@@ -316,24 +375,29 @@ __global__ void ras_residual_kernel(long long n, const double* f, const double* 
 
 // Partial dot products of vectors V_i (i < nvec, each Np x B, consecutive) with w,
 // one CTA per (chunk of kRasChunk coefficients, i): part[(i n_chunks + chunk) B + b].
-// Every thread sums a fixed set of elements; the block sum runs in warp order.
+// Every thread sums a fixed set of elements; the block sum runs in warp order.  NB
+// is the batch rounded up to a power of two: each data set's sums are the same
+// whatever NB is, so results do not depend on the batch.
+template <int NB>
 __global__ void __launch_bounds__(kRasThreads) ras_dots_kernel(const double* V, const double* w, int Np, int B,
                                                              int n_chunks, double* part) {
-    __shared__ double buf[kRasMaxBatch * 32];
+    __shared__ double buf[NB * 32];
     const int chunk = blockIdx.x, i = blockIdx.y;
     const double* vi = V + (long long)i * Np * B;
-    double acc[kRasMaxBatch];
+    double acc[NB];
 #pragma unroll
-    for (int b = 0; b < kRasMaxBatch; ++b) acc[b] = 0.0;
+    for (int b = 0; b < NB; ++b) acc[b] = 0.0;
     const int c0 = chunk * kRasChunk, c1 = min(Np, c0 + kRasChunk);
     for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const long long t = (long long)c * B;
 #pragma unroll
-        for (int b = 0; b < kRasMaxBatch; ++b)
+        for (int b = 0; b < NB; ++b)
             if (b < B) acc[b] += vi[t + b] * w[t + b];
     }
-    block_sum<double, kRasMaxBatch>(acc, buf);
-    if (threadIdx.x < B) part[((long long)i * n_chunks + chunk) * B + threadIdx.x] = acc[threadIdx.x];
+    block_sum<double, NB>(acc, buf);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)   // static indices keep acc in registers
+        if (b < B && threadIdx.x == b) part[((long long)i * n_chunks + chunk) * B + b] = acc[b];
 }
 
 // Sum of the partials in chunk order, one warp per (i, b).  mode 0: htmp[i][b] =
@@ -485,7 +549,7 @@ __global__ void ras_export_kernel(const double* c, double* out, int Np, int B) {
 // ---------------------------------------------------------------- host side
 
 struct RasOnline {
-    int M = 0, Np = 0, max_ring = 0, max_patch_ents = 0, n_ring_tot = 0, n_ent = 0;
+    int M = 0, Np = 0, max_ring = 0, max_patch_ents = 0, n_ring_tot = 0, n_ent = 0, max_k = 0;
     bool coarse = false;
     std::vector<int> ring_base_h;
     DevBuf<double> Bm, rows, z, aug;
@@ -494,7 +558,7 @@ struct RasOnline {
     // work space for kRasMaxBatch data sets, allocated on the first solve
     bool work = false;
     int n_chunks = 0;
-    DevBuf<double> V, x, f, r, t, sv, w, zc, p, q, part, hh, htmp, g, cs, sn, y, st, e;
+    DevBuf<double> V, x, f, r, t, sv, w, zc, p, q, part, hh, htmp, g, cs, sn, y, st, e, gv;
 };
 
 static RasArgs ras_args(const Basis& Bs, const RasOnline& R, int B) {
@@ -560,12 +624,20 @@ msp_status ras_setup(Basis& Bs, const Medium& F, bool coarse, cudaStream_t s) {
                 bnd.push_back(domain_ring_pos(N, i, j));
             } else {
                 bnd.push_back(-1);
-                int own[4], no = 0;
-                for (int q = 0; q < my; ++q) {
-                    if (j < Bs.yb[q] || j > Bs.yb[q + 1]) continue;
-                    for (int pp = 0; pp < mx; ++pp)
-                        if (i >= Bs.xb[pp] && i <= Bs.xb[pp + 1] && no < 4) own[no++] = pp + q * mx;
+                // patches whose closed box holds (i, j): the break interval of i (and the
+                // one before it when i sits on a break), likewise for j, in patch order
+                int px[2], qy[2], npx = 0, nqy = 0;
+                {
+                    const int p1 = (int)(std::upper_bound(Bs.xb.begin(), Bs.xb.end(), i) - Bs.xb.begin()) - 1;
+                    const int q1 = (int)(std::upper_bound(Bs.yb.begin(), Bs.yb.end(), j) - Bs.yb.begin()) - 1;
+                    if (p1 > 0 && Bs.xb[p1] == i) px[npx++] = p1 - 1;
+                    if (p1 >= 0 && p1 < mx) px[npx++] = p1;
+                    if (q1 > 0 && Bs.yb[q1] == j) qy[nqy++] = q1 - 1;
+                    if (q1 >= 0 && q1 < my) qy[nqy++] = q1;
                 }
+                int own[4], no = 0;
+                for (int a = 0; a < nqy; ++a)
+                    for (int c = 0; c < npx; ++c) own[no++] = px[c] + qy[a] * mx;
                 MSP_CHECK_ARG(no > 0, "msp_ras_setup: a ring node lies in no patch");
                 for (int o = 0; o < no; ++o) {
                     const PatchDev& Pn = Bs.patches[own[o]];
@@ -587,6 +659,7 @@ msp_status ras_setup(Basis& Bs, const Medium& F, bool coarse, cudaStream_t s) {
         ring_base[m + 1] = ring_base[m] + P.n_ring;
         b_off[m + 1] = b_off[m] + (long long)Bs.k[m] * P.n_ring;
         R->max_ring = std::max(R->max_ring, P.n_ring);
+        R->max_k = std::max(R->max_k, Bs.k[m]);
         R->max_patch_ents = std::max(R->max_patch_ents, (int)ent_patch.size() - e_first);
     }
     R->n_ring_tot = ring_base[M];
@@ -703,6 +776,7 @@ static msp_status ras_work(const Basis& Bs, RasOnline& R, cudaStream_t s) {
     MSP_TRY(R.y.alloc(Rr * cb, s));
     MSP_TRY(R.st.alloc(8 * cb, s));
     MSP_TRY(R.e.alloc((size_t)std::max(Bs.n_slots, 1) * cb, s));
+    MSP_TRY(R.gv.alloc((size_t)std::max(R.n_ring_tot, 1) * cb, s));
     R.work = true;
     return MSP_OK;
 }
@@ -713,14 +787,21 @@ static msp_status ras_batch(Basis& Bs, RasOnline& R, const double* phi, int B, d
     const int M = R.M, Np = Bs.Np, n4 = 4 * Bs.N, Rr = kRasRestart;
     const long long nb = (long long)Np * B;
     const RasArgs A = ras_args(Bs, R, B);
-    const size_t smem = sizeof(double) * (size_t)R.max_ring * B;
-    MSP_CUDA(cudaFuncSetAttribute(ras_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
+    const size_t smem = sizeof(double) * ((size_t)R.max_ring * B + (size_t)std::max(kRasThreads, R.max_k));
+    MSP_CUDA(cudaFuncSetAttribute(ras_bm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int ring_grid = std::max(1, std::min((R.n_ring_tot + 31) / 32, num_sms() * 16));
     auto apply = [&](const double* x, const double* a, double* out, int mode) {
-        ras_apply_kernel<<<M, kRasThreads, smem, s>>>(A, x, phi, n4, a, out, mode);
-        count_launches(1);
+        ras_ring_kernel<<<ring_grid, kRasThreads, 0, s>>>(A, R.n_ring_tot, x, phi, n4, R.gv.p, mode);
+        ras_bm_kernel<<<M, kRasThreads, smem, s>>>(A, R.gv.p, a, out);
+        count_launches(2);
     };
     auto dots = [&](const double* V, int nvec, const double* w) {
-        ras_dots_kernel<<<dim3(R.n_chunks, nvec), kRasThreads, 0, s>>>(V, w, Np, B, R.n_chunks, R.part.p);
+        const dim3 grid(R.n_chunks, nvec);
+        if (B == 1) ras_dots_kernel<1><<<grid, kRasThreads, 0, s>>>(V, w, Np, B, R.n_chunks, R.part.p);
+        else if (B == 2) ras_dots_kernel<2><<<grid, kRasThreads, 0, s>>>(V, w, Np, B, R.n_chunks, R.part.p);
+        else if (B <= 4) ras_dots_kernel<4><<<grid, kRasThreads, 0, s>>>(V, w, Np, B, R.n_chunks, R.part.p);
+        else if (B <= 8) ras_dots_kernel<8><<<grid, kRasThreads, 0, s>>>(V, w, Np, B, R.n_chunks, R.part.p);
+        else ras_dots_kernel<kRasMaxBatch><<<grid, kRasThreads, 0, s>>>(V, w, Np, B, R.n_chunks, R.part.p);
         count_launches(1);
     };
     auto finalize = [&](int nvec, double* hcol, int mode, int slot) {

@@ -8,7 +8,9 @@
   solves, for the plain FP64 path (relative L2 <= 1e-8) and the mixed path
   (<= 1e-6), with principal angles of the mixed bases; the serving form (the
   FP32 boundary-to-coefficient map on the tensor cores, alone and through the
-  request loop) against the oracle's FP64 online solution (<= 1e-6).
+  request loop) against the oracle's FP64 online solution (<= 1e-6); the
+  overlapping Schwarz variant of the online step against the oracle's direct
+  fixed-point solve (<= 1e-6, mixed-path basis).
 * The 8192-cell slab transport workload (64 Gauss-Legendre velocities, 64
   patches, 96 samples): the online field of Eq. rte_cond_reduced against the
   oracle (FP64 path <= 1e-8, mixed sweeps <= 1e-6).
@@ -115,6 +117,31 @@ def test_513_serving_against_the_oracle(oracle513):
         srv.close()
     for b in range(len(phis)):
         assert rel(got[b], refs[b]) <= MIXED_TOL, b
+
+
+def test_513_schwarz_against_the_oracle(oracle513):
+    """The overlapping Schwarz variant of the online step at 513^2 (the bench's
+    tiles), two-level GMRES on the mixed-path basis, against the oracle's direct
+    fixed-point solve of the same data on its FP64 bases (<= 1e-6)."""
+    ms, ps, off, phis, refs = oracle513
+    med = msp.Medium(ms, ps)
+    med.set_launch("mixed", "direct")
+    med.sample(SEED513, "mixed", tol=1e-11, max_iter=20000)
+    basis = med.extract(1e-6, "mixed")
+    full = msp.Medium(ms, ps, full_basis=True)
+    full.set_launch("mixed", "direct")
+    st = full.sample(0, "mixed", tol=1e-11, max_iter=20000)
+    assert st.n_not_converged == 0
+    basis.setup_schwarz(full, coarse=True)
+    del full
+    u, it = basis.solve(torch.tensor(phis, device="cuda"), tol=1e-12, max_iter=2000, schwarz=True)
+    u = u.cpu().numpy()
+    T, F, o = E.ras_operators(off.aE, off.aN, off.patches, off.Q, N513)
+    for b in (0, 2):
+        u_ref = E.reconstruct(off.patches, off.Q, E.ras_solve(T, F, phis[b]), o, N513, phis[b])
+        assert rel(u[b], u_ref) <= MIXED_TOL, b
+        # a different reading of the online step than the least-squares glue
+        assert rel(u[b], refs[b]) <= 1e-2, b
 
 
 KIN = dict(n_cells=8192, eps=2.0 ** -8, n_v=64, n_patches=64, buffer=32, samples=96)
