@@ -578,13 +578,8 @@ static RasArgs ras_args(const Basis& Bs, const RasOnline& R, int B) {
     return A;
 }
 
-// position of a domain-boundary node in the global ring (counter-clockwise from (0,0))
-static int domain_ring_pos(int N, int i, int j) {
-    if (j == 0 && i < N) return i;
-    if (i == N && j < N) return N + j;
-    if (j == N && i > 0) return 2 * N + (N - i);
-    return 3 * N + (N - j);
-}
+// position of a domain-boundary node in the global ring (extract.cu)
+int domain_ring_pos(int N, int i, int j);
 
 static int ew_grid(long long n) {
     return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, (long long)num_sms() * 8));
