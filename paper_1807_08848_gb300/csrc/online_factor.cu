@@ -107,38 +107,31 @@ __global__ void patch_post_kernel(const double* F, const long long* f_off, const
     }
 }
 
-// Cholesky of one <= 64 x 64 diagonal tile in shared memory and the inverse of its
-// factor; writes L (lower, strict upper zeroed) in place and inv(L) to `inv` (ld 64).
-// One CTA of 256 threads, which sits on the factorisation's critical path, so
-// the work is spread over all threads and the FP64 square root and reciprocal
-// of each pivot are taken once, by the thread that finishes that pivot:
-//   factor, column k: scale column k by the pivot reciprocal; then thread (i, g)
-//     (row i = tid mod 64, g = tid / 64) updates L[i][j] for j = k+1+g, k+5+g, ...
-//     up to i, and the thread owning L[k+1][k+1] takes the next pivot;
-//   inverse: four lanes of a warp per column j of inv(L) run down its rows,
-//     each summing every fourth term of the forward substitution, combined by
-//     shuffles; column j is kept in the free strict upper part (inv(L)[i][j] at
-//     L[j][i + 1]).
+// Cholesky of one <= 64 x 64 diagonal tile in shared memory; writes L (lower,
+// strict upper zeroed) in place.  One CTA of 256 threads on the factorisation's
+// critical path, in the LDL^T form so that each column costs one barrier: at step
+// k every thread (i, g) (row i = tid mod 64, g = tid / 64) updates
+// L[i][j] -= (L[i][k] / d_k) L[j][k] for j = k+1+g, k+5+g, ... up to i, with the
+// reciprocal 1 / d_k of the pivot taken in step k-1 by the thread that made the
+// last update of L[k][k] (while the others finish theirs).  At the end the columns
+// are scaled, L[i][j] / sqrt(d_j) below the diagonal and sqrt(d_j) on it.  A
+// non-positive pivot sets *fail (and continues with d = 1).  The inverse of the
+// factor is left to tile_inverse_kernel, off the critical path.
 template <class T>
-__device__ __forceinline__ void take_pivot(T (*L)[kTile + 1], int p, T* s_rp, int* s_ok) {
-    const T d = L[p][p];
+__device__ __forceinline__ T checked_pivot(T d, int* s_ok) {
     if (!(d > T(0)) || !isfinite(d)) {
         *s_ok = 0;
-        L[p][p] = T(1);
-        *s_rp = T(1);
-    } else {
-        const T r = sqrt(d);
-        L[p][p] = r;
-        *s_rp = T(1) / r;
+        return T(1);
     }
+    return d;
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) potrf_tile_kernel(T* A, int lda, int nb, T* inv, int* fail) {
+__global__ void __launch_bounds__(256) potrf_tile_kernel(T* A, int lda, int nb, int* fail) {
     static_assert(kTile == 64, "thread layout assumes 64-wide tiles and 256 threads");
     __shared__ T L[kTile][kTile + 1];
-    __shared__ T rdiag[kTile];
-    __shared__ T s_rp;
+    __shared__ T s_inv[2];
+    __shared__ T s_sq[kTile];
     __shared__ int s_ok;
     const int tid = threadIdx.x;
     for (int e = tid; e < nb * nb; e += blockDim.x) {
@@ -148,26 +141,52 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(T* A, int lda, int nb, 
     __syncthreads();
     if (tid == 0) {
         s_ok = 1;
-        if (nb > 0) take_pivot<T>(L, 0, &s_rp, &s_ok);
+        if (nb > 0) {
+            const T d = checked_pivot(L[0][0], &s_ok);
+            L[0][0] = d;
+            s_inv[0] = T(1) / d;
+        }
     }
     __syncthreads();
     const int ri = tid & (kTile - 1), g = tid >> 6;
     for (int k = 0; k < nb; ++k) {
-        const T rp = s_rp;
-        if (tid > k && tid < nb) L[tid][k] *= rp;
-        __syncthreads();
         if (ri > k && ri < nb) {
-            const T lik = L[ri][k];
-            for (int j = k + 1 + g; j <= ri; j += 4) L[ri][j] = fma(-lik, L[j][k], L[ri][j]);
-            if (g == 0 && ri == k + 1) take_pivot<T>(L, k + 1, &s_rp, &s_ok);
+            const T t = L[ri][k] * s_inv[k & 1];
+            for (int j = k + 1 + g; j <= ri; j += 4) L[ri][j] = fma(-t, L[j][k], L[ri][j]);
+            if (g == 0 && ri == k + 1) {   // L[k+1][k+1] is final: the next pivot
+                const T d = checked_pivot(L[ri][ri], &s_ok);
+                L[ri][ri] = d;
+                s_inv[(k + 1) & 1] = T(1) / d;
+            }
         }
         __syncthreads();
     }
     if (!s_ok && tid == 0) atomicExch(fail, 1);
+    for (int j = tid; j < nb; j += blockDim.x) s_sq[j] = sqrt(L[j][j]);
+    __syncthreads();
     for (int e = tid; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
-        A[i + (long long)j * lda] = (i >= j) ? L[i][j] : T(0);
+        A[i + (long long)j * lda] = i > j ? L[i][j] / s_sq[j] : (i == j ? s_sq[j] : T(0));
     }
+}
+
+// Inverses of the factored diagonal tiles of one n x n block (one CTA per tile kt,
+// rows/columns 64 kt ..): four lanes of a warp per column j of inv(L) run down its
+// rows, each summing every fourth term of the forward substitution, combined by
+// shuffles; column j is kept in the free strict upper part (inv(L)[i][j] at
+// L[j][i + 1]); written to inv + kt 64^2 (ld 64, zero outside the tile).
+template <class T>
+__global__ void __launch_bounds__(256) tile_inverse_kernel(const T* D, int n, T* inv) {
+    __shared__ T L[kTile][kTile + 1];
+    __shared__ T rdiag[kTile];
+    const int tid = threadIdx.x, r0 = blockIdx.x * kTile, nb = min(kTile, n - r0);
+    const T* A = D + r0 + (long long)r0 * n;
+    T* out = inv + (size_t)blockIdx.x * kTile * kTile;
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        L[i][j] = (i >= j) ? A[i + (long long)j * n] : T(0);
+    }
+    __syncthreads();
     for (int i = tid; i < nb; i += blockDim.x) rdiag[i] = T(1) / L[i][i];
     __syncthreads();
     {
@@ -186,7 +205,46 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(T* A, int lda, int nb, 
     __syncthreads();
     for (int e = tid; e < kTile * kTile; e += blockDim.x) {
         const int i = e % kTile, j = e / kTile;
-        inv[i + j * kTile] = (i < nb && j < nb && i >= j) ? L[j][i + 1] : T(0);
+        out[i + j * kTile] = (i < nb && j < nb && i >= j) ? L[j][i + 1] : T(0);
+    }
+}
+
+// Panel of the block Cholesky: P <- P L^{-T} for the m x nb panel P (ld ldp) under
+// the factored diagonal tile L (nb x nb lower, ld ldl), by forward substitution on
+// every row: x_j = (p_j - sum_{l<j} L[j][l] x_l) / L[j][j].  One CTA of 64 threads
+// per 16 rows, four lanes per row, each summing every fourth term, combined by
+// shuffles in a fixed order.
+constexpr int kTrsmRows = 16;
+template <class T>
+__global__ void __launch_bounds__(64) trsm_panel_kernel(const T* Lkk, int ldl, T* P, int ldp, int m, int nb) {
+    __shared__ T L[kTile][kTile + 1];
+    __shared__ T X[kTrsmRows][kTile + 1];
+    __shared__ T rd[kTile];
+    const int tid = threadIdx.x, r0 = blockIdx.x * kTrsmRows;
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int i = e % nb, j = e / nb;
+        L[i][j] = (i >= j) ? Lkk[i + (long long)j * ldl] : T(0);
+    }
+    for (int e = tid; e < kTrsmRows * nb; e += blockDim.x) {
+        const int i = e % kTrsmRows, j = e / kTrsmRows;
+        X[i][j] = r0 + i < m ? P[(r0 + i) + (long long)j * ldp] : T(0);
+    }
+    __syncthreads();
+    for (int i = tid; i < nb; i += blockDim.x) rd[i] = T(1) / L[i][i];
+    __syncthreads();
+    const int row = tid >> 2, part = tid & 3;
+    for (int j = 0; j < nb; ++j) {
+        T acc = T(0);
+        for (int l = part; l < j; l += 4) acc = fma(L[j][l], X[row][l], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (part == 0) X[row][j] = (X[row][j] - acc) * rd[j];
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = tid; e < kTrsmRows * nb; e += blockDim.x) {
+        const int i = e % kTrsmRows, j = e / kTrsmRows;
+        if (r0 + i < m) P[(r0 + i) + (long long)j * ldp] = X[i][j];
     }
 }
 
@@ -455,7 +513,8 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         // Collect the whole factorisation's GEMMs in order, then launch them in order
         // with their descriptors resident in one device array.
         struct Step {
-            int kind;        // 0 gemm, 1 potrf tile, 2 zero upper, 3 copy tile, 4 zero fill, 5 pivot check
+            int kind;        // 0 gemm, 1 potrf tile, 2 zero upper, 3 copy tile, 4 zero fill, 5 pivot check,
+                             // 6 panel triangular solve, 7 inverses of the diagonal tiles
             GemmDescT<T> g;
             bool tA, tB;
             T* ptr;
@@ -498,17 +557,31 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                 st.ptr = Dq + r0 + (long long)r0 * n;
                 st.ld = n;
                 st.nb = nb;
-                st.inv = tinv.p + (size_t)kt * kTile * kTile;
                 steps.push_back(st);
                 if (m > 0) {
                     T* panel = Dq + (r0 + nb) + (long long)r0 * n;
-                    // panel <- panel inv(L_kk)^T (in place: one column tile)
-                    add_gemm(panel, n, st.inv, kTile, panel, n, m, nb, nb, T(1), T(0), false, true);
+                    // panel <- panel L_kk^{-T} (in place: one column tile)
+                    Step ts{};
+                    ts.kind = 6;
+                    ts.src = st.ptr;
+                    ts.lds = n;
+                    ts.ptr = panel;
+                    ts.ld = n;
+                    ts.nr = m;
+                    ts.nb = nb;
+                    steps.push_back(ts);
                     // trailing -= panel panel^T
                     add_gemm(panel, n, panel, n, Dq + (r0 + nb) + (long long)(r0 + nb) * n, n, m, m, nb, T(-1), T(1), false,
                              true, 1);
                 }
             }
+            Step ti{};   // inverses of the diagonal tiles, off the chain of the tile factorisations
+            ti.kind = 7;
+            ti.ptr = Dq;
+            ti.nb = n;
+            ti.nr = nt;
+            ti.inv = tinv.p;
+            steps.push_back(ti);
             Step zu{};
             zu.kind = 2;
             zu.ptr = Dq;
@@ -609,10 +682,10 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                 const bool structured = g0.lower || g0.b_lower || g0.a_lower || g0.b_upper || g0.a_k_lo;
                 bool on_tc = false;
                 if constexpr (sizeof(T) == sizeof(double)) {
-                    // a group worth at least ~2^27 multiply-adds goes to the tensor cores
+                    // a group worth at least ~2^23 multiply-adds goes to the tensor cores
                     double work = 0.0;
                     for (size_t k = si; k < sj; ++k) work += (double)steps[k].g.M * steps[k].g.N * steps[k].g.K;
-                    if (fp64_gemm_engine() == MSP_GEMM_TENSOR_CORES && work >= 134217728.0) {
+                    if (fp64_gemm_engine() == MSP_GEMM_TENSOR_CORES && work >= 8388608.0) {
                         std::vector<GemmDesc> hg;
                         for (size_t k = si; k < sj; ++k) hg.push_back(steps[k].g);
                         if (ozaki_gemm_supported(hg)) {
@@ -628,7 +701,14 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                 gi += sj - si;
                 si = sj - 1;
             } else if (st.kind == 1) {
-                potrf_tile_kernel<T><<<1, 256, 0, s>>>(st.ptr, st.ld, st.nb, st.inv, fail.p);
+                potrf_tile_kernel<T><<<1, 256, 0, s>>>(st.ptr, st.ld, st.nb, fail.p);
+                count_launches(1);
+            } else if (st.kind == 6) {
+                trsm_panel_kernel<T><<<(st.nr + kTrsmRows - 1) / kTrsmRows, 64, 0, s>>>(st.src, st.lds, st.ptr, st.ld,
+                                                                                      st.nr, st.nb);
+                count_launches(1);
+            } else if (st.kind == 7) {
+                tile_inverse_kernel<T><<<st.nr, 256, 0, s>>>(st.ptr, st.nb, st.inv);
                 count_launches(1);
             } else if (st.kind == 2) {
                 zero_upper_kernel<T><<<grid_for((long long)st.nb * st.nb), 256, 0, s>>>(st.ptr, st.nb);
