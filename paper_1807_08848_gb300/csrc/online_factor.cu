@@ -210,42 +210,44 @@ __global__ void __launch_bounds__(256) tile_inverse_kernel(const T* D, int n, T*
 }
 
 // Panel of the block Cholesky: P <- P L^{-T} for the m x nb panel P (ld ldp) under
-// the factored diagonal tile L (nb x nb lower, ld ldl), by forward substitution on
-// every row: x_j = (p_j - sum_{l<j} L[j][l] x_l) / L[j][j].  One CTA of 64 threads
-// per 16 rows, four lanes per row, each summing every fourth term, combined by
-// shuffles in a fixed order.
-constexpr int kTrsmRows = 16;
+// the factored diagonal tile L (nb x nb lower, ld ldl): every row x solves
+// L x^T = p^T by column-oriented forward substitution, x_j = x_j / L[j][j], then
+// x_l -= L[l][j] x_j for l > j.  One warp per row, lane l holding x_l and x_{l+32}
+// in registers, x_j passed by one shuffle per column, so the chain of a column is
+// one product, one shuffle and one FMA; eight rows per CTA share L in shared memory.
+constexpr int kTrsmRows = 8;
 template <class T>
-__global__ void __launch_bounds__(64) trsm_panel_kernel(const T* Lkk, int ldl, T* P, int ldp, int m, int nb) {
+__global__ void __launch_bounds__(32 * kTrsmRows) trsm_panel_kernel(const T* Lkk, int ldl, T* P, int ldp, int m,
+                                                                  int nb) {
     __shared__ T L[kTile][kTile + 1];
-    __shared__ T X[kTrsmRows][kTile + 1];
     __shared__ T rd[kTile];
-    const int tid = threadIdx.x, r0 = blockIdx.x * kTrsmRows;
+    const int tid = threadIdx.x, lane = tid & 31;
     for (int e = tid; e < nb * nb; e += blockDim.x) {
         const int i = e % nb, j = e / nb;
         L[i][j] = (i >= j) ? Lkk[i + (long long)j * ldl] : T(0);
     }
-    for (int e = tid; e < kTrsmRows * nb; e += blockDim.x) {
-        const int i = e % kTrsmRows, j = e / kTrsmRows;
-        X[i][j] = r0 + i < m ? P[(r0 + i) + (long long)j * ldp] : T(0);
-    }
     __syncthreads();
     for (int i = tid; i < nb; i += blockDim.x) rd[i] = T(1) / L[i][i];
     __syncthreads();
-    const int row = tid >> 2, part = tid & 3;
+    const int row = blockIdx.x * kTrsmRows + (tid >> 5);
+    if (row >= m) return;   // warp-uniform; no barrier follows
+    T* pr = P + row;
+    const int l1 = lane + 32;
+    T x0 = lane < nb ? pr[(long long)lane * ldp] : T(0);
+    T x1 = l1 < nb ? pr[(long long)l1 * ldp] : T(0);
     for (int j = 0; j < nb; ++j) {
-        T acc = T(0);
-        for (int l = part; l < j; l += 4) acc = fma(L[j][l], X[row][l], acc);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (part == 0) X[row][j] = (X[row][j] - acc) * rd[j];
-        __syncwarp();
+        T v = j < 32 ? x0 : x1;
+        if (lane == (j & 31)) {
+            v *= rd[j];
+            if (j < 32) x0 = v;
+            else x1 = v;
+        }
+        const T xj = __shfl_sync(0xffffffffu, v, j & 31);
+        if (lane > j && lane < nb) x0 = fma(-L[lane][j], xj, x0);
+        if (l1 > j && l1 < nb) x1 = fma(-L[l1][j], xj, x1);
     }
-    __syncthreads();
-    for (int e = tid; e < kTrsmRows * nb; e += blockDim.x) {
-        const int i = e % kTrsmRows, j = e / kTrsmRows;
-        if (r0 + i < m) P[(r0 + i) + (long long)j * ldp] = X[i][j];
-    }
+    if (lane < nb) pr[(long long)lane * ldp] = x0;
+    if (l1 < nb) pr[(long long)l1 * ldp] = x1;
 }
 
 template <class T>
@@ -514,7 +516,10 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         // with their descriptors resident in one device array.
         struct Step {
             int kind;        // 0 gemm, 1 potrf tile, 2 zero upper, 3 copy tile, 4 zero fill, 5 pivot check,
-                             // 6 panel triangular solve, 7 inverses of the diagonal tiles
+                             // 6 panel triangular solve, 7 inverses of the diagonal tiles, 8 join of
+                             // the side stream into the main one
+            int stream = 0;  // 0 the caller's stream, 1 the side stream of the trailing updates
+            int wait_ev = -1, rec_ev = -1;   // event waited on before the step, recorded after it
             GemmDescT<T> g;
             bool tA, tB;
             T* ptr;
@@ -570,11 +575,27 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                     ts.nr = m;
                     ts.nb = nb;
                     steps.push_back(ts);
-                    // trailing -= panel panel^T
-                    add_gemm(panel, n, panel, n, Dq + (r0 + nb) + (long long)(r0 + nb) * n, n, m, m, nb, T(-1), T(1), false,
-                             true, 1);
+                    steps.back().rec_ev = 0;          // panel kt final
+                    // trailing -= panel panel^T, with a lookahead of one tile: the next tile
+                    // column first, on the caller's stream (after the previous rest, which
+                    // also writes it), so that the next tile's factorisation and panel solve
+                    // run while the rest of the update runs on the side stream
+                    const int nb1 = std::min(kTile, m);
+                    add_gemm(panel, n, panel, n, Dq + (r0 + nb) + (long long)(r0 + nb) * n, n, m, nb1, nb, T(-1), T(1),
+                             false, true);
+                    steps.back().wait_ev = 1;
+                    if (m > nb1) {
+                        add_gemm(panel + nb1, n, panel + nb1, n, Dq + (r0 + nb + nb1) + (long long)(r0 + nb + nb1) * n, n,
+                                 m - nb1, m - nb1, nb, T(-1), T(1), false, true, 1);
+                        steps.back().stream = 1;
+                        steps.back().wait_ev = 0;
+                        steps.back().rec_ev = 1;
+                    }
                 }
             }
+            Step jn{};   // the side stream's trailing updates end before the block's other steps
+            jn.kind = 8;
+            steps.push_back(jn);
             Step ti{};   // inverses of the diagonal tiles, off the chain of the tile factorisations
             ti.kind = 7;
             ti.ptr = Dq;
@@ -667,8 +688,30 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         DevBuf<GemmDescT<T>> d_all;
         MSP_TRY(upload(d_all, gds, s));
         size_t gi = 0;
+        // side stream of the trailing updates and its events (panel final, rest of a
+        // trailing update done, join), released on every way out
+        struct SideStream {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+            ~SideStream() {
+                if (st) cudaStreamSynchronize(st);
+                for (cudaEvent_t e : ev)
+                    if (e) cudaEventDestroy(e);
+                if (st) cudaStreamDestroy(st);
+            }
+        } side;
+        MSP_CUDA(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : side.ev) MSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        OzakiWork ozw_side;   // the tensor-core products of the side stream have their own workspace
         for (size_t si = 0; si < steps.size(); ++si) {
             const Step& st = steps[si];
+            const cudaStream_t ss = st.stream ? side.st : s;
+            if (st.wait_ev >= 0) MSP_CUDA(cudaStreamWaitEvent(ss, side.ev[st.wait_ev], 0));
+            if (st.kind == 8) {
+                MSP_CUDA(cudaEventRecord(side.ev[2], side.st));
+                MSP_CUDA(cudaStreamWaitEvent(s, side.ev[2], 0));
+                continue;
+            }
             if (st.kind == 0) {
                 // consecutive GEMMs of one group (independent outputs) go out as one batch
                 size_t sj = si + 1;
@@ -690,22 +733,24 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                         for (size_t k = si; k < sj; ++k) hg.push_back(steps[k].g);
                         if (ozaki_gemm_supported(hg)) {
                             MSP_TRY(ozaki_gemm_batched(hg, reinterpret_cast<const GemmDesc*>(d_all.p + gi), st.tA, st.tB,
-                                                       s, ozw));
+                                                       ss, st.stream ? ozw_side : ozw));
                             on_tc = true;
                         }
                     }
                 }
                 if (!on_tc)
-                    gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, s,
+                    gemm_batched<T>(d_all.p + gi, (int)(sj - si), mm, nn, st.tA, st.tB, ss,
                                     (sj - si == 1 && g0.C == g0.A ? kGemmInPlace : 0u) | (structured ? kGemmStructured : 0u));
                 gi += sj - si;
                 si = sj - 1;
+                if (steps[si].rec_ev >= 0) MSP_CUDA(cudaEventRecord(side.ev[steps[si].rec_ev], ss));
+                continue;
             } else if (st.kind == 1) {
                 potrf_tile_kernel<T><<<1, 256, 0, s>>>(st.ptr, st.ld, st.nb, fail.p);
                 count_launches(1);
             } else if (st.kind == 6) {
-                trsm_panel_kernel<T><<<(st.nr + kTrsmRows - 1) / kTrsmRows, 64, 0, s>>>(st.src, st.lds, st.ptr, st.ld,
-                                                                                      st.nr, st.nb);
+                trsm_panel_kernel<T><<<(st.nr + kTrsmRows - 1) / kTrsmRows, 32 * kTrsmRows, 0, s>>>(
+                    st.src, st.lds, st.ptr, st.ld, st.nr, st.nb);
                 count_launches(1);
             } else if (st.kind == 7) {
                 tile_inverse_kernel<T><<<st.nr, 256, 0, s>>>(st.ptr, st.nb, st.inv);
@@ -725,11 +770,14 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                 MSP_CUDA(cudaStreamSynchronize(s));
                 if (hfail) break;
             }
+            if (st.rec_ev >= 0) MSP_CUDA(cudaEventRecord(side.ev[st.rec_ev], ss));
         }
         MSP_CUDA(cudaGetLastError());
         MSP_CUDA(cudaMemcpyAsync(&hfail, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         MSP_CUDA(cudaStreamSynchronize(s));
+        MSP_CUDA(cudaStreamSynchronize(side.st));
         MSP_TRY(ozaki_check(ozw, s));
+        MSP_TRY(ozaki_check(ozw_side, side.st));
         B.bt_shift = shift;
     }
     *fail_out = hfail;
