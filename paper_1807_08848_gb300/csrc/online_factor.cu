@@ -520,6 +520,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                              // the side stream into the main one
             int stream = 0;  // 0 the caller's stream, 1 the side stream of the trailing updates
             int wait_ev = -1, rec_ev = -1;   // event waited on before the step, recorded after it
+            bool chain = false;  // a product on the chain of tile steps: CUDA cores (no slicing launches)
             GemmDescT<T> g;
             bool tA, tB;
             T* ptr;
@@ -584,6 +585,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                     add_gemm(panel, n, panel, n, Dq + (r0 + nb) + (long long)(r0 + nb) * n, n, m, nb1, nb, T(-1), T(1),
                              false, true);
                     steps.back().wait_ev = 1;
+                    steps.back().chain = true;
                     if (m > nb1) {
                         add_gemm(panel + nb1, n, panel + nb1, n, Dq + (r0 + nb + nb1) + (long long)(r0 + nb + nb1) * n, n,
                                  m - nb1, m - nb1, nb, T(-1), T(1), false, true, 1);
@@ -728,7 +730,7 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
                     // a group worth at least ~2^23 multiply-adds goes to the tensor cores
                     double work = 0.0;
                     for (size_t k = si; k < sj; ++k) work += (double)steps[k].g.M * steps[k].g.N * steps[k].g.K;
-                    if (fp64_gemm_engine() == MSP_GEMM_TENSOR_CORES && work >= 8388608.0) {
+                    if (fp64_gemm_engine() == MSP_GEMM_TENSOR_CORES && work >= 8388608.0 && !st.chain) {
                         std::vector<GemmDesc> hg;
                         for (size_t k = si; k < sj; ++k) hg.push_back(steps[k].g);
                         if (ozaki_gemm_supported(hg)) {
