@@ -15,7 +15,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <map>
 #include <utility>
 
 namespace msp {
@@ -947,58 +946,74 @@ msp_status finish_basis(Basis& B, const double* aE_dev, const double* aN_dev, cu
     }
     B.slot_off[np] = slots;
     B.n_slots = slots;
-    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> skel;   // (j, i) -> (m, t)
+    // skeleton nodes in row-major node order, each with the (patch, ring position)
+    // pairs that hold it in patch order: a counting pass over the nodes of the grid
+    const long long nn = (long long)(N + 1) * (N + 1);
+    std::vector<int> node_cnt(nn + 1, 0);
     for (int m = 0; m < np; ++m) {
         const PatchDev& P = B.patches[m];
         for (int t = 0; t < B.n_e[m]; ++t) {
             int i, j;
             ring_node(P.x0, P.x1, P.y0, P.y1, t, i, j);
-            skel[{j, i}].push_back({m, t});
+            ++node_cnt[(long long)j * (N + 1) + i + 1];
+        }
+    }
+    for (long long v = 0; v < nn; ++v) node_cnt[v + 1] += node_cnt[v];
+    std::vector<int> holder(node_cnt[nn]);   // slot of (m, t), grouped by node, patches ascending
+    {
+        std::vector<int> cur(node_cnt.begin(), node_cnt.end() - 1);
+        for (int m = 0; m < np; ++m) {
+            const PatchDev& P = B.patches[m];
+            for (int t = 0; t < B.n_e[m]; ++t) {
+                int i, j;
+                ring_node(P.x0, P.x1, P.y0, P.y1, t, i, j);
+                holder[cur[(long long)j * (N + 1) + i]++] = B.slot_off[m] + 2 * t;
+            }
         }
     }
     std::vector<int> row_ptr{0}, row_slot, row_bnd, sk_ptr{0}, sk_slot, sk_node, sk_ring;
     const unsigned neg = 0x80000000u;
-    for (auto& kv : skel) {
-        const int j = kv.first.first, i = kv.first.second;
-        auto lst = kv.second;
-        std::sort(lst.begin(), lst.end());
+    for (long long v = 0; v < nn; ++v) {
+        const int h0 = node_cnt[v], h1 = node_cnt[v + 1];
+        if (h0 == h1) continue;
+        const int j = (int)(v / (N + 1)), i = (int)(v % (N + 1));
         const bool bnd = (i == 0 || i == N || j == 0 || j == N);
-        for (auto& mt : lst) sk_slot.push_back(B.slot_off[mt.first] + 2 * mt.second);
+        for (int h = h0; h < h1; ++h) sk_slot.push_back(holder[h]);
         sk_ptr.push_back((int)sk_slot.size());
-        sk_node.push_back(j * (N + 1) + i);
+        sk_node.push_back((int)v);
         sk_ring.push_back(bnd ? domain_ring_pos(N, i, j) : -1);
         if (bnd) {
             if (B.no_boundary_rows) continue;   // constrained variant: the boundary data hold exactly
-            for (auto& mt : lst) {
-                row_slot.push_back(B.slot_off[mt.first] + 2 * mt.second);
+            for (int h = h0; h < h1; ++h) {
+                row_slot.push_back(holder[h]);
                 row_ptr.push_back((int)row_slot.size());
                 row_bnd.push_back(domain_ring_pos(N, i, j));
             }
         } else {
-            for (size_t r = 1; r < lst.size(); ++r) {
-                row_slot.push_back(B.slot_off[lst[0].first] + 2 * lst[0].second);
-                row_slot.push_back((int)((unsigned)(B.slot_off[lst[r].first] + 2 * lst[r].second) | neg));
+            for (int h = h0 + 1; h < h1; ++h) {
+                row_slot.push_back(holder[h0]);
+                row_slot.push_back((int)((unsigned)holder[h] | neg));
                 row_ptr.push_back((int)row_slot.size());
                 row_bnd.push_back(-1);
             }
-            for (auto& mt : lst) row_slot.push_back(B.slot_off[mt.first] + 2 * mt.second + 1);
+            for (int h = h0; h < h1; ++h) row_slot.push_back(holder[h] + 1);
             row_ptr.push_back((int)row_slot.size());
             row_bnd.push_back(-1);
         }
     }
     B.n_rows = (int)row_bnd.size();
     B.n_skel = (int)sk_node.size();
-    // transpose: per slot, rows touching it
-    std::vector<std::vector<int>> tl(slots);
-    for (int r = 0; r < B.n_rows; ++r)
-        for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-            const unsigned v = (unsigned)row_slot[e];
-            tl[v & 0x7fffffffu].push_back((int)((unsigned)r | (v & neg)));
-        }
-    std::vector<int> tr_ptr{0}, tr_ent;
-    for (int g = 0; g < slots; ++g) {
-        for (int v : tl[g]) tr_ent.push_back(v);
-        tr_ptr.push_back((int)tr_ent.size());
+    // transpose: per slot, the rows touching it (rows ascending), by a counting pass
+    std::vector<int> tr_ptr(slots + 1, 0), tr_ent(row_slot.size());
+    for (size_t e = 0; e < row_slot.size(); ++e) ++tr_ptr[((unsigned)row_slot[e] & 0x7fffffffu) + 1];
+    for (int g = 0; g < slots; ++g) tr_ptr[g + 1] += tr_ptr[g];
+    {
+        std::vector<int> cur(tr_ptr.begin(), tr_ptr.end() - 1);
+        for (int r = 0; r < B.n_rows; ++r)
+            for (int e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+                const unsigned v = (unsigned)row_slot[e];
+                tr_ent[cur[v & 0x7fffffffu]++] = (int)((unsigned)r | (v & neg));
+            }
     }
     MSP_TRY(upload(B.row_ptr, row_ptr, s)); MSP_TRY(upload(B.row_slot, row_slot, s)); MSP_TRY(upload(B.row_bnd, row_bnd, s));
     MSP_TRY(upload(B.tr_ptr, tr_ptr, s)); MSP_TRY(upload(B.tr_ent, tr_ent, s));

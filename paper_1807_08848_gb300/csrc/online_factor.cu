@@ -22,7 +22,6 @@
 #include "device_util.cuh"
 
 #include <algorithm>
-#include <map>
 #include <utility>
 
 namespace msp {
@@ -833,56 +832,83 @@ msp_status build_online_factor(Basis& B, const std::vector<int>& row_ptr, const 
     }
     const long long total = off;
     // pair lists: for every row and ordered pair of its entries in the same or the
-    // next-lower patch row
-    std::map<std::pair<int, int>, std::vector<std::pair<std::pair<int, int>, signed char>>> pairs;
-    for (int r = 0; r + 1 < (int)row_ptr.size(); ++r) {
-        for (int a = row_ptr[r]; a < row_ptr[r + 1]; ++a) {
-            const unsigned va = (unsigned)row_slot[a];
-            const int sa = (int)(va & 0x7fffffffu), ma = slot_patch[sa];
-            for (int b = row_ptr[r]; b < row_ptr[r + 1]; ++b) {
-                const unsigned vb = (unsigned)row_slot[b];
-                const int sb = (int)(vb & 0x7fffffffu), mb = slot_patch[sb];
-                const int qa = ma / mx, qb = mb / mx;
-                if (!(qa == qb || qa == qb + 1)) continue;
-                const signed char sg = (((va ^ vb) & 0x80000000u) ? -1 : 1);
-                pairs[{ma, mb}].push_back({{sa, sb}, sg});
+    // next-lower patch row, the (slot a, slot b, sign) triple, grouped by patch pair
+    // (ma, mb) in ascending order and in row order inside a pair.  Patches sharing a
+    // skeleton node are grid neighbours, so mb is one of six positions relative to
+    // ma (one row down or the same row, one column left, the same or one right),
+    // numbered in ascending mb; two counting passes build the groups.
+    auto pair_slot = [&](int ma, int mb) {
+        const int dq = ma / mx - mb / mx, dp = ma % mx - mb % mx;   // dq in {0, 1}, dp in {-1, 0, 1}
+        return ma * 6 + (1 - dq) * 3 + (1 - dp);
+    };
+    std::vector<int> pcount((size_t)np * 6 + 1, 0);
+    auto for_pairs = [&](auto&& fn) {
+        for (int r = 0; r + 1 < (int)row_ptr.size(); ++r)
+            for (int a = row_ptr[r]; a < row_ptr[r + 1]; ++a) {
+                const unsigned va = (unsigned)row_slot[a];
+                const int sa = (int)(va & 0x7fffffffu), ma = slot_patch[sa];
+                for (int b = row_ptr[r]; b < row_ptr[r + 1]; ++b) {
+                    const unsigned vb = (unsigned)row_slot[b];
+                    const int sb = (int)(vb & 0x7fffffffu), mb = slot_patch[sb];
+                    const int qa = ma / mx, qb = mb / mx;
+                    if (!(qa == qb || qa == qb + 1)) continue;
+                    fn(ma, mb, sa, sb, (signed char)(((va ^ vb) & 0x80000000u) ? -1 : 1));
+                }
             }
-        }
+    };
+    bool adjacency_ok = true;
+    for_pairs([&](int ma, int mb, int, int, signed char) {
+        const int dp = ma % mx - mb % mx;
+        if (dp < -1 || dp > 1) adjacency_ok = false;
+        else ++pcount[pair_slot(ma, mb) + 1];
+    });
+    if (!adjacency_ok) {
+        set_error("msp_extract_basis: a skeleton row couples patches that are not grid neighbours");
+        return MSP_ERR_INVALID_ARG;
+    }
+    for (size_t t = 0; t + 1 < pcount.size(); ++t) pcount[t + 1] += pcount[t];
+    std::vector<int> lsa(pcount.back()), lsb(pcount.back());
+    std::vector<signed char> lsg(pcount.back());
+    {
+        std::vector<int> cur(pcount.begin(), pcount.end() - 1);
+        for_pairs([&](int ma, int mb, int sa, int sb, signed char sg) {
+            const int at = cur[pair_slot(ma, mb)]++;
+            lsa[at] = sa;
+            lsb[at] = sb;
+            lsg[at] = sg;
+        });
     }
     std::vector<PairBlock> pb;
     B.bt_elo.assign(np, -1);
     B.bt_ehi.assign(np, -1);
-    std::vector<int> lsa, lsb;
-    std::vector<signed char> lsg;
-    for (auto& kv : pairs) {
-        const int ma = kv.first.first, mb = kv.first.second;
-        if (B.k[ma] == 0 || B.k[mb] == 0) continue;
-        const int qa = ma / mx, qb = mb / mx;
-        PairBlock p{};
-        p.ma = ma;
-        p.mb = mb;
-        p.list_begin = (int)lsa.size();
-        for (auto& e : kv.second) {
-            lsa.push_back(e.first.first);
-            lsb.push_back(e.first.second);
-            lsg.push_back(e.second);
+    for (int ma = 0; ma < np; ++ma)
+        for (int c = 0; c < 6; ++c) {
+            const int t = ma * 6 + c;
+            if (pcount[t] == pcount[t + 1]) continue;
+            const int dq = 1 - c / 3, dp = 1 - c % 3;
+            const int mb = ma - dq * mx - dp;
+            if (B.k[ma] == 0 || B.k[mb] == 0) continue;
+            const int qa = ma / mx, qb = mb / mx;
+            PairBlock p{};
+            p.ma = ma;
+            p.mb = mb;
+            p.list_begin = pcount[t];
+            p.list_end = pcount[t + 1];
+            if (qa == qb) {
+                const int n = B.bt_off[qa + 1] - B.bt_off[qa];
+                p.dst = B.bt_d_off[qa] + (B.c_off[ma] - B.bt_off[qa]) + (long long)(B.c_off[mb] - B.bt_off[qb]) * n;
+                p.ld = n;
+            } else {   // E_qb: rows from block qb+1, columns from block qb
+                const int n1 = B.bt_off[qa + 1] - B.bt_off[qa];
+                p.dst = B.bt_e_off[qb] + (B.c_off[ma] - B.bt_off[qa]) + (long long)(B.c_off[mb] - B.bt_off[qb]) * n1;
+                p.ld = n1;
+            }
+            pb.push_back(p);
+            if (qa == qb + 1) {   // patch ma (row qb+1) couples with patch mb of row qb
+                B.bt_elo[ma] = B.bt_elo[ma] < 0 ? mb : std::min(B.bt_elo[ma], mb);
+                B.bt_ehi[ma] = std::max(B.bt_ehi[ma], mb);
+            }
         }
-        p.list_end = (int)lsa.size();
-        if (qa == qb) {
-            const int n = B.bt_off[qa + 1] - B.bt_off[qa];
-            p.dst = B.bt_d_off[qa] + (B.c_off[ma] - B.bt_off[qa]) + (long long)(B.c_off[mb] - B.bt_off[qb]) * n;
-            p.ld = n;
-        } else {   // E_qb: rows from block qb+1, columns from block qb
-            const int n1 = B.bt_off[qa + 1] - B.bt_off[qa];
-            p.dst = B.bt_e_off[qb] + (B.c_off[ma] - B.bt_off[qa]) + (long long)(B.c_off[mb] - B.bt_off[qb]) * n1;
-            p.ld = n1;
-        }
-        pb.push_back(p);
-        if (qa == qb + 1) {   // patch ma (row qb+1) couples with patch mb of row qb
-            B.bt_elo[ma] = B.bt_elo[ma] < 0 ? mb : std::min(B.bt_elo[ma], mb);
-            B.bt_ehi[ma] = std::max(B.bt_ehi[ma], mb);
-        }
-    }
     DevBuf<PairBlock> d_pb;
     DevBuf<int> d_lsa, d_lsb;
     DevBuf<signed char> d_lsg;
