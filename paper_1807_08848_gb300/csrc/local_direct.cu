@@ -89,7 +89,15 @@ __host__ __device__ inline Geo geo(const PatchDev& P) {
 __device__ __forceinline__ int swz(int k, int c) { return k * kCB + ((((c >> 2) ^ (k & 7))) << 2) + (c & 3); }
 
 // ------------------------------------------------------------------ factor
-// One CTA per patch: s, the couplings c_j, and W_j = Z_j^{-1} row by row.
+// One CTA per patch: s, the couplings c_j, and W_j = Z_j^{-1} row by row.  The
+// block lives in registers: thread (tr, tc) of a 16 x 16 layout holds the TS x TS
+// sub-block of rows tr TS .., columns tc TS .. (TS = ceil(ld / 16), one value for the
+// launch).  Z_j = T_j - C_{j-1} W_{j-1} C_{j-1} is formed elementwise from the
+// registers holding W_{j-1}; Gauss-Jordan inversion in place without pivoting (Z_j
+// is SPD), one barrier per pivot: after updating, the owners of row and column k+1
+// publish them to double-buffered shared rows for the next pivot.  W_j^T goes to
+// global memory through a padded shared copy (coalesced stores).
+template <int TS>
 __global__ void __launch_bounds__(kDirThreads) direct_factor_kernel(DirArgs A) {
     extern __shared__ __align__(16) float fsm[];
     const int m = blockIdx.x;
@@ -97,10 +105,10 @@ __global__ void __launch_bounds__(kDirThreads) direct_factor_kernel(DirArgs A) {
     const Geo g = geo(P);
     if (g.nx < 1 || g.ny < 1) return;
     const int n = g.nx, ld = g.ld, N = A.N;
-    float* Z = fsm;                // ld x ld, the block being inverted
-    float* Wp = Z + ld * ld;       // ld x ld, W_{j-1}
-    float* rowk = Wp + ld * ld;    // ld
-    float* colk = rowk + ld;       // ld
+    constexpr int kW = 16 * TS;    // rows (and columns) the thread layout covers
+    float* Zs = fsm;               // ld x (ld + 1): staging of W_j for the transposed store
+    float* rb = Zs + ld * (ld + 1);   // 2 x kW: row k of the current block
+    float* cb = rb + 2 * kW;          // 2 x kW: column k
     double* sv = A.s + A.s_off[m];
     float* Dv = A.D + A.s_off[m];
     float* Wout = A.W + A.w_off[m];
@@ -122,59 +130,93 @@ __global__ void __launch_bounds__(kDirThreads) direct_factor_kernel(DirArgs A) {
         }
         Dv[t] = c;
     }
-    for (int t = threadIdx.x; t < ld * ld; t += blockDim.x) Wp[t] = 0.f;
     __syncthreads();
-    // 2-D thread layout for the rank-1 updates: 16 x 16 threads, strided loops
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+    const int r0 = (threadIdx.x >> 4) * TS, c0 = (threadIdx.x & 15) * TS;
+    float z[TS][TS];
+#pragma unroll
+    for (int a = 0; a < TS; ++a)
+#pragma unroll
+        for (int b = 0; b < TS; ++b) z[a][b] = 0.f;
     for (int j = 0; j < g.ny; ++j) {
         const long long gj = P.Y0 + 1 + j;
-        for (int r = tr; r < ld; r += 16) {
-            for (int c = tc; c < ld; c += 16) {
-                float v = 0.f;
+        // Z_j from T_j and the registers holding W_{j-1}; identity on the padding
+#pragma unroll
+        for (int a = 0; a < TS; ++a) {
+            const int r = r0 + a;
+            const float dr = (j > 0 && r < n) ? Dv[(j - 1) * n + r] : 0.f;
+#pragma unroll
+            for (int b = 0; b < TS; ++b) {
+                const int c = c0 + b;
+                float v = (r == c) ? 1.f : 0.f;
                 if (r < n && c < n) {
-                    if (r == c) {
-                        v = 1.f;
-                    } else if (c == r + 1 || c + 1 == r) {
+                    if (c == r + 1 || c + 1 == r) {
                         const int i = min(r, c);
                         v = -(float)(aE[gj * N + P.X0 + 1 + i] * sv[j * n + i] * sv[j * n + i + 1]);
                     }
-                    if (j > 0) v -= Dv[(j - 1) * n + r] * Wp[r * ld + c] * Dv[(j - 1) * n + c];
-                } else if (r == c) {
-                    v = 1.f;
+                    if (j > 0) v -= dr * z[a][b] * Dv[(j - 1) * n + c];
                 }
-                Z[r * ld + c] = v;
+                z[a][b] = v;
             }
         }
+        // publish row 0 and column 0
+        if (r0 == 0)
+#pragma unroll
+            for (int b = 0; b < TS; ++b) rb[c0 + b] = z[0][b];
+        if (c0 == 0)
+#pragma unroll
+            for (int a = 0; a < TS; ++a) cb[r0 + a] = z[a][0];
         __syncthreads();
-        // Gauss-Jordan inversion in place; Z is symmetric positive definite, so the
-        // pivots are positive without row exchanges
         for (int k = 0; k < n; ++k) {
-            const float inv = 1.f / Z[k * ld + k];
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                rowk[t] = Z[k * ld + t] * inv;
-                colk[t] = Z[t * ld + k];
-            }
-            __syncthreads();
-            for (int r = tr; r < n; r += 16) {
-                const float cr = colk[r];
-                for (int c = tc; c < n; c += 16) {
-                    float v;
-                    if (r == k) v = (c == k) ? inv : rowk[c];
-                    else if (c == k) v = -cr * inv;
-                    else v = Z[r * ld + c] - cr * rowk[c];
-                    Z[r * ld + c] = v;
+            const int p = (k & 1) * kW, q = kW - p;
+            const float inv = 1.f / cb[p + k];
+            float fr[TS], rk[TS];
+#pragma unroll
+            for (int a = 0; a < TS; ++a) fr[a] = cb[p + r0 + a] * inv;
+#pragma unroll
+            for (int b = 0; b < TS; ++b) rk[b] = rb[p + c0 + b];
+#pragma unroll
+            for (int a = 0; a < TS; ++a) {
+                const int r = r0 + a;
+#pragma unroll
+                for (int b = 0; b < TS; ++b) {
+                    const int c = c0 + b;
+                    float v = z[a][b];
+                    if (r != k && c != k) v = fmaf(-fr[a], rk[b], v);
+                    else if (r == k && c != k) v = rk[b] * inv;
+                    else if (r != k) v = -fr[a];
+                    else v = inv;
+                    z[a][b] = v;
                 }
+            }
+            // publish row k+1 and column k+1 of the updated block for the next pivot
+            const int k1 = k + 1;
+            if (k1 < n) {
+#pragma unroll
+                for (int a = 0; a < TS; ++a)
+                    if (r0 + a == k1)
+#pragma unroll
+                        for (int b = 0; b < TS; ++b) rb[q + c0 + b] = z[a][b];
+#pragma unroll
+                for (int b = 0; b < TS; ++b)
+                    if (c0 + b == k1)
+#pragma unroll
+                        for (int a = 0; a < TS; ++a) cb[q + r0 + a] = z[a][b];
             }
             __syncthreads();
         }
-        // W_j^T to global (padding zero); W_j kept for the next row's Schur complement
-        float* wj = Wout + (long long)j * ld * ld;
-        for (int r = tr; r < ld; r += 16) {
-            for (int c = tc; c < ld; c += 16) {
-                const bool in = r < n && c < n;
-                wj[r * ld + c] = in ? Z[c * ld + r] : 0.f;
-                Wp[r * ld + c] = in ? Z[r * ld + c] : 0.f;
+        // W_j^T to global (padding zero) through the padded shared copy
+#pragma unroll
+        for (int a = 0; a < TS; ++a)
+#pragma unroll
+            for (int b = 0; b < TS; ++b) {
+                const int r = r0 + a, c = c0 + b;
+                if (r < ld && c < ld) Zs[r * (ld + 1) + c] = (r < n && c < n) ? z[a][b] : 0.f;
             }
+        __syncthreads();
+        float* wj = Wout + (long long)j * ld * ld;
+        for (int t = threadIdx.x; t < ld * ld; t += blockDim.x) {
+            const int r = t / ld, c = t - r * ld;
+            wj[t] = Zs[c * (ld + 1) + r];
         }
         __syncthreads();
     }
@@ -447,7 +489,7 @@ msp_status direct_plan(Medium& M, cudaStream_t s) {
         for (int q = 0; q < nch; ++q) chunks.push_back(make_int4(m, q * kCB, std::min(kCB, P.cols - q * kCB), q));
         max_ld = std::max(max_ld, g.ld);
         const int G = std::max(1, (g.ld + 31) / 32);
-        fsm = std::max(fsm, (int)sizeof(float) * (2 * g.ld * g.ld + 2 * g.ld));
+        fsm = std::max(fsm, (int)sizeof(float) * (g.ld * (g.ld + 1) + 4 * 16 * std::max(1, (g.ld + 15) / 16)));
         csm = std::max(csm, (int)sizeof(float) * (g.ld * g.ld + 32 * G + 2 * g.ld * kCB));
     }
     // statistics slot of every column: its position in the mixed-precision item order
@@ -547,6 +589,13 @@ bool direct_fits(const Medium& M) {
     return !M.patches.empty();
 }
 
+template <int TS>
+static msp_status launch_factor(const DirArgs& A, int np, int smem, cudaStream_t s) {
+    MSP_CUDA(cudaFuncSetAttribute(direct_factor_kernel<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    direct_factor_kernel<TS><<<np, kDirThreads, smem, s>>>(A);
+    return MSP_OK;
+}
+
 msp_status launch_local_solves_direct(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s) {
     if (!direct_fits(M)) {
         set_error("direct local solver: a buffered patch is wider than 160 interior nodes");
@@ -558,10 +607,20 @@ msp_status launch_local_solves_direct(Medium& M, const LocalSolveCfg& cfg, cudaS
     const int np = (int)M.patches.size();
     D.ev_used = 0;
     if (!D.factored) {
-        MSP_CUDA(cudaFuncSetAttribute(direct_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      D.factor_smem_max));
         MSP_TRY(mark(D, kPhFactor, true, s));
-        direct_factor_kernel<<<np, kDirThreads, D.factor_smem_max, s>>>(A);
+        // one sub-block size for the launch, from the widest padded row
+        switch (std::max(1, (D.max_nxp + 15) / 16)) {
+            case 1: MSP_TRY(launch_factor<1>(A, np, D.factor_smem_max, s)); break;
+            case 2: MSP_TRY(launch_factor<2>(A, np, D.factor_smem_max, s)); break;
+            case 3: MSP_TRY(launch_factor<3>(A, np, D.factor_smem_max, s)); break;
+            case 4: MSP_TRY(launch_factor<4>(A, np, D.factor_smem_max, s)); break;
+            case 5: MSP_TRY(launch_factor<5>(A, np, D.factor_smem_max, s)); break;
+            case 6: MSP_TRY(launch_factor<6>(A, np, D.factor_smem_max, s)); break;
+            case 7: MSP_TRY(launch_factor<7>(A, np, D.factor_smem_max, s)); break;
+            case 8: MSP_TRY(launch_factor<8>(A, np, D.factor_smem_max, s)); break;
+            case 9: MSP_TRY(launch_factor<9>(A, np, D.factor_smem_max, s)); break;
+            default: MSP_TRY(launch_factor<10>(A, np, D.factor_smem_max, s)); break;
+        }
         count_launches(1);
         MSP_TRY(mark(D, kPhFactor, false, s));
         MSP_CUDA(cudaGetLastError());
