@@ -74,10 +74,16 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const SmallMat* mats, 
             const double piv = l[k + (long long)k * c];
             for (int i = k + 1 + threadIdx.x; i < c; i += blockDim.x) l[i + (long long)k * c] /= piv;
             __syncthreads();
-            const int R = c - k - 1;
-            for (long long e = threadIdx.x; e < (long long)R * R; e += blockDim.x) {
-                const int i = k + 1 + (int)(e % R), j = k + 1 + (int)(e / R);
-                if (i >= j) l[i + (long long)j * c] -= l[i + (long long)k * c] * l[j + (long long)k * c];
+            // trailing update of the lower triangle: a warp per column j, lanes along
+            // the rows i >= j (contiguous in the column-major block)
+            {
+                const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+                for (int j = k + 1 + (threadIdx.x >> 5); j < c; j += nw) {
+                    const double ljk = l[j + (long long)k * c];
+                    double* lj = l + (long long)j * c;
+                    const double* lk = l + (long long)k * c;
+                    for (int i = j + lane; i < c; i += 32) lj[i] -= lk[i] * ljk;
+                }
             }
             __syncthreads();
         }
@@ -94,14 +100,24 @@ __global__ void __launch_bounds__(256) chol_factor_kernel(const SmallMat* mats, 
         const int i = (int)(e % c), j = (int)(e / c);
         f[e] = (i <= j) ? l[j + (long long)i * c] : 0.0;
     }
-    // Fi = (L^{-1})^T: thread j forward-substitutes column j of L^{-1},
-    // X(i, j) stored at Fi(j, i) = fi[j + i c]
-    for (int j = threadIdx.x; j < c; j += blockDim.x) {
-        for (int i = 0; i < j; ++i) fi[j + (long long)i * c] = 0.0;
-        for (int i = j; i < c; ++i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int q = j; q < i; ++q) s -= l[i + (long long)q * c] * fi[j + (long long)q * c];
-            fi[j + (long long)i * c] = s / l[i + (long long)i * c];
+    // Fi = (L^{-1})^T, X = L^{-1} with X(i, j) stored at Fi(j, i) = fi[j + i c]: row i
+    // of X, X(i, j) = (delta_ij - sum_{q<i} l_iq X(q, j)) / l_ii, for all j <= i at
+    // once -- one barrier per row, a warp per column j, lanes along q, the partial
+    // sums of a warp combined by shuffles in a fixed order
+    for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) fi[e] = 0.0;
+    __syncthreads();
+    {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = 0; i < c; ++i) {
+            const double rli = 1.0 / l[i + (long long)i * c];
+            const double* li = l + i;   // l_iq at li[q c]
+            for (int j = threadIdx.x >> 5; j <= i; j += nw) {
+                double a = 0.0;
+                for (int q = j + lane; q < i; q += 32) a += li[(long long)q * c] * fi[j + (long long)q * c];
+                a = warp_sum(a);
+                if (lane == 0) fi[j + (long long)i * c] = ((i == j ? 1.0 : 0.0) - a) * rli;
+            }
+            __syncthreads();
         }
     }
 }
