@@ -413,15 +413,19 @@ msp_status msp_medium_set_launch(msp_medium m, int precision, int mode, int rows
 msp_status msp_medium_set_timing(msp_medium m, int enable);
 msp_status msp_medium_direct_timing(msp_medium m, double* ms_host, int* launches_host);
 
-/* Autotuner of that launch: every candidate (split or fused, each rows instance
+/* Autotuner of that launch: every CG candidate (split or fused, each rows instance
  * the eligible tiles fit) runs an even-strided subset of at most max_probe_items
- * of the medium's columns, once to warm up and once timed (CUDA events); the
- * fastest is kept for msp_sample_patches of that precision and reported.  The
- * probe writes the subset's snapshot columns with the values a full run writes.
- * Synchronises. */
+ * of the medium's columns, once to warm up and once timed (CUDA events).  With
+ * precision MSP_MIXED and a medium the direct solver fits, MSP_LAUNCH_DIRECT is a
+ * candidate too (rows 0): it runs the whole medium once untimed (factorising every
+ * patch; the factor is kept) and once timed, and its ms is that time scaled to the
+ * probe's share of the columns.  The fastest is kept for msp_sample_patches of that
+ * precision and reported.  The CG probes write the subset's snapshot columns with
+ * the values a full run writes; the direct candidate writes every column (its own
+ * values, replaced by the next msp_sample_patches).  Synchronises. */
 #define MSP_TUNE_MAX_CANDIDATES 8
 typedef struct {
-    int mode, rows;
+    int mode, rows;    /* mode: MSP_LAUNCH_SPLIT, MSP_LAUNCH_FUSED or MSP_LAUNCH_DIRECT */
     float ms;          /* device time of the probe; -1 if the configuration does not fit */
 } msp_tune_candidate;
 typedef struct {

@@ -163,13 +163,15 @@ class Medium:
 
     def autotune(self, seed: int, precision="mixed", tol: float = 1e-10, max_iter: int = 20000,
                  max_probe_items: int = 2048, stream=None) -> dict:
-        """Time every launch configuration on a subset of the columns and keep the fastest."""
+        """Time every launch configuration (CG on a subset of the columns, the direct
+        solver on the whole medium) and keep the fastest."""
         r = N.TuneReport()
         N.check(N.load().msp_medium_autotune(self._h, precision_code(precision), C.c_uint64(seed), tol, max_iter,
                                              max_probe_items, _stream_ptr(stream), C.byref(r)))
-        return {"probe_items": r.probe_items, "best_mode": ["split", "fused"][r.best_mode],
+        names = ["split", "fused", "direct"]
+        return {"probe_items": r.probe_items, "best_mode": names[r.best_mode],
                 "best_rows": r.best_rows, "best_ms": r.best_ms,
-                "candidates": [{"mode": ["split", "fused"][c.mode], "rows": c.rows, "ms": c.ms}
+                "candidates": [{"mode": names[c.mode], "rows": c.rows, "ms": c.ms}
                                for c in r.candidates[:r.n_candidates]]}
 
     def tile_shape(self):

@@ -181,6 +181,7 @@ struct Medium {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     double graph_key[2][6] = {};
+    long long graph_launches[2] = {0, 0};   // kernel launches one replay of the graph makes
 };
 
 // Ring node t of node box (X0,X1,Y0,Y1): counter-clockwise from (X0,Y0).

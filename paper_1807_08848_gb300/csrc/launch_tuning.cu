@@ -2,12 +2,17 @@
 // instance of the tile kernel, the autotuner that picks them, and replay of the
 // launches through a CUDA graph.
 //
-// Autotuner: every candidate (split / fused x each rows instance the eligible
+// Autotuner: every CG candidate (split / fused x each rows instance the eligible
 // tiles fit) runs the same strided subset of the medium's items (both the tiles
-// that fit on chip and the rest), once to warm up and once timed with CUDA events;
-// the fastest per item is kept for msp_sample_patches.  The probe runs write the
-// snapshot columns of the subset with exactly the values a full run writes (every
-// item's arithmetic is independent of the launch), so they leave no trace.
+// that fit on chip and the rest), once to warm up and once timed with CUDA events.
+// In mixed precision the direct solver is a candidate too when the medium fits it:
+// its factorisation serves every column of a patch, so it runs the whole medium,
+// once untimed (which also factorises; the factor is kept) and once timed, its time
+// scaled to the probe's share of the columns.  The fastest per column is kept for
+// msp_sample_patches.  The CG probe runs write the snapshot columns of the subset
+// with exactly the values a full run writes (every item's arithmetic is independent
+// of the launch); the direct candidate writes every column with its own values, which
+// the next msp_sample_patches overwrites.
 #include "internal.h"
 
 #include <algorithm>
@@ -37,7 +42,7 @@ msp_status sample_launch(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s) {
     for (int i = 0; i < 6 && same; ++i) same = M.graph_key[pi][i] == key[i];
     if (same) {
         MSP_CUDA(cudaGraphLaunch(M.graph[pi], s));
-        count_launches(M.launch_mode[pi] == 1 || M.n_tile_items[pi] == M.n_items ? 1 : 2);
+        count_launches(M.graph_launches[pi]);
         return MSP_OK;
     }
     // first call of this configuration: a direct run (it sizes and allocates the
@@ -55,7 +60,8 @@ msp_status sample_launch(Medium& M, const LocalSolveCfg& cfg, cudaStream_t s) {
     const long long before = msp_kernel_launches();
     const msp_status st = launch_local_solves(M, cfg, M.capture_stream);
     cudaError_t e = cudaStreamEndCapture(M.capture_stream, &g);
-    count_launches(before - msp_kernel_launches());   // captured, not run
+    M.graph_launches[pi] = msp_kernel_launches() - before;
+    count_launches(-M.graph_launches[pi]);   // captured, not run
     if (st != MSP_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
@@ -179,6 +185,41 @@ extern "C" msp_status msp_medium_autotune(msp_medium m, int precision, uint64_t 
             }
             clear_error();
         }
+    }
+    if (precision == MSP_MIXED && direct_fits(M) && M.n_items > 0) {
+        const int saved = M.launch_mode[pi];
+        M.launch_mode[pi] = MSP_LAUNCH_DIRECT;
+        float ms = -1.f;
+        msp_status st = launch_local_solves(M, cfg, s);   // warm-up, factorisation
+        if (st == MSP_OK) {
+            MSP_CUDA(cudaEventRecord(e0, s));
+            st = launch_local_solves(M, cfg, s);
+            MSP_CUDA(cudaEventRecord(e1, s));
+            MSP_CUDA(cudaEventSynchronize(e1));
+            if (st == MSP_OK) {
+                MSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                ms *= (float)rep.probe_items / (float)M.n_items;
+            }
+        }
+        M.launch_mode[pi] = saved;
+        if (st != MSP_OK && st != MSP_ERR_INVALID_ARG) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        if (rep.n_candidates < MSP_TUNE_MAX_CANDIDATES) {
+            msp_tune_candidate& c = rep.candidates[rep.n_candidates++];
+            c.mode = MSP_LAUNCH_DIRECT;
+            c.rows = 0;
+            c.ms = st == MSP_OK ? ms : -1.f;
+        }
+        if (st == MSP_OK && (best < 0 || ms < best)) {
+            best = ms;
+            rep.best_mode = MSP_LAUNCH_DIRECT;
+            rep.best_rows = 0;
+            rep.best_ms = ms;
+        }
+        clear_error();
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

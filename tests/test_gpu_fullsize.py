@@ -85,8 +85,12 @@ def test_2049_online_boundary_data_and_least_squares_optimality(batched):
 def test_1025_uneven_sampled_patches_in_the_autotuned_launch():
     w = synth.workload_uneven()
     med = msp.Medium(w["medium"], w["patches"])
-    med.autotune(w["seed"], "mixed", tol=1e-10, max_iter=40000, max_probe_items=1024)
-    st = med.sample(w["seed"], "mixed", tol=1e-10, max_iter=40000)
+    # the solvers stop on the FP64 residual; on the channel patches (contrast 1e3) the
+    # direct solver's error per unit of residual is about 1e5, so the autotuned launch
+    # (the direct solver here) stops at 1e-12 to stay inside 1e-6 in the solution
+    rep = med.autotune(w["seed"], "mixed", tol=1e-12, max_iter=40000, max_probe_items=1024)
+    assert rep["best_mode"] in ("split", "fused", "direct")
+    st = med.sample(w["seed"], "mixed", tol=1e-12, max_iter=40000)
     assert st.n_not_converged == 0
     aE, aN = E.face_coefficients(w["medium"])
     patches = E.patch_boxes(1024, w["patches"])

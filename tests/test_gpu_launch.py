@@ -105,14 +105,23 @@ def test_graph_replay_equals_direct_launch():
 
 
 def test_autotune_reports_and_keeps_the_fastest():
+    """Every launch form is timed (the CG forms on the probe, the direct solver on
+    the whole medium), the fastest is kept, and a later sample gives what that form
+    gives when set by hand (bitwise on the patches that fit on chip) and agrees with
+    the CG split launch to the solver tolerance."""
     ms, ps = spec()
-    ref = msp.Medium(ms, ps)
-    ref.sample(4, "mixed", tol=1e-10, max_iter=40000)
     med = msp.Medium(ms, ps)
     rep = med.autotune(4, "mixed", tol=1e-10, max_iter=40000, max_probe_items=400)
     ran = [c for c in rep["candidates"] if c["ms"] > 0]
-    assert {c["mode"] for c in ran} == {"split", "fused"}
+    assert {c["mode"] for c in ran} == {"split", "fused", "direct"}
     assert rep["best_ms"] == min(c["ms"] for c in ran)
     assert 0 < rep["probe_items"] <= 400
+    ref = msp.Medium(ms, ps)
+    ref.set_launch("mixed", rep["best_mode"], rep["best_rows"])
+    ref.sample(4, "mixed", tol=1e-10, max_iter=40000)
     med.sample(4, "mixed", tol=1e-10, max_iter=40000)
     assert_same(ref, med, ps, 1e-7)
+    split = msp.Medium(ms, ps)
+    split.sample(4, "mixed", tol=1e-10, max_iter=40000)
+    for m, (x, y) in enumerate(zip(snapshots(split), snapshots(med))):
+        assert rel(y, x) <= TOL["mixed"], m
