@@ -288,7 +288,14 @@ __global__ void __launch_bounds__(kDirThreads) direct_residual_kernel(DirArgs A,
             if (c >= nc || !s_act[c]) continue;
             const double* x = A.X + A.x_off[m] + (long long)(c0 + c) * g.hd * g.wd + (j + 1) * g.wd + 1;
             float* rr = Rc + ((long long)j * kCB + c) * n;
+            // first pass: the interior of the iterate is zero, so only nodes next to the
+            // ring have a nonzero residual; the others are written as the zeros they are
+            const bool edge_only = first && j > 0 && j + 1 < g.ny;
             for (int k = lane; k < n; k += 32) {
+                if (edge_only && k > 0 && k + 1 < n) {
+                    rr[k] = 0.f;
+                    continue;
+                }
                 const long long gi = P.X0 + 1 + k;
                 const double ae = A.aE[gj * N + gi], aw = A.aE[gj * N + gi - 1];
                 const double an = A.aN[gj * (N + 1) + gi], as = A.aN[(gj - 1) * (N + 1) + gi];

@@ -41,19 +41,29 @@ struct PairBlock {
 __global__ void assemble_kernel(const PairBlock* pb, const int* list_sa, const int* list_sb, const signed char* list_sg,
                                 const int* k, const long long* e_off, const int* slot_off, const double* E,
                                 double* dst_base) {
+    // one warp per (column j, 128 rows): lanes own rows i, i + 32, i + 64, i + 96 and
+    // accumulate them from one broadcast E_b value per list entry, in list order
     const PairBlock b = pb[blockIdx.x];
     const int ka = k[b.ma], kb = k[b.mb];
     const double* Ea = E + e_off[b.ma];
     const double* Eb = E + e_off[b.mb];
     const int ga = slot_off[b.ma], gb = slot_off[b.mb];
-    for (long long w = threadIdx.x; w < (long long)ka * kb; w += blockDim.x) {
-        const int i = (int)(w % ka), j = (int)(w / ka);
-        double a = 0.0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nib = (ka + 127) / 128;
+    for (int task = threadIdx.x >> 5; task < kb * nib; task += nw) {
+        const int j = task / nib, i0 = (task - j * nib) * 128 + lane;
+        double a[4] = {0.0, 0.0, 0.0, 0.0};
         for (int t = b.list_begin; t < b.list_end; ++t) {
-            const double v = Ea[(long long)(list_sa[t] - ga) * ka + i] * Eb[(long long)(list_sb[t] - gb) * kb + j];
-            a += list_sg[t] > 0 ? v : -v;
+            const double* ea = Ea + (long long)(list_sa[t] - ga) * ka;
+            double e = Eb[(long long)(list_sb[t] - gb) * kb + j];
+            if (list_sg[t] < 0) e = -e;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + 32 * u < ka) a[u] = fma(ea[i0 + 32 * u], e, a[u]);
         }
-        dst_base[b.dst + i + (long long)j * b.ld] = a;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + 32 * u < ka) dst_base[b.dst + (i0 + 32 * u) + (long long)j * b.ld] = a[u];
     }
 }
 
