@@ -22,6 +22,12 @@
  *                       over rows of patches (or, on request, the patch blocks
  *                       alone: one-level additive Schwarz), then
  *                       u = sum_m chi_m G_m c_m with a partition of unity.
+ *   msp_online_solve_constrained, msp_ras_setup / msp_online_solve_ras
+ *                       online variants: the boundary data imposed exactly
+ *                       (the remark after Eq. elliptic_cond_reduced), and
+ *                       restricted additive Schwarz on the buffered patches
+ *                       reduced to the bases (the online step as a standard
+ *                       domain-decomposition step, Sec. 3).
  *   msp_kinetic_*       the slab radiative-transfer example of Sec. 4 with
  *                       discrete ordinates (Eq. RTE, Eq. rte_random, Eq.
  *                       rte_cond_reduced).
@@ -63,7 +69,7 @@ typedef int msp_status;
 #define MSP_ERR_INVALID_ARG   -1   /* bad pointer, size or option; nothing was launched   */
 #define MSP_ERR_OOM           -2   /* device allocation failed                             */
 #define MSP_ERR_NOT_CONVERGED -3   /* an iteration hit max_iter; results are the last iterate */
-#define MSP_ERR_BREAKDOWN     -4   /* Cholesky-QR met a non-positive pivot after all shifts */
+#define MSP_ERR_BREAKDOWN     -4   /* a factorisation broke down (non-positive pivot after all shifts, singular coarse matrix) */
 #define MSP_ERR_TIMEOUT       -5   /* a bounded wait gave up                               */
 #define MSP_ERR_CUDA          -6   /* a CUDA runtime call failed (message has the CUDA text) */
 #define MSP_ERR_STATE         -7   /* call out of order (e.g. extract before sample)       */
