@@ -1,7 +1,8 @@
 // Online stage (Sec. 5.2, Eq. elliptic_cond_reduced): c = argmin |P~ c - d|_2 by
-// CGLS on the normal equations with the patch-block (additive Schwarz)
-// preconditioner M = blockdiag((P~^T P~)_mm), then the reconstruction
-// u = sum_m chi_m Q_m c_m with chi_m = 1/#patches sharing the node.
+// CGLS on the normal equations, preconditioned by the block-tridiagonal Cholesky
+// factor of the scaled normal matrix over rows of patches (online_factor.cu) or, on
+// request, by the patch blocks alone, M = blockdiag((P~^T P~)_mm); then the
+// reconstruction u = sum_m chi_m Q_m c_m with chi_m = 1/#patches sharing the node.
 //
 // A batch of B right-hand sides runs side by side; vectors are stored
 // element-major with the batch index fastest ([element][B]).  Every quantity of

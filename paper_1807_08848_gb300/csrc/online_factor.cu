@@ -4,15 +4,19 @@
 //
 // H couples a patch only with its eight neighbours, so with the unknowns of one
 // row of patches as a block, H is block tridiagonal: diagonal blocks D_q and
-// sub-diagonal blocks E_q = H_{q+1,q}.  The factor is computed in FP32 on the
-// patch-block scaled matrix Hs = R^{-T} H R^{-1} (R = blockdiag(R_m), H_mm = R_m^T R_m,
-// so the diagonal patch blocks of Hs are identities):
+// sub-diagonal blocks E_q = H_{q+1,q}.  The factor is computed on the patch-block
+// scaled matrix Hs = R^{-T} H R^{-1} (R = blockdiag(R_m), H_mm = R_m^T R_m, so the
+// diagonal patch blocks of Hs are identities):
 //     L_q L_q^T = D_q - C_{q-1} C_{q-1}^T,   C_q = E_q L_q^{-T}
-// with explicit inverses Li_q = L_q^{-1}.  Applying M^{-1} = R^{-1} (L L^T)^{-1} R^{-T}
-// is then a per-patch triangular product, a forward and a backward sweep, and a
-// second per-patch product.  The FP64 CGLS iteration around
-// it keeps the least-squares solution at FP64 accuracy; on a non-positive pivot
-// the factorisation is repeated with a diagonal shift.
+// with explicit inverses Li_q = L_q^{-1}; in FP32 when every pivot of that attempt is
+// positive, else in FP64 (the large products on the tensor cores), repeated with a
+// growing diagonal shift on a non-positive pivot.  Each D_q is factorised by 64-wide
+// tiles (tile Cholesky, panel solve, trailing update) with a lookahead of one tile:
+// the next tile column is updated first, the rest of the trailing update runs on a
+// second stream while the next tile is factorised.  Applying
+// M^{-1} = R^{-1} (L L^T)^{-1} R^{-T} is then a per-patch triangular product, a
+// forward and a backward sweep, and a second per-patch product.  The FP64 CGLS
+// iteration around it keeps the least-squares solution at FP64 accuracy.
 #include "internal.h"
 
 #include <mutex>
