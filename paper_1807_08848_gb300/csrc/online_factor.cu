@@ -703,6 +703,9 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         DevBuf<GemmDescT<T>> d_all;
         MSP_TRY(upload(d_all, gds, s));
         size_t gi = 0;
+        // the tensor-core products of the side stream have their own workspace; declared
+        // before the stream, so that on every way out the stream is synchronised first
+        OzakiWork ozw_side;
         // side stream of the trailing updates and its events (panel final, rest of a
         // trailing update done, join), released on every way out
         struct SideStream {
@@ -717,7 +720,6 @@ msp_status factorize(Basis& B, const double* Hs64p, long long total, double shif
         } side;
         MSP_CUDA(cudaStreamCreateWithFlags(&side.st, cudaStreamNonBlocking));
         for (cudaEvent_t& e : side.ev) MSP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        OzakiWork ozw_side;   // the tensor-core products of the side stream have their own workspace
         for (size_t si = 0; si < steps.size(); ++si) {
             const Step& st = steps[si];
             const cudaStream_t ss = st.stream ? side.st : s;
